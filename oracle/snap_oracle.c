@@ -1,0 +1,796 @@
+/*
+ * FP64 CPU oracle for dynamic-bonding MD — TEST INFRASTRUCTURE ONLY.
+ *
+ * Follows "pySNAP + DyBond-v2" (arXiv 2609.21204):
+ *   Sec. II.A  two-state reaction, Eq. (1) K = k_on/k_off, eps = ln K
+ *   Sec. II.A  per-sweep probabilities, Eq. (2)
+ *   Sec. II.B  Metropolis factor on formation only, Eqs. (3)-(4)
+ *   Sec. II.C  the bonding sweep (Fig. 1): proposal, matching, acceptance,
+ *              breaking; occupancy read as it stood when the reaction began
+ *   Sec. II.E  counter-based Philox keyed by seed, step and stream, counted by
+ *              the sorted tag pair
+ * plus a plain WCA/LJ + FENE/harmonic force field and a Langevin integrator
+ * for the MD around the sweep.
+ *
+ * Readings where the paper is silent (shared with the CUDA path only as a
+ * written specification, never as code):
+ *   - valence > 1 is an occupancy counter with a per-type capacity; a particle
+ *     joins at most one new bond per reaction per sweep and never a second
+ *     bond to a partner it is already bonded to;
+ *   - the matching phase is a one-round locally dominant matching: every
+ *     proposal edge gets the priority word Philox(MATCH; min tag, max tag)[0];
+ *     an edge survives iff at both endpoints its key (priority << 32 | other
+ *     tag) is the largest among the edges touching that endpoint;
+ *   - the proposal keeps the partner minimising |r - r0|, ties to the smaller
+ *     tag; the window test is r_min^2 <= r^2 <= r_max^2 in FP64;
+ *   - T in Eq. (3) is the set-point kT; at kT = 0 the factor is [U_b <= 0];
+ *   - exp() in Eq. (3) is this file's own (Cody–Waite + Taylor), so that the
+ *     CUDA path, which implements the same published recipe, decides alike;
+ *   - Langevin: leapfrog form of velocity Verlet with drag -gamma v_{t-1/2}
+ *     and a uniform random force sqrt(2 gamma kT / dt) * sqrt(3) (2u - 1);
+ *   - no pair exclusions: WCA acts on bonded pairs too.
+ *
+ * Parity unpinned: none of the functions below is left without a test that
+ * ties it to the paper or to mathematics (closed forms, brute force,
+ * invariants); see tests/test_oracle_*.py.
+ */
+#include "snap_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- Philox */
+
+static void mulhilo32(uint32_t a, uint32_t b, uint32_t *hi, uint32_t *lo)
+{
+    uint64_t p = (uint64_t)a * (uint64_t)b;
+    *hi = (uint32_t)(p >> 32);
+    *lo = (uint32_t)p;
+}
+
+/* Philox-4x32 with 10 rounds: multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key
+ * increments 0x9E3779B9 / 0xBB67AE85 (Salmon, Moraes, Dror, Shaw, SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint32_t hi0, lo0, hi1, lo1;
+        mulhilo32(0xD2511F53u, c0, &hi0, &lo0);
+        mulhilo32(0xCD9E8D57u, c2, &hi1, &lo1);
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+double orc_u53(uint32_t w0, uint32_t w1)
+{
+    uint64_t m = ((uint64_t)w0 << 21) | (uint64_t)(w1 >> 11);
+    return (double)m * 0x1.0p-53;
+}
+
+static void orc_key(const orc_params *P, int32_t rx, int32_t stream, uint32_t key[2])
+{
+    key[0] = (uint32_t)(P->seed & 0xFFFFFFFFull);
+    key[1] = (uint32_t)(((P->seed >> 32) & 0xFFFFull) << 16) |
+             ((uint32_t)(rx & 0xFF) << 8) | (uint32_t)(stream & 0xFF);
+}
+
+/* Draw for the unordered tag pair (a < b) at a step on one stream of one reaction. */
+static void orc_pair_draw(const orc_params *P, int32_t rx, int32_t stream, int64_t step,
+                          int64_t a, int64_t b, uint32_t out[4])
+{
+    uint32_t key[2], ctr[4];
+    orc_key(P, rx, stream, key);
+    ctr[0] = (uint32_t)((uint64_t)step & 0xFFFFFFFFull);
+    ctr[1] = (uint32_t)((uint64_t)step >> 32);
+    ctr[2] = (uint32_t)a;
+    ctr[3] = (uint32_t)b;
+    orc_philox4x32_10(ctr, key, out);
+}
+
+/* ------------------------------------------------------------------ exp */
+
+/* exp(x) = 2^k exp(r), k = rint(x / ln2), r = x - k ln2 reduced in two fma
+ * steps with ln2 split into its nearest double and the remainder (Cody and
+ * Waite, "Software Manual for the Elementary Functions", 1980); exp(r) by its
+ * Taylor series to degree 13 (truncation < 5e-18 for |r| <= ln2/2), Horner
+ * form with fused multiply-adds; 2^k applied as two exact powers of two. */
+static const double ORC_INV_LN2 = 0x1.71547652b82fep+0;
+static const double ORC_LN2_HI = 0x1.62e42fefa39efp-1;
+static const double ORC_LN2_LO = 0x1.abc9e3b39803fp-56;
+
+static double orc_pow2i(int n)
+{
+    uint64_t bits = (uint64_t)(n + 1023) << 52;
+    double d;
+    memcpy(&d, &bits, sizeof d);
+    return d;
+}
+
+double orc_exp(double x)
+{
+    if (x != x) return x;
+    if (x > 709.7) return INFINITY;
+    if (x < -745.2) return 0.0;
+    double k = rint(x * ORC_INV_LN2);
+    double r = fma(-k, ORC_LN2_HI, x);
+    r = fma(-k, ORC_LN2_LO, r);
+    double p = 1.0 / 6227020800.0;            /* 1/13! */
+    p = fma(p, r, 1.0 / 479001600.0);         /* 1/12! */
+    p = fma(p, r, 1.0 / 39916800.0);          /* 1/11! */
+    p = fma(p, r, 1.0 / 3628800.0);           /* 1/10! */
+    p = fma(p, r, 1.0 / 362880.0);            /* 1/9!  */
+    p = fma(p, r, 1.0 / 40320.0);             /* 1/8!  */
+    p = fma(p, r, 1.0 / 5040.0);              /* 1/7!  */
+    p = fma(p, r, 1.0 / 720.0);               /* 1/6!  */
+    p = fma(p, r, 1.0 / 120.0);               /* 1/5!  */
+    p = fma(p, r, 1.0 / 24.0);                /* 1/4!  */
+    p = fma(p, r, 1.0 / 6.0);                 /* 1/3!  */
+    p = fma(p, r, 0.5);
+    p = fma(p, r, 1.0);
+    p = fma(p, r, 1.0);
+    int ki = (int)k;
+    int k1 = ki / 2;
+    int k2 = ki - k1;
+    return (p * orc_pow2i(k1)) * orc_pow2i(k2);
+}
+
+/* ------------------------------------------------------- bond energies */
+
+double orc_bond_energy(const orc_params *P, int32_t bt, double r)
+{
+    double k = P->bk[bt], r0 = P->br0[bt];
+    if (P->bkind[bt] == ORC_HARMONIC) {
+        double dr = r - r0;
+        return 0.5 * k * dr * dr;
+    }
+    /* FENE: -1/2 k R0^2 ln(1 - (r/R0)^2) */
+    double q = (r * r) / (r0 * r0);
+    if (q >= 1.0) return INFINITY;
+    return -0.5 * k * r0 * r0 * log(1.0 - q);
+}
+
+/* Eq. (3): P_on(r) = P_on^0 exp(-U_b(r)/kT); at kT = 0 the factor is [U_b <= 0]. */
+static double orc_p_on(const orc_params *P, const orc_reaction *R, double r)
+{
+    double dr = r - P->br0[R->bond_type];
+    double U = 0.5 * P->bk[R->bond_type] * dr * dr;
+    if (P->kT > 0.0) {
+        double a = U / P->kT;
+        return R->p_on0 * orc_exp(-a);
+    }
+    return (U <= 0.0) ? R->p_on0 : 0.0;
+}
+
+/* ------------------------------------------------------------ geometry */
+
+static double orc_min_image(double d, double L, double invL)
+{
+    double k = rint(d * invL);
+    double s = L * k;
+    return d - s;
+}
+
+static double orc_dist2(const orc_params *P, const orc_state *S, int64_t i, int64_t j,
+                        double *dx, double *dy, double *dz)
+{
+    double ix = 1.0 / P->box[0], iy = 1.0 / P->box[1], iz = 1.0 / P->box[2];
+    double a = orc_min_image(S->x[j] - S->x[i], P->box[0], ix);
+    double b = orc_min_image(S->y[j] - S->y[i], P->box[1], iy);
+    double c = orc_min_image(S->z[j] - S->z[i], P->box[2], iz);
+    *dx = a; *dy = b; *dz = c;
+    double aa = a * a;
+    double bb = b * b;
+    double cc = c * c;
+    return (aa + bb) + cc;
+}
+
+/* Cell grid with head/next linked lists; falls back to all pairs when any
+ * axis has fewer than three cells. */
+typedef struct {
+    int nc[3];
+    int brute;
+    int64_t *head, *next;
+} orc_grid;
+
+static int orc_grid_build(const orc_params *P, const orc_state *S, double cut, orc_grid *g)
+{
+    g->head = g->next = NULL;
+    g->brute = 0;
+    for (int d = 0; d < 3; ++d) {
+        g->nc[d] = (int)floor(P->box[d] / cut);
+        if (g->nc[d] < 3) g->brute = 1;
+    }
+    if (g->brute) return 0;
+    int64_t ncell = (int64_t)g->nc[0] * g->nc[1] * g->nc[2];
+    g->head = (int64_t *)malloc(sizeof(int64_t) * (size_t)ncell);
+    g->next = (int64_t *)malloc(sizeof(int64_t) * (size_t)(P->n > 0 ? P->n : 1));
+    if (!g->head || !g->next) return -1;
+    for (int64_t c = 0; c < ncell; ++c) g->head[c] = -1;
+    for (int64_t i = P->n - 1; i >= 0; --i) {
+        int cx = (int)floor(S->x[i] / P->box[0] * g->nc[0]);
+        int cy = (int)floor(S->y[i] / P->box[1] * g->nc[1]);
+        int cz = (int)floor(S->z[i] / P->box[2] * g->nc[2]);
+        cx = ((cx % g->nc[0]) + g->nc[0]) % g->nc[0];
+        cy = ((cy % g->nc[1]) + g->nc[1]) % g->nc[1];
+        cz = ((cz % g->nc[2]) + g->nc[2]) % g->nc[2];
+        int64_t c = ((int64_t)cz * g->nc[1] + cy) * g->nc[0] + cx;
+        g->next[i] = g->head[c];
+        g->head[c] = i;
+    }
+    return 0;
+}
+
+static void orc_grid_free(orc_grid *g)
+{
+    free(g->head);
+    free(g->next);
+    g->head = g->next = NULL;
+}
+
+/* Calls fn(j, ctx) for every particle j != i in the 27 cells around i
+ * (every j != i when the grid is in all-pairs mode). */
+typedef void (*orc_visit)(int64_t j, void *ctx);
+
+static void orc_grid_visit(const orc_params *P, const orc_state *S, const orc_grid *g,
+                           int64_t i, orc_visit fn, void *ctx)
+{
+    if (g->brute) {
+        for (int64_t j = 0; j < P->n; ++j)
+            if (j != i) fn(j, ctx);
+        return;
+    }
+    int cx = (int)floor(S->x[i] / P->box[0] * g->nc[0]);
+    int cy = (int)floor(S->y[i] / P->box[1] * g->nc[1]);
+    int cz = (int)floor(S->z[i] / P->box[2] * g->nc[2]);
+    cx = ((cx % g->nc[0]) + g->nc[0]) % g->nc[0];
+    cy = ((cy % g->nc[1]) + g->nc[1]) % g->nc[1];
+    cz = ((cz % g->nc[2]) + g->nc[2]) % g->nc[2];
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int x = (cx + dx + g->nc[0]) % g->nc[0];
+                int y = (cy + dy + g->nc[1]) % g->nc[1];
+                int z = (cz + dz + g->nc[2]) % g->nc[2];
+                int64_t c = ((int64_t)z * g->nc[1] + y) * g->nc[0] + x;
+                for (int64_t j = g->head[c]; j >= 0; j = g->next[j])
+                    if (j != i) fn(j, ctx);
+            }
+}
+
+/* ----------------------------------------------------------- the sweep */
+
+static int orc_partner_type_ok(const orc_reaction *R, int32_t ti, int32_t tj)
+{
+    if (ti == R->type_a && tj == R->type_b) return 1;
+    if (ti == R->type_b && tj == R->type_a) return 1;
+    return 0;
+}
+
+static int orc_is_bonded(const orc_state *S, int64_t i, int64_t j)
+{
+    for (int s = 0; s < ORC_VMAX; ++s)
+        if (S->dp[i * ORC_VMAX + s] == (int32_t)j) return 1;
+    return 0;
+}
+
+typedef struct {
+    const orc_params *P;
+    const orc_state *S;
+    const orc_reaction *R;
+    int64_t i;
+    double rmin2, rmax2, r0;
+    int64_t best;
+    double best_d, best_r;
+    int64_t scanned, in_window;
+    int32_t *list;      /* optional candidate list */
+    int32_t cap, count;
+} orc_prop_ctx;
+
+/* Proposal phase (Sec. II.C, Fig. 1a): a free site keeps the free,
+ * type-compatible partner inside [r_min, r_max] whose separation is closest
+ * to the rest length r0 of the reaction's bond. */
+static void orc_prop_visit(int64_t j, void *vctx)
+{
+    orc_prop_ctx *c = (orc_prop_ctx *)vctx;
+    const orc_state *S = c->S;
+    const orc_params *P = c->P;
+    int32_t ti = S->type[c->i], tj = S->type[j];
+    if (!orc_partner_type_ok(c->R, ti, tj)) return;
+    if (S->occ[j] >= P->valence[tj]) return;
+    if (orc_is_bonded(S, c->i, j)) return;
+    c->scanned++;
+    double dx, dy, dz;
+    double r2 = orc_dist2(P, S, c->i, j, &dx, &dy, &dz);
+    if (r2 < c->rmin2 || r2 > c->rmax2) return;
+    c->in_window++;
+    if (c->list && c->count < c->cap) c->list[c->count] = (int32_t)j;
+    c->count++;
+    double r = sqrt(r2);
+    double d = fabs(r - c->r0);
+    if (c->best < 0 || d < c->best_d || (d == c->best_d && j < c->best)) {
+        c->best = j;
+        c->best_d = d;
+        c->best_r = r;
+    }
+}
+
+static double orc_max_rmax(const orc_params *P)
+{
+    double m = 0.0;
+    for (int a = 0; a < P->nrx; ++a)
+        if (P->rx[a].r_max > m) m = P->rx[a].r_max;
+    return m;
+}
+
+static void orc_slot_remove(orc_state *S, int64_t i, int64_t j)
+{
+    int32_t *p = S->dp + i * ORC_VMAX;
+    int32_t *x = S->drx + i * ORC_VMAX;
+    int64_t *b = S->dbirth + i * ORC_VMAX;
+    int w = 0;
+    for (int s = 0; s < ORC_VMAX; ++s) {
+        if (p[s] < 0 || p[s] == (int32_t)j) continue;
+        p[w] = p[s]; x[w] = x[s]; b[w] = b[s];
+        ++w;
+    }
+    for (; w < ORC_VMAX; ++w) { p[w] = -1; x[w] = -1; b[w] = 0; }
+    S->occ[i] -= 1;
+}
+
+static void orc_slot_insert(orc_state *S, int64_t i, int64_t j, int32_t rx, int64_t step)
+{
+    int32_t *p = S->dp + i * ORC_VMAX;
+    int32_t *x = S->drx + i * ORC_VMAX;
+    int64_t *b = S->dbirth + i * ORC_VMAX;
+    int s = ORC_VMAX - 1;
+    /* shift larger partners right; the caller guarantees a free slot */
+    while (s > 0 && (p[s - 1] < 0 || p[s - 1] > (int32_t)j)) {
+        p[s] = p[s - 1]; x[s] = x[s - 1]; b[s] = b[s - 1];
+        --s;
+    }
+    p[s] = (int32_t)j; x[s] = rx; b[s] = step;
+    S->occ[i] += 1;
+}
+
+int32_t orc_candidates(const orc_params *P, const orc_state *S, int32_t a, int64_t i,
+                       int32_t *out, int32_t cap)
+{
+    if (a < 0 || a >= P->nrx) return -1;
+    orc_grid g;
+    if (orc_grid_build(P, S, orc_max_rmax(P), &g) != 0) return -1;
+    const orc_reaction *R = &P->rx[a];
+    orc_prop_ctx c;
+    memset(&c, 0, sizeof c);
+    c.P = P; c.S = S; c.R = R; c.i = i;
+    c.rmin2 = R->r_min * R->r_min;
+    c.rmax2 = R->r_max * R->r_max;
+    c.r0 = P->br0[R->bond_type];
+    c.best = -1;
+    c.list = out; c.cap = cap;
+    int32_t ti = S->type[i];
+    if ((ti == R->type_a || ti == R->type_b) && S->occ[i] < P->valence[ti])
+        orc_grid_visit(P, S, &g, i, orc_prop_visit, &c);
+    orc_grid_free(&g);
+    return c.count;
+}
+
+int orc_sweep(const orc_params *P, orc_state *S, int64_t step, orc_sweep_stats *st,
+              orc_trace *tr)
+{
+    int64_t n = P->n;
+    if (P->nrx <= 0 || n <= 0) return ORC_OK;
+    orc_sweep_stats local;
+    memset(&local, 0, sizeof local);
+    orc_grid g;
+    if (orc_grid_build(P, S, orc_max_rmax(P), &g) != 0) return ORC_ERR_ARG;
+
+    int32_t *prop = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    double *prop_r = (double *)malloc(sizeof(double) * (size_t)n);
+    uint64_t *bestkey = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    int32_t *fpart = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    uint8_t *brk = (uint8_t *)malloc((size_t)n * ORC_VMAX);
+    int64_t nb_max = n * ORC_VMAX / 2 + 1;
+    int64_t *brk_i = (int64_t *)malloc(sizeof(int64_t) * (size_t)nb_max);
+    int64_t *brk_j = (int64_t *)malloc(sizeof(int64_t) * (size_t)nb_max);
+    int64_t *brk_life = (int64_t *)malloc(sizeof(int64_t) * (size_t)nb_max);
+
+    /* reaction order: Fisher–Yates driven by Philox(ORDER), redrawn every sweep
+     * so that no reaction is favoured by its registration order (Sec. II.C) */
+    int32_t order[ORC_MAX_RX];
+    for (int a = 0; a < P->nrx; ++a) order[a] = a;
+    for (int k = P->nrx - 1; k >= 1; --k) {
+        uint32_t w[4];
+        orc_pair_draw(P, 0, ORC_ORDER, step, k, 0, w);
+        int j = (int)(((uint64_t)w[0] * (uint64_t)(k + 1)) >> 32);
+        int32_t t = order[k]; order[k] = order[j]; order[j] = t;
+    }
+    if (tr && tr->order)
+        for (int a = 0; a < P->nrx; ++a) tr->order[a] = order[a];
+
+    for (int slot = 0; slot < P->nrx; ++slot) {
+        int32_t a = order[slot];
+        const orc_reaction *R = &P->rx[a];
+        double rmin2 = R->r_min * R->r_min, rmax2 = R->r_max * R->r_max;
+        double r0 = P->br0[R->bond_type];
+
+        /* (a) proposal — occupancies as they stand when the reaction begins */
+        for (int64_t i = 0; i < n; ++i) {
+            prop[i] = -1;
+            prop_r[i] = 0.0;
+            bestkey[i] = 0;
+            fpart[i] = -1;
+            int32_t ti = S->type[i];
+            if (ti != R->type_a && ti != R->type_b) continue;
+            if (S->occ[i] >= P->valence[ti]) continue;
+            orc_prop_ctx c;
+            memset(&c, 0, sizeof c);
+            c.P = P; c.S = S; c.R = R; c.i = i;
+            c.rmin2 = rmin2; c.rmax2 = rmax2; c.r0 = r0;
+            c.best = -1;
+            orc_grid_visit(P, S, &g, i, orc_prop_visit, &c);
+            local.scanned += c.scanned;
+            local.in_window += c.in_window;
+            if (c.best >= 0) {
+                prop[i] = (int32_t)c.best;
+                prop_r[i] = c.best_r;
+                local.proposals++;
+            }
+        }
+        /* (b) matching — per-edge Philox priority, locally dominant edges win */
+        for (int64_t i = 0; i < n; ++i) {
+            if (prop[i] < 0) continue;
+            int64_t j = prop[i];
+            int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+            uint32_t w[4];
+            orc_pair_draw(P, a, ORC_MATCH, step, lo, hi, w);
+            uint64_t ki = ((uint64_t)w[0] << 32) | (uint64_t)(uint32_t)j;
+            uint64_t kj = ((uint64_t)w[0] << 32) | (uint64_t)(uint32_t)i;
+            if (ki > bestkey[i]) bestkey[i] = ki;
+            if (kj > bestkey[j]) bestkey[j] = kj;
+        }
+        /* (c) acceptance of surviving edges with Eq. (3) */
+        for (int64_t i = 0; i < n; ++i) {
+            if (prop[i] < 0) continue;
+            int64_t j = prop[i];
+            if (prop[j] == (int32_t)i && j < i) continue;   /* mutual edge: handled once */
+            local.edges++;
+            int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+            uint32_t w[4];
+            orc_pair_draw(P, a, ORC_MATCH, step, lo, hi, w);
+            uint64_t ki = ((uint64_t)w[0] << 32) | (uint64_t)(uint32_t)j;
+            uint64_t kj = ((uint64_t)w[0] << 32) | (uint64_t)(uint32_t)i;
+            if (bestkey[i] != ki || bestkey[j] != kj) continue;
+            local.survivors++;
+            if (tr && slot == 0 && tr->matched) { tr->matched[i] = (int32_t)j; tr->matched[j] = (int32_t)i; }
+            orc_pair_draw(P, a, ORC_FORM, step, lo, hi, w);
+            double u = orc_u53(w[0], w[1]);
+            double pon = orc_p_on(P, R, prop_r[i]);
+            if (u < pon) {
+                fpart[i] = (int32_t)j;
+                fpart[j] = (int32_t)i;
+                local.formed++;
+            }
+        }
+        if (tr && slot == 0) {
+            for (int64_t i = 0; i < n; ++i) {
+                if (tr->prop) tr->prop[i] = prop[i];
+                if (tr->prop_r) tr->prop_r[i] = prop_r[i];
+                if (tr->formed) tr->formed[i] = (uint8_t)(fpart[i] >= 0);
+            }
+        }
+        /* (d) breaking of this reaction's pre-existing bonds with P_off */
+        memset(brk, 0, (size_t)n * ORC_VMAX);
+        for (int64_t i = 0; i < n; ++i) {
+            for (int s = 0; s < ORC_VMAX; ++s) {
+                int32_t j = S->dp[i * ORC_VMAX + s];
+                if (j < 0 || j < i) continue;
+                if (S->drx[i * ORC_VMAX + s] != a) continue;
+                local.break_tested++;
+                uint32_t w[4];
+                orc_pair_draw(P, a, ORC_BREAK, step, i, j, w);
+                if (orc_u53(w[0], w[1]) < R->p_off) brk[i * ORC_VMAX + s] = 1;
+            }
+        }
+        /* apply: breaks first, then the formed bonds (occupancy updated for the
+         * reactions processed later in this sweep).  Broken pairs are listed
+         * before any slot moves so that the flags keep their meaning. */
+        int64_t nbrk = 0;
+        for (int64_t i = 0; i < n; ++i)
+            for (int s = 0; s < ORC_VMAX; ++s)
+                if (brk[i * ORC_VMAX + s]) {
+                    brk_i[nbrk] = i;
+                    brk_j[nbrk] = S->dp[i * ORC_VMAX + s];
+                    brk_life[nbrk] = step - S->dbirth[i * ORC_VMAX + s];
+                    ++nbrk;
+                }
+        for (int64_t q = 0; q < nbrk; ++q) {
+            if (S->life_hist && S->nhist > 0) {
+                int64_t per = P->bond_period > 0 ? P->bond_period : 1;
+                int64_t b = brk_life[q] / per;
+                if (b >= S->nhist) b = S->nhist - 1;
+                if (b < 0) b = 0;
+                S->life_hist[b]++;
+            }
+            orc_slot_remove(S, brk_i[q], brk_j[q]);
+            orc_slot_remove(S, brk_j[q], brk_i[q]);
+            local.broken++;
+        }
+        for (int64_t i = 0; i < n; ++i)
+            if (fpart[i] >= 0) orc_slot_insert(S, i, fpart[i], a, step);
+    }
+    free(prop); free(prop_r); free(bestkey); free(fpart); free(brk);
+    free(brk_i); free(brk_j); free(brk_life);
+    orc_grid_free(&g);
+    if (st) {
+        st->scanned += local.scanned;
+        st->in_window += local.in_window;
+        st->proposals += local.proposals;
+        st->edges += local.edges;
+        st->survivors += local.survivors;
+        st->formed += local.formed;
+        st->break_tested += local.break_tested;
+        st->broken += local.broken;
+    }
+    return ORC_OK;
+}
+
+/* --------------------------------------------------------------- forces */
+
+static double orc_pair_rc(const orc_params *P, int32_t ti, int32_t tj)
+{
+    double rc = P->rcut[ti * ORC_MAX_TYPES + tj];
+    if (rc > 0.0) return rc;
+    double sig = 0.5 * (P->sigma[ti] + P->sigma[tj]);
+    return sig * pow(2.0, 1.0 / 6.0);
+}
+
+typedef struct {
+    const orc_params *P;
+    orc_state *S;
+    int64_t i;
+    double epair, vir;
+} orc_force_ctx;
+
+/* Shifted Lennard-Jones, U = 4 eps [(s/r)^12 - (s/r)^6] - U(r_c) for r < r_c;
+ * with r_c = 2^(1/6) s this is the WCA potential. */
+static void orc_force_visit(int64_t j, void *vctx)
+{
+    orc_force_ctx *c = (orc_force_ctx *)vctx;
+    const orc_params *P = c->P;
+    orc_state *S = c->S;
+    int64_t i = c->i;
+    if (j <= i) return;
+    int32_t ti = S->type[i], tj = S->type[j];
+    double rc = orc_pair_rc(P, ti, tj);
+    double dx, dy, dz;
+    double r2 = orc_dist2(P, S, i, j, &dx, &dy, &dz);
+    if (r2 >= rc * rc) return;
+    double eps = P->eps[ti * ORC_MAX_TYPES + tj];
+    double sig = 0.5 * (P->sigma[ti] + P->sigma[tj]);
+    double s2 = (sig * sig) / r2;
+    double s6 = s2 * s2 * s2;
+    double s12 = s6 * s6;
+    double fr = 24.0 * eps * (2.0 * s12 - s6) / r2;   /* -(dU/dr)/r */
+    double c2 = (sig * sig) / (rc * rc);
+    double c6 = c2 * c2 * c2;
+    double u = 4.0 * eps * (s12 - s6) - 4.0 * eps * (c6 * c6 - c6);
+    S->fx[i] -= fr * dx; S->fy[i] -= fr * dy; S->fz[i] -= fr * dz;
+    S->fx[j] += fr * dx; S->fy[j] += fr * dy; S->fz[j] += fr * dz;
+    if (S->pe) { S->pe[i] += 0.5 * u; S->pe[j] += 0.5 * u; }
+    c->epair += u;
+    c->vir += fr * r2;
+}
+
+/* Bond force between i and j (j > i) of bond type bt; returns 0 or ORC_ERR_FENE. */
+static int orc_bond_pair(const orc_params *P, orc_state *S, int64_t i, int64_t j, int32_t bt,
+                         double *eb, double *vir)
+{
+    double dx, dy, dz;
+    double r2 = orc_dist2(P, S, i, j, &dx, &dy, &dz);
+    double k = P->bk[bt], r0 = P->br0[bt];
+    double fb, u;
+    if (P->bkind[bt] == ORC_HARMONIC) {
+        double r = sqrt(r2);
+        fb = k * (r - r0) / r;       /* (dU/dr)/r, pulls i towards j when stretched */
+        u = 0.5 * k * (r - r0) * (r - r0);
+    } else {
+        double q = r2 / (r0 * r0);
+        if (q >= 1.0) return ORC_ERR_FENE;
+        fb = k / (1.0 - q);
+        u = -0.5 * k * r0 * r0 * log(1.0 - q);
+    }
+    S->fx[i] += fb * dx; S->fy[i] += fb * dy; S->fz[i] += fb * dz;
+    S->fx[j] -= fb * dx; S->fy[j] -= fb * dy; S->fz[j] -= fb * dz;
+    if (S->pe) { S->pe[i] += 0.5 * u; S->pe[j] += 0.5 * u; }
+    *eb += u;
+    *vir -= fb * r2;
+    return 0;
+}
+
+int orc_forces(const orc_params *P, orc_state *S, double *e_pair, double *e_bond,
+               double *virial)
+{
+    int64_t n = P->n;
+    double rcmax = 0.0;
+    for (int a = 0; a < P->ntypes; ++a)
+        for (int b = 0; b < P->ntypes; ++b) {
+            double rc = orc_pair_rc(P, a, b);
+            if (rc > rcmax) rcmax = rc;
+        }
+    for (int64_t i = 0; i < n; ++i) {
+        S->fx[i] = S->fy[i] = S->fz[i] = 0.0;
+        if (S->pe) S->pe[i] = 0.0;
+    }
+    orc_grid g;
+    if (orc_grid_build(P, S, rcmax > 0 ? rcmax : 1.0, &g) != 0) return ORC_ERR_ARG;
+    orc_force_ctx c;
+    c.P = P; c.S = S; c.epair = 0.0; c.vir = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        c.i = i;
+        orc_grid_visit(P, S, &g, i, orc_force_visit, &c);
+    }
+    orc_grid_free(&g);
+    double eb = 0.0, vir = c.vir;
+    int err = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int s = 0; s < ORC_SMAX; ++s) {
+            int32_t j = S->sp[i * ORC_SMAX + s];
+            if (j <= i) continue;
+            if (orc_bond_pair(P, S, i, j, S->sbt[i * ORC_SMAX + s], &eb, &vir)) err = ORC_ERR_FENE;
+        }
+        for (int s = 0; s < ORC_VMAX; ++s) {
+            int32_t j = S->dp[i * ORC_VMAX + s];
+            if (j <= i) continue;
+            int32_t bt = P->rx[S->drx[i * ORC_VMAX + s]].bond_type;
+            if (orc_bond_pair(P, S, i, j, bt, &eb, &vir)) err = ORC_ERR_FENE;
+        }
+    }
+    if (e_pair) *e_pair = c.epair;
+    if (e_bond) *e_bond = eb;
+    if (virial) *virial = vir;
+    return err;
+}
+
+/* ----------------------------------------------------------- integrator */
+
+static void orc_wrap(double *x, int32_t *img, double L)
+{
+    if (*x >= L) {
+        *x -= L;
+        *img += 1;
+    } else if (*x < 0.0) {
+        *x += L;
+        *img -= 1;
+        if (*x >= L) {
+            *x -= L;
+            *img += 1;
+        }
+    }
+}
+
+/* One MD step per iteration: [bond sweep if step % period == 0] ->
+ * conservative forces at x_t -> Langevin kick with drag on v_{t-1/2} and a
+ * counter-based random force -> drift -> wrap. */
+int orc_run(const orc_params *P, orc_state *S, int64_t nsteps, double *ke_out)
+{
+    int64_t n = P->n;
+    double c = sqrt(((2.0 * P->gamma) * P->kT) / P->dt);
+    double s3 = sqrt(3.0);
+    uint32_t key[2];
+    orc_key(P, 0, ORC_LANGEVIN, key);
+    int err = 0;
+    double ke = 0.0;
+    for (int64_t it = 0; it < nsteps; ++it) {
+        int64_t t = S->step;
+        int64_t per = P->bond_period > 0 ? P->bond_period : 1;
+        if (P->nrx > 0 && t % per == 0) orc_sweep(P, S, t, NULL, NULL);
+        int e = orc_forces(P, S, NULL, NULL, NULL);
+        if (e) err = e;
+        ke = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            uint32_t ctr[4] = {(uint32_t)((uint64_t)t & 0xFFFFFFFFull), (uint32_t)((uint64_t)t >> 32),
+                               (uint32_t)i, 0u};
+            uint32_t w[4];
+            orc_philox4x32_10(ctr, key, w);
+            double xi[3];
+            for (int d = 0; d < 3; ++d) {
+                double u = (double)w[d] * 0x1.0p-32 + 0x1.0p-33;
+                xi[d] = s3 * (2.0 * u - 1.0);
+            }
+            double f[3] = {S->fx[i], S->fy[i], S->fz[i]};
+            double *v[3] = {&S->vx[i], &S->vy[i], &S->vz[i]};
+            double *x[3] = {&S->x[i], &S->y[i], &S->z[i]};
+            for (int d = 0; d < 3; ++d) {
+                double drag = P->gamma * *v[d];
+                double acc = (f[d] - drag) + c * xi[d];
+                double vs = *v[d] + (0.5 * P->dt) * acc;   /* synchronised v_t */
+                ke += 0.5 * vs * vs;
+                *v[d] = *v[d] + P->dt * acc;
+                *x[d] = *x[d] + P->dt * *v[d];
+                if (!isfinite(*x[d])) err = ORC_ERR_NONFINITE;
+                orc_wrap(x[d], &S->img[3 * i + d], P->box[d]);
+            }
+        }
+        S->step = t + 1;
+    }
+    if (ke_out) *ke_out = ke;
+    return err;
+}
+
+/* ------------------------------------------------------------ pair sets */
+
+typedef struct {
+    const orc_params *P;
+    const orc_state *S;
+    int64_t i;
+    double extra;
+    int use_rx;
+    int32_t *out;
+    int64_t cap, count;
+} orc_pairs_ctx;
+
+static double orc_reactive_cut(const orc_params *P, int32_t ti, int32_t tj)
+{
+    double m = 0.0;
+    for (int a = 0; a < P->nrx; ++a)
+        if (orc_partner_type_ok(&P->rx[a], ti, tj) && P->rx[a].r_max > m) m = P->rx[a].r_max;
+    return m;
+}
+
+static void orc_pairs_visit(int64_t j, void *vctx)
+{
+    orc_pairs_ctx *c = (orc_pairs_ctx *)vctx;
+    if (j <= c->i) return;
+    int32_t ti = c->S->type[c->i], tj = c->S->type[j];
+    double rc = orc_pair_rc(c->P, ti, tj);
+    if (c->use_rx) {
+        double rr = orc_reactive_cut(c->P, ti, tj);
+        if (rr > rc) rc = rr;
+    }
+    rc += c->extra;
+    double dx, dy, dz;
+    double r2 = orc_dist2(c->P, c->S, c->i, j, &dx, &dy, &dz);
+    if (r2 >= rc * rc) return;
+    if (c->count < c->cap) {
+        c->out[2 * c->count] = (int32_t)c->i;
+        c->out[2 * c->count + 1] = (int32_t)j;
+    }
+    c->count++;
+}
+
+int64_t orc_pairs_within(const orc_params *P, const orc_state *S, double extra,
+                         int use_reactive_cut, int32_t *out, int64_t cap)
+{
+    double cut = 0.0;
+    for (int a = 0; a < P->ntypes; ++a)
+        for (int b = 0; b < P->ntypes; ++b) {
+            double rc = orc_pair_rc(P, a, b);
+            if (use_reactive_cut) {
+                double rr = orc_reactive_cut(P, a, b);
+                if (rr > rc) rc = rr;
+            }
+            if (rc > cut) cut = rc;
+        }
+    orc_grid g;
+    if (orc_grid_build(P, S, cut + extra, &g) != 0) return -1;
+    orc_pairs_ctx c;
+    c.P = P; c.S = S; c.extra = extra; c.use_rx = use_reactive_cut;
+    c.out = out; c.cap = cap; c.count = 0;
+    for (int64_t i = 0; i < P->n; ++i) {
+        c.i = i;
+        orc_grid_visit(P, S, &g, i, orc_pairs_visit, &c);
+    }
+    orc_grid_free(&g);
+    return c.count;
+}

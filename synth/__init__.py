@@ -1,0 +1,8 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+Holds geometry and parameter values only; no dynamic-bonding arithmetic."""
+from .configs import (System, Reaction, BondType, HARMONIC, FENE, assoc_ab, telechelic,
+                      colloid_linker, telechelic_sweep, frozen_pairs, random_frozen)
+
+__all__ = ["System", "Reaction", "BondType", "HARMONIC", "FENE", "assoc_ab", "telechelic",
+           "colloid_linker", "telechelic_sweep", "frozen_pairs", "random_frozen"]
