@@ -1,0 +1,232 @@
+/*
+ * snap — B300-native dynamic-bonding molecular dynamics: C ABI.
+ *
+ * One MD step = [neighbour-list rebuild when any particle moved more than
+ * skin/2] -> [bond sweep every bond_period steps] -> pair + bond forces ->
+ * Langevin kick/drift.  All of it runs in hand-written CUDA kernels for
+ * sm_103a on the stream given in snap_config; nothing returns to the host
+ * except on the snap_get_* / snap_sync calls.
+ *
+ * The method is the dynamic-bonding scheme of "pySNAP + DyBond-v2"
+ * (arXiv 2609.21204), Sec. II:
+ *   - a reaction (snap_add_reaction) is a two-state process between sites of
+ *     two types with per-sweep probabilities P_on^0 and P_off (Eqs. 1-2);
+ *   - formation is accepted with P_on^0 exp(-U_b(r)/kT), breaking with P_off
+ *     (Eq. 3; Eq. 4 for the harmonic bond);
+ *   - the sweep runs proposal, matching, acceptance and breaking per
+ *     reaction, reading occupancies as they stood when the reaction began
+ *     (Sec. II.C, Fig. 1), in a random reaction order redrawn every sweep;
+ *   - every random decision is a Philox-4x32-10 draw keyed by the seed, the
+ *     reaction and the stream, counted by the step and the sorted tag pair
+ *     (Sec. II.E), so results do not depend on thread scheduling or memory
+ *     order.
+ * Readings where the paper is silent: valence is a per-type occupancy counter
+ * (a particle joins at most one new bond per reaction per sweep, never two
+ * bonds to one partner); matching is a one-round locally dominant matching on
+ * per-edge Philox priorities; kT in Eq. 3 is the set-point kT (kT = 0 gives
+ * the factor [U_b <= 0]); the window test r_min^2 <= r^2 <= r_max^2 and the
+ * acceptance are computed in FP64 in every precision mode.
+ *
+ * Conventions for every call:
+ *   - particles are identified by their tag 0..n-1 (global over replicas:
+ *     replica r owns tags [sum_{q<r} n_q, sum_{q<=r} n_q)); every host array
+ *     is in tag order; positions are x,y,z triples (n*3 doubles);
+ *   - host arrays passed in are copied before the call returns; host arrays
+ *     passed out are owned by the caller and must hold the stated size;
+ *   - no call aborts the process; errors are returned as snap_status and
+ *     described by snap_last_error(); device-side faults (non-finite
+ *     positions, FENE overstretch, neighbour-list overflow) latch a status
+ *     word that snap_sync / snap_step / snap_get_* report;
+ *   - all GPU work is ordered on cfg.stream; calls that return host data
+ *     synchronise that stream.
+ */
+#ifndef SNAP_H
+#define SNAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct snap_ctx snap_ctx;
+
+typedef enum {
+    SNAP_OK = 0,
+    SNAP_ERR_ARG = 1,            /* invalid argument or size */
+    SNAP_ERR_STATE = 2,          /* call out of order (e.g. step before particles) */
+    SNAP_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    SNAP_ERR_OOM = 4,            /* device allocation failed */
+    SNAP_ERR_NLIST_OVERFLOW = 5, /* neighbour capacity exceeded (grown and retried internally) */
+    SNAP_ERR_FENE_OVERSTRETCH = 6,
+    SNAP_ERR_NONFINITE = 7,      /* a position became NaN/Inf */
+    SNAP_ERR_TIMEOUT = 8
+} snap_status;
+
+enum { SNAP_FP64 = 0, SNAP_MIXED = 1 };     /* precision modes */
+enum { SNAP_HARMONIC = 0, SNAP_FENE = 1 };  /* bond kinds */
+
+#define SNAP_MAX_TYPES 8
+#define SNAP_MAX_BOND_TYPES 8
+#define SNAP_MAX_REACTIONS 8
+#define SNAP_MAX_VALENCE 4       /* dynamic bonds per particle */
+#define SNAP_MAX_STATIC 4        /* static bonds per particle */
+
+typedef void *(*snap_alloc_fn)(size_t bytes, void *user);
+typedef void (*snap_free_fn)(void *ptr, void *user);
+
+typedef struct {
+    int64_t n;               /* total particles (sum over replicas) */
+    double box[3];           /* periodic box edges (single system; replica_box overrides) */
+    double dt, kT, gamma;    /* time step, set-point temperature, Langevin friction */
+    uint64_t seed;           /* Philox key; only the low 48 bits are used */
+    int32_t precision;       /* SNAP_FP64: all FP64; SNAP_MIXED: FP32 pair/bond forces */
+    int32_t bond_period;     /* n of Eq. 2: sweep every bond_period steps (>= 1) */
+    double skin;             /* neighbour-list skin (> 0) */
+    int32_t n_replicas;      /* 0 or 1: one system; > 1: independent replicas */
+    const int64_t *replica_n;     /* n_replicas counts (NULL if one system) */
+    const double *replica_box;    /* n_replicas*3 box edges (NULL: all use box) */
+    const double *replica_kT;     /* n_replicas set-point kT (NULL: all use kT) */
+    const uint64_t *replica_seed; /* n_replicas seeds (NULL: seed + replica index) */
+    void *stream;            /* cudaStream_t the library launches on (NULL: default stream) */
+    snap_alloc_fn alloc;     /* device allocator (NULL: cudaMalloc) */
+    snap_free_fn free;       /* matching release function */
+    void *alloc_user;        /* passed to alloc/free */
+    int32_t block_size;      /* threads per block for particle kernels (0: 256) */
+    int32_t nlist_capacity;  /* initial neighbours per particle (0: from density) */
+    int32_t lifetime_bins;   /* bins of the bond-lifetime histogram (0: 256) */
+} snap_config;
+
+typedef struct {
+    int64_t step;            /* steps taken so far */
+    int64_t n_bonds;         /* dynamic bonds present */
+    int64_t sweeps;          /* sweeps performed */
+    int64_t formed_total, broken_total;
+    /* counters of the most recent sweep (summed over reactions and replicas) */
+    int64_t scanned;         /* neighbour entries examined by free reactive sites */
+    int64_t in_window;       /* compatible partners inside [r_min, r_max] */
+    int64_t proposals, edges, survivors, formed, break_tested, broken;
+    int64_t nlist_builds;    /* neighbour-list rebuilds so far */
+    int64_t nlist_entries;   /* neighbour entries written by the last rebuild */
+    int32_t nlist_capacity;  /* current neighbours-per-particle capacity */
+    int32_t status;          /* latched device status (snap_status value) */
+} snap_stats;
+
+typedef struct {
+    double e_pair, e_bond;   /* potential energies (FP64 sums, fixed order) */
+    double kinetic;          /* kinetic energy of v_{t-1/2} (sum of v^2/2) */
+    double virial;
+} snap_energy;
+
+/* Create a context; validates cfg and copies it (replica arrays included).
+ * Allocates device memory for n particles through cfg.alloc.  On error
+ * *out is NULL and nothing is allocated. */
+snap_status snap_init(snap_ctx **out, const snap_config *cfg);
+
+/* Interaction types.  sigma[ntypes]; eps_pair[ntypes*ntypes] (row-major, must
+ * be symmetric); rcut[ntypes*ntypes] pair cut-offs, or NULL for the WCA cut
+ * 2^(1/6) sigma_ij with sigma_ij = (sigma_i + sigma_j)/2.  The pair potential is
+ * the Lennard-Jones potential shifted to zero at the cut (the WCA potential
+ * for the default cut); it acts on every pair, bonded or not. */
+snap_status snap_set_types(snap_ctx *, int32_t ntypes, const double *sigma,
+                           const double *eps_pair, const double *rcut);
+
+/* Dynamic-bond capacity per type: valence[ntypes] in 0..SNAP_MAX_VALENCE
+ * (0 = not reactive).  The occupancy counter generalises the paper's unit
+ * valence flag (Sec. II.A, II.C). */
+snap_status snap_set_valence(snap_ctx *, const int32_t *valence);
+
+/* Bond type bt: SNAP_HARMONIC U = k/2 (r - r0)^2, or SNAP_FENE
+ * U = -k R0^2/2 ln(1 - (r/R0)^2) with r0_or_R0 = R0.  Dynamic bonds must be
+ * harmonic (Eq. 4); FENE is for static bonds. */
+snap_status snap_set_bond_params(snap_ctx *, int32_t bt, int32_t kind, double k,
+                                 double r0_or_R0);
+
+/* Static bonds: nb tag pairs (2*nb ints) of bond type bt; at most
+ * SNAP_MAX_STATIC per particle.  Never change during the run. */
+snap_status snap_add_static_bonds(snap_ctx *, int64_t nb, const int32_t *tag_pairs,
+                                  int32_t bt);
+
+/* Register a reaction between particle types type_a and type_b forming bonds
+ * of harmonic bond type bt when r_min <= r <= r_max, with per-sweep
+ * probabilities p_on0 and p_off (Eqs. 1-3; K = p_on0/p_off).  self_avoid must
+ * be 0 (intramolecular exclusion is not built).  Writes the reaction index to
+ * *index_out when non-NULL. */
+snap_status snap_add_reaction(snap_ctx *, int32_t type_a, int32_t type_b, int32_t bt,
+                              double r_min, double r_max, double p_on0, double p_off,
+                              int32_t self_avoid, int32_t *index_out);
+
+/* Per-replica rates of one reaction (batched sweeps over the bond energy). */
+snap_status snap_set_reaction_rates(snap_ctx *, int32_t reaction, int32_t replica,
+                                    double p_on0, double p_off);
+
+/* Initial state in tag order: pos3[n*3] (wrapped into the box on entry),
+ * vel3[n*3] half-step velocities v_{-1/2} (NULL: zero), type[n].  Clears the
+ * dynamic bonds and resets the step counter to 0. */
+snap_status snap_set_particles(snap_ctx *, const double *pos3, const double *vel3,
+                               const int32_t *type);
+
+/* Overwrite positions (tag order, wrapped on entry) and optionally velocities. */
+snap_status snap_set_positions(snap_ctx *, const double *pos3, const double *vel3);
+
+/* Replace the dynamic-bond set: nb bonds given as tag pairs and reaction
+ * indices; birth steps set to the current step.  Fails with SNAP_ERR_ARG if a
+ * particle would exceed SNAP_MAX_VALENCE. */
+snap_status snap_set_bonds(snap_ctx *, int64_t nb, const int32_t *tag_pairs,
+                           const int32_t *reaction);
+
+/* Advance nsteps MD steps (asynchronous on the stream except for the final
+ * status poll, which waits).  Captured as CUDA graphs after the first call. */
+snap_status snap_step(snap_ctx *, int64_t nsteps);
+
+/* Advance nsteps MD steps launched one kernel at a time with CUDA events
+ * between the phases, and write the average milliseconds per step of each
+ * phase to ms[SNAP_NPHASES]: [0] neighbour-list maintenance (all rebuild
+ * kernels, mostly early exits), [1] bond sweep, [2] force kernel, [3]
+ * integrator + step end.  Same results as snap_step; slower (no graphs). */
+#define SNAP_NPHASES 4
+snap_status snap_step_profiled(snap_ctx *, int64_t nsteps, double *ms);
+
+/* One bond sweep at the current positions with the current step counter as
+ * its Philox counter; positions and the step counter are unchanged. */
+snap_status snap_bond_update(snap_ctx *);
+
+/* Conservative forces at the current positions and topology (tag order,
+ * n*3 doubles; the FP32 values in SNAP_MIXED mode). */
+snap_status snap_get_forces(snap_ctx *, double *f3);
+
+/* Dynamic bonds ascending by (min tag, max tag): tag_pairs[2*cap] and
+ * reaction[cap] (nullable).  *n_out = number of bonds; SNAP_ERR_ARG if it
+ * exceeds cap (nothing written). */
+snap_status snap_get_bonds(snap_ctx *, int32_t *tag_pairs, int32_t *reaction, int64_t cap,
+                           int64_t *n_out);
+
+snap_status snap_get_positions(snap_ctx *, double *pos3);
+snap_status snap_get_velocities(snap_ctx *, double *vel3);
+snap_status snap_get_images(snap_ctx *, int32_t *img3);
+
+/* Neighbour list as tag pairs (i, j), i < j, each unordered pair once. */
+snap_status snap_get_neighbors(snap_ctx *, int32_t *tag_pairs, int64_t cap, int64_t *n_out);
+
+snap_status snap_get_stats(snap_ctx *, snap_stats *out);
+snap_status snap_get_energy(snap_ctx *, snap_energy *out);
+/* Bond lifetimes (in sweeps) of every bond broken so far; bins[nbins], last
+ * bin collects the tail. */
+snap_status snap_get_lifetime_hist(snap_ctx *, int64_t *bins, int32_t nbins);
+
+/* Checkpoint: positions, velocities, images, dynamic bonds with birth steps and
+ * the step counter.  Philox is counter-based, so a restored run continues
+ * bit-identically.  Call with buf NULL to query *len. */
+snap_status snap_get_state(snap_ctx *, void *buf, size_t *len);
+snap_status snap_set_state(snap_ctx *, const void *buf, size_t len);
+
+/* Wait for the stream and return the latched device status (then cleared). */
+snap_status snap_sync(snap_ctx *);
+const char *snap_last_error(const snap_ctx *);
+void snap_destroy(snap_ctx *);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

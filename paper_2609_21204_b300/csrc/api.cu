@@ -1,0 +1,1302 @@
+// Host runtime behind the C ABI of include/snap.h: context, device memory,
+// CUDA-graph capture of MD steps, error latching and tag-order I/O.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/snap.h"
+#include "snap_kernels.h"
+
+using namespace snap;
+
+namespace {
+
+constexpr int kGraphSteps = 20;     // steps captured per CUDA graph launch
+constexpr int kPollSteps = 2000;    // status poll interval inside snap_step
+
+struct RxHost {
+    int ta, tb, bt;
+    double rmin, rmax, pon, poff;
+};
+
+struct RepHost {
+    int64_t n, tag_off;
+    double L[3];
+    double kT;
+    uint64_t seed;
+    int nc[3];
+    int cell_off;
+};
+
+}  // namespace
+
+struct snap_ctx {
+    snap_config cfg{};
+    std::string err;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool fp64 = false;
+    int block = 256;
+    int64_t n = 0;
+    // model
+    int ntypes = 0;
+    double sigma[kMaxTypes]{}, eps[kMaxTypes * kMaxTypes]{}, rcut[kMaxTypes * kMaxTypes]{};
+    bool types_set = false;
+    int valence[kMaxTypes]{};
+    int bkind[kMaxBondTypes]{};
+    double bk[kMaxBondTypes]{}, br0[kMaxBondTypes]{};
+    bool bset[kMaxBondTypes]{};
+    std::vector<RxHost> rx;
+    std::vector<std::vector<double>> rep_pon, rep_poff;  // [reaction][replica]
+    std::vector<RepHost> reps;
+    std::vector<int32_t> sp_host, sbt_host;  // tag-indexed static slots
+    int64_t bonds_base = 0;                  // dynamic bonds set explicitly
+    // device
+    bool ready = false, particles_set = false;
+    int ncell_total = 0;
+    DevParams P{};
+    DevArrays A{}, B{};
+    RepDev *d_reps = nullptr;
+    int32_t *d_bsum = nullptr;
+    double *d_red = nullptr;
+    std::vector<void *> allocs;
+    // graphs
+    cudaGraphExec_t graph = nullptr;
+    bool graph_dirty = true;
+    int nbr_cap = 0;
+};
+
+namespace {
+
+snap_status fail(snap_ctx *c, snap_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CUDA_TRY(c, expr)                                                                       \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail((c), SNAP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void *dalloc(snap_ctx *c, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void *p = nullptr;
+    if (c->cfg.alloc) {
+        p = c->cfg.alloc(bytes, c->cfg.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->allocs.push_back(p);
+    return p;
+}
+
+void dfree(snap_ctx *c, void *p)
+{
+    if (!p) return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    if (c->cfg.free) c->cfg.free(p, c->cfg.alloc_user);
+    else cudaFree(p);
+}
+
+template <typename T> bool alloc_arr(snap_ctx *c, T *&p, size_t count)
+{
+    p = static_cast<T *>(dalloc(c, sizeof(T) * count));
+    return p != nullptr;
+}
+
+Launch launch(snap_ctx *c) { return Launch{c->stream, c->block}; }
+
+uint32_t morton3(uint32_t x, uint32_t y, uint32_t z)
+{
+    uint32_t m = 0;
+    for (int b = 0; b < 10; ++b)
+        m |= ((x >> b) & 1u) << (3 * b) | ((y >> b) & 1u) << (3 * b + 1) | ((z >> b) & 1u) << (3 * b + 2);
+    return m;
+}
+
+double pair_rc(const snap_ctx *c, int a, int b)
+{
+    const double rc = c->rcut[a * kMaxTypes + b];
+    if (rc > 0.0) return rc;
+    const double sig = 0.5 * (c->sigma[a] + c->sigma[b]);
+    return sig * std::pow(2.0, 1.0 / 6.0);
+}
+
+double reactive_cut(const snap_ctx *c, int a, int b)
+{
+    double m = 0.0;
+    for (const auto &r : c->rx)
+        if ((r.ta == a && r.tb == b) || (r.ta == b && r.tb == a)) m = std::max(m, r.rmax);
+    return m;
+}
+
+snap_status upload_reps(snap_ctx *c)
+{
+    std::vector<RepDev> h(c->reps.size());
+    for (size_t r = 0; r < c->reps.size(); ++r) {
+        const RepHost &R = c->reps[r];
+        RepDev &D = h[r];
+        std::memset(&D, 0, sizeof D);
+        for (int d = 0; d < 3; ++d) {
+            D.L[d] = R.L[d];
+            D.invL[d] = 1.0 / R.L[d];
+            D.halfL[d] = 0.5 * R.L[d];
+            D.nc[d] = R.nc[d];
+            D.w[d] = R.nc[d] > 0 ? R.L[d] / (double)R.nc[d] : R.L[d];
+            D.wf[d] = (float)D.w[d];
+        }
+        D.cell_off = R.cell_off;
+        D.tag_off = R.tag_off;
+        D.n = R.n;
+        D.kT = R.kT;
+        D.noise_c = std::sqrt(((2.0 * c->cfg.gamma) * R.kT) / c->cfg.dt);
+        D.key0 = (uint32_t)(R.seed & 0xFFFFFFFFull);
+        D.key1hi = (uint32_t)(((R.seed >> 32) & 0xFFFFull) << 16);
+        for (size_t a = 0; a < c->rx.size(); ++a) {
+            D.p_on0[a] = c->rep_pon[a][r];
+            D.p_off[a] = c->rep_poff[a][r];
+        }
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_reps, h.data(), sizeof(RepDev) * h.size(), cudaMemcpyHostToDevice,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNAP_OK;
+}
+
+void fill_params(snap_ctx *c)
+{
+    DevParams &P = c->P;
+    std::memset(&P, 0, sizeof P);
+    P.ntypes = c->ntypes;
+    P.nrx = (int)c->rx.size();
+    P.period = c->cfg.bond_period;
+    P.nhist = c->cfg.lifetime_bins;
+    for (int t = 0; t < kMaxTypes; ++t) P.valence[t] = c->valence[t];
+    const double skin = c->cfg.skin;
+    for (int a = 0; a < c->ntypes; ++a)
+        for (int b = 0; b < c->ntypes; ++b) {
+            const int k = a * kMaxTypes + b;
+            const double rc = pair_rc(c, a, b);
+            const double sig = 0.5 * (c->sigma[a] + c->sigma[b]);
+            const double e = c->eps[k];
+            const double rl = std::max(rc, reactive_cut(c, a, b)) + skin + 1e-4;
+            P.rc2d[k] = rc * rc;
+            P.rc2f[k] = (float)(rc * rc);
+            P.rl2f[k] = (float)(rl * rl);
+            P.sig2d[k] = sig * sig;
+            P.sig2f[k] = (float)(sig * sig);
+            P.eps24d[k] = 24.0 * e;
+            P.eps24f[k] = (float)(24.0 * e);
+            const double c2 = (sig * sig) / (rc * rc), c6 = c2 * c2 * c2;
+            P.shiftd[k] = 4.0 * e * (c6 * c6 - c6);
+            P.shiftf[k] = (float)P.shiftd[k];
+        }
+    for (int b = 0; b < kMaxBondTypes; ++b) {
+        P.bkind[b] = c->bkind[b];
+        P.bk[b] = c->bk[b];
+        P.br0[b] = c->br0[b];
+        P.bkf[b] = (float)c->bk[b];
+        P.br0f[b] = (float)c->br0[b];
+    }
+    for (size_t a = 0; a < c->rx.size(); ++a) {
+        P.rx_ta[a] = c->rx[a].ta;
+        P.rx_tb[a] = c->rx[a].tb;
+        P.rx_bt[a] = c->rx[a].bt;
+        P.rx_rmin2[a] = c->rx[a].rmin * c->rx[a].rmin;
+        P.rx_rmax2[a] = c->rx[a].rmax * c->rx[a].rmax;
+    }
+    P.dt = c->cfg.dt;
+    P.half_dt = 0.5 * c->cfg.dt;
+    P.gamma = c->cfg.gamma;
+    P.sqrt3 = std::sqrt(3.0);
+    const double dmax = 0.5 * skin - 1e-4;
+    P.disp2f = (float)(dmax * dmax);
+    P.nbr_cap = c->nbr_cap;
+    P.n = c->n;
+    P.nbr_stride = ((c->n + 31) / 32) * 32;
+    P.nrep = (int)c->reps.size();
+}
+
+// everything that depends on the model (cut-offs -> cell grids -> capacities)
+snap_status ensure_ready(snap_ctx *c)
+{
+    if (c->ready) return SNAP_OK;
+    if (!c->types_set) return fail(c, SNAP_ERR_STATE, "snap_set_types has not been called");
+    double rl_max = 0.0;
+    for (int a = 0; a < c->ntypes; ++a)
+        for (int b = 0; b < c->ntypes; ++b)
+            rl_max = std::max(rl_max, std::max(pair_rc(c, a, b), reactive_cut(c, a, b)));
+    const double cell_min = rl_max + c->cfg.skin + 2e-4;
+    int off = 0;
+    double dens_max = 0.0;
+    for (auto &R : c->reps) {
+        for (int d = 0; d < 3; ++d) {
+            R.nc[d] = (int)std::floor(R.L[d] / cell_min);
+            if (R.nc[d] < 3)
+                return fail(c, SNAP_ERR_ARG, "box edge shorter than three neighbour cells (3 x " +
+                                                 std::to_string(cell_min) + ")");
+            if (R.nc[d] > 511) return fail(c, SNAP_ERR_ARG, "more than 511 cells along an axis");
+        }
+        R.cell_off = off;
+        off += R.nc[0] * R.nc[1] * R.nc[2];
+        dens_max = std::max(dens_max, (double)R.n / (R.L[0] * R.L[1] * R.L[2]));
+    }
+    c->ncell_total = off;
+    // capacity: expected neighbours within the largest list cut-off, doubled, + margin
+    if (c->nbr_cap <= 0) {
+        const double rl = rl_max + c->cfg.skin + 1e-4;
+        const double expect = dens_max * 4.0 / 3.0 * M_PI * rl * rl * rl;
+        int cap = (int)std::ceil(expect * 2.0 + 16.0);
+        c->nbr_cap = (cap + 7) & ~7;
+    }
+    // cell tables
+    std::vector<int32_t> rank_of(off);
+    for (const auto &R : c->reps) {
+        const int nx = R.nc[0], ny = R.nc[1], nz = R.nc[2];
+        std::vector<std::pair<uint32_t, int>> codes;
+        codes.reserve((size_t)nx * ny * nz);
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) codes.emplace_back(morton3(x, y, z), (z * ny + y) * nx + x);
+        std::sort(codes.begin(), codes.end());
+        for (size_t k = 0; k < codes.size(); ++k) rank_of[R.cell_off + codes[k].second] = R.cell_off + (int)k;
+    }
+    DevArrays &A = c->A;
+    const int nb = (off + 4095) / 4096 + 1;
+    if (!alloc_arr(c, A.cell_count, off) || !alloc_arr(c, A.cell_start, off + 1) ||
+        !alloc_arr(c, A.cell_cursor, off) || !alloc_arr(c, A.rank_of, off) || !alloc_arr(c, c->d_bsum, nb + 1))
+        return fail(c, SNAP_ERR_OOM, "cell arrays");
+    CUDA_TRY(c, cudaMemsetAsync(A.cell_count, 0, sizeof(int32_t) * off, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(A.cell_cursor, 0, sizeof(int32_t) * off, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(A.rank_of, rank_of.data(), sizeof(int32_t) * off, cudaMemcpyHostToDevice,
+                                c->stream));
+    const int64_t stride = ((c->n + 31) / 32) * 32;
+    if (!alloc_arr(c, A.nbr, (size_t)stride * c->nbr_cap)) return fail(c, SNAP_ERR_OOM, "neighbour list");
+    fill_params(c);
+    snap_status s = upload_reps(c);
+    if (s != SNAP_OK) return s;
+    c->ready = true;
+    c->graph_dirty = true;
+    return SNAP_OK;
+}
+
+// ---- kernel sequences -------------------------------------------------
+void seq_rebuild(snap_ctx *c)
+{
+    const Launch L = launch(c);
+    launch_cell_key(c->P, c->A, L);
+    launch_cell_scan(c->A, c->d_bsum, c->ncell_total, L);
+    launch_scatter(c->P, c->A, L);
+    launch_cell_sort(c->A, c->ncell_total, L);
+    launch_gather(c->P, c->A, c->B, c->fp64, L);
+    launch_copyback(c->P, c->A, c->B, c->fp64, L);
+    launch_nlist(c->P, c->A, c->fp64, L);
+    launch_rebuild_done(c->A, L);
+}
+
+void seq_sweep(snap_ctx *c, bool forced)
+{
+    if (c->rx.empty()) return;
+    const Launch L = launch(c);
+    if (forced) launch_sweep_begin_forced(c->P, c->A, L);
+    else launch_sweep_begin(c->P, c->A, L);
+    for (int s = 0; s < (int)c->rx.size(); ++s) {
+        if (forced) launch_sweep_reaction_forced(c->P, c->A, s, L);
+        else launch_sweep_reaction(c->P, c->A, s, L);
+    }
+}
+
+void seq_step(snap_ctx *c)
+{
+    const Launch L = launch(c);
+    seq_rebuild(c);
+    seq_sweep(c, false);
+    launch_force(c->P, c->A, c->fp64, false, L);
+    launch_integrate(c->P, c->A, c->fp64, L);
+    launch_step_end(c->A, L);
+}
+
+snap_status build_graph(snap_ctx *c)
+{
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    for (int s = 0; s < kGraphSteps; ++s) seq_step(c);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return fail(c, SNAP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, SNAP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    c->graph_dirty = false;
+    return SNAP_OK;
+}
+
+snap_status read_status(snap_ctx *c, uint32_t &st)
+{
+    CUDA_TRY(c, cudaMemcpyAsync(&st, c->A.status, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNAP_OK;
+}
+
+snap_status clear_status(snap_ctx *c)
+{
+    CUDA_TRY(c, cudaMemsetAsync(c->A.status, 0, sizeof(uint32_t), c->stream));
+    return SNAP_OK;
+}
+
+snap_status set_need_rebuild(snap_ctx *c)
+{
+    const int32_t one = 1;
+    CUDA_TRY(c, cudaMemcpyAsync(c->A.need_rebuild, &one, sizeof one, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNAP_OK;
+}
+
+// Neighbour capacity exceeded: grow, force a rebuild, clear the status.  The
+// rebuild happens at the start of a step before any state changes, and every
+// kernel after it returns early while the status is set, so the step is
+// simply retried.
+snap_status grow_nlist(snap_ctx *c)
+{
+    int32_t need = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&need, c->A.nbr_need, sizeof need, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int cap = std::max(need + need / 4 + 8, c->nbr_cap + 8);
+    cap = (cap + 7) & ~7;
+    dfree(c, c->A.nbr);
+    const int64_t stride = ((c->n + 31) / 32) * 32;
+    if (!alloc_arr(c, c->A.nbr, (size_t)stride * cap)) return fail(c, SNAP_ERR_OOM, "neighbour list regrow");
+    c->nbr_cap = cap;
+    c->P.nbr_cap = cap;
+    c->graph_dirty = true;
+    snap_status s = clear_status(c);
+    if (s != SNAP_OK) return s;
+    return set_need_rebuild(c);
+}
+
+snap_status status_to_code(snap_ctx *c, uint32_t st)
+{
+    if (st == 0) return SNAP_OK;
+    if (st & kStNonfinite) return fail(c, SNAP_ERR_NONFINITE, "non-finite position");
+    if (st & kStFene) return fail(c, SNAP_ERR_FENE_OVERSTRETCH, "FENE bond stretched beyond R0");
+    if (st & kStOverflow) return fail(c, SNAP_ERR_NLIST_OVERFLOW, "neighbour list overflow");
+    return fail(c, SNAP_ERR_STATE, "unknown device status");
+}
+
+// run a non-graph sequence with overflow retry (rebuild + f)
+template <typename F> snap_status run_with_retry(snap_ctx *c, F f)
+{
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        f();
+        CUDA_TRY(c, cudaGetLastError());
+        uint32_t st = 0;
+        snap_status s = read_status(c, st);
+        if (s != SNAP_OK) return s;
+        if (st == kStOverflow) {
+            s = grow_nlist(c);
+            if (s != SNAP_OK) return s;
+            continue;
+        }
+        if (st) {
+            clear_status(c);
+            return status_to_code(c, st);
+        }
+        return SNAP_OK;
+    }
+    return fail(c, SNAP_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
+}
+
+snap_status check_ready(snap_ctx *c)
+{
+    if (!c) return SNAP_ERR_ARG;
+    snap_status s = ensure_ready(c);
+    if (s != SNAP_OK) return s;
+    if (!c->particles_set) return fail(c, SNAP_ERR_STATE, "snap_set_particles has not been called");
+    return SNAP_OK;
+}
+
+void wrap_host(double &x, int32_t &img, double L)
+{
+    const double k = std::floor(x / L);
+    x -= k * L;
+    img += (int32_t)k;
+    if (x >= L) { x -= L; img += 1; }
+    if (x < 0.0) { x += L; img -= 1; }
+    if (x >= L) x = 0.0;
+}
+
+int rep_of_tag(const snap_ctx *c, int64_t t)
+{
+    int lo = 0, hi = (int)c->reps.size() - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (c->reps[mid].tag_off <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// upload tag-ordered host data into the current memory order through staging
+template <typename T> snap_status upload_in(snap_ctx *c, T *dst, T *stage, const T *host, size_t count)
+{
+    CUDA_TRY(c, cudaMemcpyAsync(stage, host, sizeof(T) * count, cudaMemcpyHostToDevice, c->stream));
+    launch_in<T>(dst, stage, c->A.rtag, (long long)count, launch(c));
+    CUDA_TRY(c, cudaGetLastError());
+    return SNAP_OK;
+}
+
+template <typename T> snap_status download_out(snap_ctx *c, T *host, const T *src, T *stage, size_t count)
+{
+    launch_out<T>(stage, src, c->A.rtag, (long long)count, launch(c));
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(host, stage, sizeof(T) * count, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNAP_OK;
+}
+
+snap_status upload_static(snap_ctx *c)
+{
+    std::vector<int4> sp(c->n);
+    std::vector<int32_t> sbt(c->n);
+    for (int64_t t = 0; t < c->n; ++t) {
+        sp[t] = make_int4(c->sp_host[4 * t], c->sp_host[4 * t + 1], c->sp_host[4 * t + 2], c->sp_host[4 * t + 3]);
+        sbt[t] = c->sbt_host[t];
+    }
+    snap_status s = upload_in<int4>(c, c->A.sp, c->B.sp, sp.data(), c->n);
+    if (s != SNAP_OK) return s;
+    s = upload_in<int32_t>(c, c->A.sbt, c->B.sbt, sbt.data(), c->n);
+    if (s != SNAP_OK) return s;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNAP_OK;
+}
+
+snap_status positions_in(snap_ctx *c, const double *pos3, std::vector<int32_t> *img)
+{
+    std::vector<double> xs[3];
+    for (int d = 0; d < 3; ++d) xs[d].resize(c->n);
+    for (int64_t t = 0; t < c->n; ++t) {
+        const RepHost &R = c->reps[rep_of_tag(c, t)];
+        for (int d = 0; d < 3; ++d) {
+            double x = pos3[3 * t + d];
+            if (!std::isfinite(x)) return fail(c, SNAP_ERR_NONFINITE, "non-finite input position");
+            int32_t im = 0;
+            wrap_host(x, im, R.L[d]);
+            xs[d][t] = x;
+            if (img) (*img)[3 * t + d] = im;
+        }
+    }
+    double *dst[3] = {c->A.x, c->A.y, c->A.z};
+    double *stg[3] = {c->B.x, c->B.y, c->B.z};
+    for (int d = 0; d < 3; ++d) {
+        snap_status s = upload_in<double>(c, dst[d], stg[d], xs[d].data(), c->n);
+        if (s != SNAP_OK) return s;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNAP_OK;
+}
+
+snap_status velocities_in(snap_ctx *c, const double *vel3)
+{
+    std::vector<double> vs[3];
+    for (int d = 0; d < 3; ++d) vs[d].assign(c->n, 0.0);
+    if (vel3)
+        for (int64_t t = 0; t < c->n; ++t)
+            for (int d = 0; d < 3; ++d) vs[d][t] = vel3[3 * t + d];
+    double *dst[3] = {c->A.vx, c->A.vy, c->A.vz};
+    double *stg[3] = {c->B.vx, c->B.vy, c->B.vz};
+    for (int d = 0; d < 3; ++d) {
+        snap_status s = upload_in<double>(c, dst[d], stg[d], vs[d].data(), c->n);
+        if (s != SNAP_OK) return s;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNAP_OK;
+}
+
+struct BondRec {
+    int32_t a, b, rx, birth;
+};
+
+snap_status bonds_in(snap_ctx *c, const std::vector<BondRec> &bonds)
+{
+    std::vector<std::vector<BondRec>> per(c->n);
+    for (const auto &bd : bonds) {
+        per[bd.a].push_back(bd);
+        per[bd.b].push_back(BondRec{bd.b, bd.a, bd.rx, bd.birth});
+    }
+    std::vector<int4> dp(c->n), db(c->n);
+    std::vector<int32_t> drx(c->n), occ(c->n);
+    for (int64_t t = 0; t < c->n; ++t) {
+        auto &v = per[t];
+        if ((int)v.size() > kVmax) return fail(c, SNAP_ERR_ARG, "more than SNAP_MAX_VALENCE dynamic bonds on a particle");
+        std::sort(v.begin(), v.end(), [](const BondRec &x, const BondRec &y) { return x.b < y.b; });
+        int p[4] = {-1, -1, -1, -1}, bi[4] = {0, 0, 0, 0}, r[4] = {0, 0, 0, 0};
+        for (size_t s = 0; s < v.size(); ++s) {
+            if (s > 0 && v[s].b == v[s - 1].b) return fail(c, SNAP_ERR_ARG, "duplicate dynamic bond");
+            p[s] = v[s].b;
+            bi[s] = v[s].birth;
+            r[s] = v[s].rx;
+        }
+        dp[t] = make_int4(p[0], p[1], p[2], p[3]);
+        db[t] = make_int4(bi[0], bi[1], bi[2], bi[3]);
+        drx[t] = (r[0] & 0xFF) | ((r[1] & 0xFF) << 8) | ((r[2] & 0xFF) << 16) | ((r[3] & 0xFF) << 24);
+        occ[t] = (int32_t)v.size();
+    }
+    snap_status s;
+    if ((s = upload_in<int4>(c, c->A.dp, c->B.dp, dp.data(), c->n)) != SNAP_OK) return s;
+    if ((s = upload_in<int4>(c, c->A.dbirth, c->B.dbirth, db.data(), c->n)) != SNAP_OK) return s;
+    if ((s = upload_in<int32_t>(c, c->A.drx, c->B.drx, drx.data(), c->n)) != SNAP_OK) return s;
+    if ((s = upload_in<int32_t>(c, c->A.occ, c->B.occ, occ.data(), c->n)) != SNAP_OK) return s;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNAP_OK;
+}
+
+snap_status bonds_out(snap_ctx *c, std::vector<BondRec> &out)
+{
+    std::vector<int4> dp(c->n), db(c->n);
+    std::vector<int32_t> drx(c->n);
+    snap_status s;
+    if ((s = download_out<int4>(c, dp.data(), c->A.dp, c->B.dp, c->n)) != SNAP_OK) return s;
+    if ((s = download_out<int4>(c, db.data(), c->A.dbirth, c->B.dbirth, c->n)) != SNAP_OK) return s;
+    if ((s = download_out<int32_t>(c, drx.data(), c->A.drx, c->B.drx, c->n)) != SNAP_OK) return s;
+    out.clear();
+    for (int64_t t = 0; t < c->n; ++t) {
+        const int p[4] = {dp[t].x, dp[t].y, dp[t].z, dp[t].w};
+        const int b[4] = {db[t].x, db[t].y, db[t].z, db[t].w};
+        for (int k = 0; k < kVmax; ++k)
+            if (p[k] > t) out.push_back(BondRec{(int32_t)t, p[k], (drx[t] >> (8 * k)) & 0xFF, b[k]});
+    }
+    std::sort(out.begin(), out.end(),
+              [](const BondRec &x, const BondRec &y) { return x.a != y.a ? x.a < y.a : x.b < y.b; });
+    return SNAP_OK;
+}
+
+snap_status counters_out(snap_ctx *c, unsigned long long *h)
+{
+    CUDA_TRY(c, cudaMemcpyAsync(h, c->A.counters, sizeof(unsigned long long) * cNumCounters,
+                                cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNAP_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
+{
+    if (!out) return SNAP_ERR_ARG;
+    *out = nullptr;
+    if (!cfg) return SNAP_ERR_ARG;
+    if (cfg->n < 0 || cfg->n > (int64_t)INT32_MAX / 2) return SNAP_ERR_ARG;
+    if (!(cfg->dt > 0.0) || !(cfg->kT >= 0.0) || !(cfg->gamma >= 0.0) || !(cfg->skin > 0.0)) return SNAP_ERR_ARG;
+    if (cfg->precision != SNAP_FP64 && cfg->precision != SNAP_MIXED) return SNAP_ERR_ARG;
+    if (cfg->bond_period < 1) return SNAP_ERR_ARG;
+    if (cfg->block_size < 0 || cfg->block_size > 1024 || (cfg->block_size % 32) != 0) return SNAP_ERR_ARG;
+    if ((cfg->alloc == nullptr) != (cfg->free == nullptr)) return SNAP_ERR_ARG;
+    const int nrep = cfg->n_replicas > 1 ? cfg->n_replicas : 1;
+    if (cfg->n_replicas > 1 && !cfg->replica_n) return SNAP_ERR_ARG;
+    std::vector<RepHost> reps(nrep);
+    int64_t off = 0;
+    for (int r = 0; r < nrep; ++r) {
+        RepHost &R = reps[r];
+        R.n = cfg->n_replicas > 1 ? cfg->replica_n[r] : cfg->n;
+        if (R.n < 0) return SNAP_ERR_ARG;
+        R.tag_off = off;
+        off += R.n;
+        for (int d = 0; d < 3; ++d) {
+            R.L[d] = (cfg->n_replicas > 1 && cfg->replica_box) ? cfg->replica_box[3 * r + d] : cfg->box[d];
+            if (!(R.L[d] > 0.0) || !std::isfinite(R.L[d])) return SNAP_ERR_ARG;
+        }
+        R.kT = (cfg->n_replicas > 1 && cfg->replica_kT) ? cfg->replica_kT[r] : cfg->kT;
+        if (!(R.kT >= 0.0)) return SNAP_ERR_ARG;
+        R.seed = (cfg->n_replicas > 1 && cfg->replica_seed) ? cfg->replica_seed[r] : cfg->seed + (uint64_t)r;
+        R.nc[0] = R.nc[1] = R.nc[2] = 0;
+        R.cell_off = 0;
+    }
+    if (off != cfg->n) return SNAP_ERR_ARG;
+
+    snap_ctx *c = new snap_ctx();
+    c->cfg = *cfg;
+    c->cfg.replica_n = nullptr;
+    c->cfg.replica_box = nullptr;
+    c->cfg.replica_kT = nullptr;
+    c->cfg.replica_seed = nullptr;
+    if (c->cfg.lifetime_bins <= 0) c->cfg.lifetime_bins = 256;
+    c->reps = reps;
+    c->n = cfg->n;
+    c->fp64 = cfg->precision == SNAP_FP64;
+    c->block = cfg->block_size > 0 ? cfg->block_size : 256;
+    c->nbr_cap = cfg->nlist_capacity > 0 ? ((cfg->nlist_capacity + 7) & ~7) : 0;
+    c->sp_host.assign((size_t)c->n * 4, -1);
+    c->sbt_host.assign((size_t)c->n, 0);
+    for (int t = 0; t < kMaxTypes * kMaxTypes; ++t) c->eps[t] = 1.0;
+
+    auto bail = [&](snap_status s, const char *what) {
+        (void)what;
+        snap_destroy(c);
+        return s;
+    };
+    if (cfg->stream) {
+        c->stream = (cudaStream_t)cfg->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return SNAP_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    const size_t n = (size_t)std::max<int64_t>(c->n, 1);
+    const size_t v4 = c->fp64 ? sizeof(double4_32a) : sizeof(float4);
+    for (DevArrays *D : {&c->A, &c->B}) {
+        bool ok = alloc_arr(c, D->x, n) && alloc_arr(c, D->y, n) && alloc_arr(c, D->z, n) &&
+                  alloc_arr(c, D->vx, n) && alloc_arr(c, D->vy, n) && alloc_arr(c, D->vz, n) &&
+                  alloc_arr(c, D->ix, n) && alloc_arr(c, D->iy, n) && alloc_arr(c, D->iz, n) &&
+                  alloc_arr(c, D->type, n) && alloc_arr(c, D->tag, n) && alloc_arr(c, D->rep, n) &&
+                  alloc_arr(c, D->sp, n) && alloc_arr(c, D->sbt, n) && alloc_arr(c, D->dp, n) &&
+                  alloc_arr(c, D->drx, n) && alloc_arr(c, D->dbirth, n) && alloc_arr(c, D->occ, n);
+        D->pos4 = dalloc(c, v4 * n);
+        if (!ok || !D->pos4) return bail(SNAP_ERR_OOM, "particles");
+    }
+    DevArrays &A = c->A;
+    A.force = dalloc(c, v4 * n);
+    bool ok = A.force && alloc_arr(c, A.rtag, n) && alloc_arr(c, A.ref4, n) && alloc_arr(c, A.nn, n) &&
+              alloc_arr(c, A.cell_key, n) && alloc_arr(c, A.order, n) && alloc_arr(c, A.prop, n) &&
+              alloc_arr(c, A.prop_r, n) && alloc_arr(c, A.prio, n) && alloc_arr(c, A.best, n) &&
+              alloc_arr(c, A.fpart, n) && alloc_arr(c, A.brk, n) && alloc_arr(c, A.rx_order, (size_t)nrep * kMaxRx) &&
+              alloc_arr(c, A.step, 1) && alloc_arr(c, A.status, 1) && alloc_arr(c, A.need_rebuild, 1) &&
+              alloc_arr(c, A.nbr_need, 1) && alloc_arr(c, A.counters, cNumCounters) &&
+              alloc_arr(c, A.life_hist, (size_t)c->cfg.lifetime_bins) && alloc_arr(c, A.e_part, 4 * n) &&
+              alloc_arr(c, c->d_red, 8);
+    c->d_reps = static_cast<RepDev *>(dalloc(c, sizeof(RepDev) * nrep));
+    if (!ok || !c->d_reps) return bail(SNAP_ERR_OOM, "work arrays");
+    A.reps = c->d_reps;
+    // B shares the non-permuted arrays with A
+    DevArrays &B = c->B;
+    B.rtag = A.rtag; B.ref4 = A.ref4; B.force = A.force; B.status = A.status; B.need_rebuild = A.need_rebuild;
+    B.step = A.step; B.reps = A.reps; B.order = A.order;
+    if (cudaMemsetAsync(A.status, 0, 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.step, 0, 8, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.need_rebuild, 0, 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.nbr_need, 0, 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.counters, 0, sizeof(unsigned long long) * cNumCounters, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.life_hist, 0, sizeof(unsigned long long) * c->cfg.lifetime_bins, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(SNAP_ERR_CUDA, "init memset");
+    }
+    *out = c;
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_set_types(snap_ctx *c, int32_t ntypes, const double *sigma, const double *eps_pair,
+                                      const double *rcut)
+{
+    if (!c) return SNAP_ERR_ARG;
+    if (ntypes < 1 || ntypes > kMaxTypes || !sigma || !eps_pair) return fail(c, SNAP_ERR_ARG, "bad types");
+    for (int a = 0; a < ntypes; ++a) {
+        if (!(sigma[a] > 0.0)) return fail(c, SNAP_ERR_ARG, "sigma must be > 0");
+        for (int b = 0; b < ntypes; ++b) {
+            if (!(eps_pair[a * ntypes + b] >= 0.0) || eps_pair[a * ntypes + b] != eps_pair[b * ntypes + a])
+                return fail(c, SNAP_ERR_ARG, "eps_pair must be symmetric and >= 0");
+            if (rcut && (rcut[a * ntypes + b] != rcut[b * ntypes + a]))
+                return fail(c, SNAP_ERR_ARG, "rcut must be symmetric");
+        }
+    }
+    c->ntypes = ntypes;
+    for (int a = 0; a < ntypes; ++a) {
+        c->sigma[a] = sigma[a];
+        for (int b = 0; b < ntypes; ++b) {
+            c->eps[a * kMaxTypes + b] = eps_pair[a * ntypes + b];
+            c->rcut[a * kMaxTypes + b] = rcut ? rcut[a * ntypes + b] : 0.0;
+        }
+    }
+    c->types_set = true;
+    if (c->ready) return fail(c, SNAP_ERR_STATE, "types cannot change after the first step");
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_set_valence(snap_ctx *c, const int32_t *valence)
+{
+    if (!c || !valence) return SNAP_ERR_ARG;
+    if (!c->types_set) return fail(c, SNAP_ERR_STATE, "call snap_set_types first");
+    for (int a = 0; a < c->ntypes; ++a)
+        if (valence[a] < 0 || valence[a] > kVmax) return fail(c, SNAP_ERR_ARG, "valence out of range");
+    for (int a = 0; a < c->ntypes; ++a) c->valence[a] = valence[a];
+    if (c->ready) {
+        fill_params(c);
+        c->graph_dirty = true;
+    }
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_set_bond_params(snap_ctx *c, int32_t bt, int32_t kind, double k, double r0)
+{
+    if (!c) return SNAP_ERR_ARG;
+    if (bt < 0 || bt >= kMaxBondTypes) return fail(c, SNAP_ERR_ARG, "bond type out of range");
+    if (kind != SNAP_HARMONIC && kind != SNAP_FENE) return fail(c, SNAP_ERR_ARG, "unknown bond kind");
+    if (!(k >= 0.0) || !(r0 > 0.0) || !std::isfinite(k) || !std::isfinite(r0))
+        return fail(c, SNAP_ERR_ARG, "bond parameters must be finite, k >= 0, r0 > 0");
+    for (const auto &r : c->rx)
+        if (r.bt == bt && kind != SNAP_HARMONIC) return fail(c, SNAP_ERR_ARG, "reaction bond types must be harmonic");
+    c->bkind[bt] = kind;
+    c->bk[bt] = k;
+    c->br0[bt] = r0;
+    c->bset[bt] = true;
+    if (c->ready) {
+        fill_params(c);
+        c->graph_dirty = true;
+    }
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_add_static_bonds(snap_ctx *c, int64_t nb, const int32_t *pairs, int32_t bt)
+{
+    if (!c) return SNAP_ERR_ARG;
+    if (nb < 0 || (nb > 0 && !pairs)) return fail(c, SNAP_ERR_ARG, "bad bond list");
+    if (bt < 0 || bt >= kMaxBondTypes || !c->bset[bt]) return fail(c, SNAP_ERR_ARG, "bond type not set");
+    std::vector<int32_t> sp = c->sp_host, sbt = c->sbt_host;
+    for (int64_t q = 0; q < nb; ++q) {
+        const int32_t a = pairs[2 * q], b = pairs[2 * q + 1];
+        if (a < 0 || b < 0 || a >= c->n || b >= c->n || a == b) return fail(c, SNAP_ERR_ARG, "bond tag out of range");
+        if (rep_of_tag(c, a) != rep_of_tag(c, b)) return fail(c, SNAP_ERR_ARG, "bond across replicas");
+        for (int32_t u : {a, b}) {
+            const int32_t v = (u == a) ? b : a;
+            int s = 0;
+            while (s < kSmax && sp[4 * (size_t)u + s] >= 0) ++s;
+            if (s == kSmax) return fail(c, SNAP_ERR_ARG, "more than SNAP_MAX_STATIC static bonds on a particle");
+            sp[4 * (size_t)u + s] = v;
+            sbt[u] |= (bt & 0xFF) << (8 * s);
+        }
+    }
+    c->sp_host.swap(sp);
+    c->sbt_host.swap(sbt);
+    if (c->particles_set) return upload_static(c);
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_add_reaction(snap_ctx *c, int32_t ta, int32_t tb, int32_t bt, double rmin, double rmax,
+                                         double pon, double poff, int32_t self_avoid, int32_t *index_out)
+{
+    if (!c) return SNAP_ERR_ARG;
+    if (!c->types_set) return fail(c, SNAP_ERR_STATE, "call snap_set_types first");
+    if (c->ready) return fail(c, SNAP_ERR_STATE, "reactions must be registered before the first step");
+    if ((int)c->rx.size() >= kMaxRx) return fail(c, SNAP_ERR_ARG, "too many reactions");
+    if (ta < 0 || tb < 0 || ta >= c->ntypes || tb >= c->ntypes) return fail(c, SNAP_ERR_ARG, "reaction type out of range");
+    if (bt < 0 || bt >= kMaxBondTypes || !c->bset[bt] || c->bkind[bt] != SNAP_HARMONIC)
+        return fail(c, SNAP_ERR_ARG, "reaction bond type must be a harmonic bond type that has been set");
+    if (!(rmin >= 0.0) || !(rmax > rmin) || !std::isfinite(rmax)) return fail(c, SNAP_ERR_ARG, "bad formation window");
+    if (!(pon >= 0.0 && pon <= 1.0) || !(poff >= 0.0 && poff <= 1.0))
+        return fail(c, SNAP_ERR_ARG, "per-sweep probabilities must lie in [0, 1] (Eq. 2)");
+    if (self_avoid != 0) return fail(c, SNAP_ERR_ARG, "intramolecular exclusion is not supported");
+    c->rx.push_back(RxHost{ta, tb, bt, rmin, rmax, pon, poff});
+    c->rep_pon.push_back(std::vector<double>(c->reps.size(), pon));
+    c->rep_poff.push_back(std::vector<double>(c->reps.size(), poff));
+    if (index_out) *index_out = (int32_t)c->rx.size() - 1;
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_set_reaction_rates(snap_ctx *c, int32_t a, int32_t r, double pon, double poff)
+{
+    if (!c) return SNAP_ERR_ARG;
+    if (a < 0 || a >= (int)c->rx.size() || r < 0 || r >= (int)c->reps.size())
+        return fail(c, SNAP_ERR_ARG, "reaction or replica out of range");
+    if (!(pon >= 0.0 && pon <= 1.0) || !(poff >= 0.0 && poff <= 1.0))
+        return fail(c, SNAP_ERR_ARG, "per-sweep probabilities must lie in [0, 1] (Eq. 2)");
+    c->rep_pon[a][r] = pon;
+    c->rep_poff[a][r] = poff;
+    if (c->ready) return upload_reps(c);
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_set_particles(snap_ctx *c, const double *pos3, const double *vel3, const int32_t *type)
+{
+    if (!c) return SNAP_ERR_ARG;
+    if (c->n > 0 && (!pos3 || !type)) return fail(c, SNAP_ERR_ARG, "positions and types are required");
+    snap_status s = ensure_ready(c);
+    if (s != SNAP_OK) return s;
+    for (int64_t t = 0; t < c->n; ++t)
+        if (type[t] < 0 || type[t] >= c->ntypes) return fail(c, SNAP_ERR_ARG, "particle type out of range");
+    const Launch L = launch(c);
+    launch_iota(c->A.tag, c->n, L);
+    launch_iota(c->A.rtag, c->n, L);
+    CUDA_TRY(c, cudaGetLastError());
+    std::vector<int32_t> img((size_t)c->n * 3, 0), rep(c->n);
+    for (int64_t t = 0; t < c->n; ++t) rep[t] = rep_of_tag(c, t);
+    if ((s = positions_in(c, pos3, &img)) != SNAP_OK) return s;
+    if ((s = velocities_in(c, vel3)) != SNAP_OK) return s;
+    std::vector<int32_t> ic[3];
+    for (int d = 0; d < 3; ++d) {
+        ic[d].resize(c->n);
+        for (int64_t t = 0; t < c->n; ++t) ic[d][t] = img[3 * t + d];
+    }
+    int32_t *idst[3] = {c->A.ix, c->A.iy, c->A.iz};
+    int32_t *istg[3] = {c->B.ix, c->B.iy, c->B.iz};
+    for (int d = 0; d < 3; ++d)
+        if ((s = upload_in<int32_t>(c, idst[d], istg[d], ic[d].data(), c->n)) != SNAP_OK) return s;
+    if ((s = upload_in<int32_t>(c, c->A.type, c->B.type, type, c->n)) != SNAP_OK) return s;
+    if ((s = upload_in<int32_t>(c, c->A.rep, c->B.rep, rep.data(), c->n)) != SNAP_OK) return s;
+    if ((s = upload_static(c)) != SNAP_OK) return s;
+    if ((s = bonds_in(c, {})) != SNAP_OK) return s;
+    c->bonds_base = 0;
+    CUDA_TRY(c, cudaMemsetAsync(c->A.step, 0, 8, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->A.status, 0, 4, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->A.counters, 0, sizeof(unsigned long long) * cNumCounters, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->A.life_hist, 0, sizeof(unsigned long long) * c->cfg.lifetime_bins, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->A.force, 0, (c->fp64 ? sizeof(double4_32a) : sizeof(float4)) * c->n, c->stream));
+    c->particles_set = true;
+    return set_need_rebuild(c);
+}
+
+extern "C" snap_status snap_set_positions(snap_ctx *c, const double *pos3, const double *vel3)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (c->n > 0 && !pos3) return fail(c, SNAP_ERR_ARG, "positions are required");
+    std::vector<int32_t> img((size_t)c->n * 3, 0);
+    if ((s = positions_in(c, pos3, &img)) != SNAP_OK) return s;
+    if (vel3 && (s = velocities_in(c, vel3)) != SNAP_OK) return s;
+    std::vector<int32_t> ic(c->n);
+    int32_t *idst[3] = {c->A.ix, c->A.iy, c->A.iz};
+    int32_t *istg[3] = {c->B.ix, c->B.iy, c->B.iz};
+    for (int d = 0; d < 3; ++d) {
+        for (int64_t t = 0; t < c->n; ++t) ic[t] = img[3 * t + d];
+        if ((s = upload_in<int32_t>(c, idst[d], istg[d], ic.data(), c->n)) != SNAP_OK) return s;
+    }
+    return set_need_rebuild(c);
+}
+
+extern "C" snap_status snap_set_bonds(snap_ctx *c, int64_t nb, const int32_t *pairs, const int32_t *reaction)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (nb < 0 || (nb > 0 && !pairs)) return fail(c, SNAP_ERR_ARG, "bad bond list");
+    long long step = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&step, c->A.step, 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    std::vector<BondRec> bonds;
+    bonds.reserve(nb);
+    for (int64_t q = 0; q < nb; ++q) {
+        int32_t a = pairs[2 * q], b = pairs[2 * q + 1];
+        const int32_t r = reaction ? reaction[q] : 0;
+        if (a < 0 || b < 0 || a >= c->n || b >= c->n || a == b) return fail(c, SNAP_ERR_ARG, "bond tag out of range");
+        if (r < 0 || r >= (int)c->rx.size()) return fail(c, SNAP_ERR_ARG, "bond reaction out of range");
+        if (rep_of_tag(c, a) != rep_of_tag(c, b)) return fail(c, SNAP_ERR_ARG, "bond across replicas");
+        if (a > b) std::swap(a, b);
+        bonds.push_back(BondRec{a, b, r, (int32_t)(uint32_t)step});
+    }
+    if ((s = bonds_in(c, bonds)) != SNAP_OK) return s;
+    unsigned long long h[cNumCounters];
+    if ((s = counters_out(c, h)) != SNAP_OK) return s;
+    c->bonds_base = nb - (int64_t)h[cFormedTotal] + (int64_t)h[cBrokenTotal];
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_step(snap_ctx *c, int64_t nsteps)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (nsteps < 0) return fail(c, SNAP_ERR_ARG, "nsteps < 0");
+    long long step0 = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&step0, c->A.step, 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const long long target = step0 + nsteps;
+    long long cur = step0;
+    int retries = 0;
+    while (cur < target) {
+        long long todo = std::min<long long>(target - cur, kPollSteps);
+        long long ngraph = todo / kGraphSteps;
+        if (ngraph > 0 && c->graph_dirty) {
+            if ((s = build_graph(c)) != SNAP_OK) return s;
+        }
+        for (long long g = 0; g < ngraph; ++g) CUDA_TRY(c, cudaGraphLaunch(c->graph, c->stream));
+        for (long long r = ngraph * kGraphSteps; r < todo; ++r) seq_step(c);
+        CUDA_TRY(c, cudaGetLastError());
+        uint32_t st = 0;
+        if ((s = read_status(c, st)) != SNAP_OK) return s;
+        CUDA_TRY(c, cudaMemcpyAsync(&cur, c->A.step, 8, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if (st == kStOverflow) {
+            if (++retries > 16) return fail(c, SNAP_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
+            if ((s = grow_nlist(c)) != SNAP_OK) return s;
+            continue;
+        }
+        if (st) {
+            clear_status(c);
+            return status_to_code(c, st);
+        }
+    }
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_step_profiled(snap_ctx *c, int64_t nsteps, double *ms)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (nsteps < 0 || !ms) return fail(c, SNAP_ERR_ARG, "bad arguments");
+    for (int k = 0; k < SNAP_NPHASES; ++k) ms[k] = 0.0;
+    if (nsteps == 0) return SNAP_OK;
+    std::vector<cudaEvent_t> ev((size_t)nsteps * (SNAP_NPHASES + 1));
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto &x : ev)
+                if (x) cudaEventDestroy(x);
+            return fail(c, SNAP_ERR_CUDA, "event create");
+        }
+    const Launch L = launch(c);
+    for (int64_t t = 0; t < nsteps; ++t) {
+        cudaEvent_t *e = &ev[(size_t)t * (SNAP_NPHASES + 1)];
+        cudaEventRecord(e[0], c->stream);
+        seq_rebuild(c);
+        cudaEventRecord(e[1], c->stream);
+        seq_sweep(c, false);
+        cudaEventRecord(e[2], c->stream);
+        launch_force(c->P, c->A, c->fp64, false, L);
+        cudaEventRecord(e[3], c->stream);
+        launch_integrate(c->P, c->A, c->fp64, L);
+        launch_step_end(c->A, L);
+        cudaEventRecord(e[4], c->stream);
+    }
+    cudaError_t err = cudaStreamSynchronize(c->stream);
+    for (int64_t t = 0; t < nsteps && err == cudaSuccess; ++t)
+        for (int k = 0; k < SNAP_NPHASES; ++k) {
+            float x = 0.f;
+            err = cudaEventElapsedTime(&x, ev[(size_t)t * (SNAP_NPHASES + 1) + k],
+                                       ev[(size_t)t * (SNAP_NPHASES + 1) + k + 1]);
+            ms[k] += x;
+        }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (err != cudaSuccess) return fail(c, SNAP_ERR_CUDA, cudaGetErrorString(err));
+    for (int k = 0; k < SNAP_NPHASES; ++k) ms[k] /= (double)nsteps;
+    uint32_t st = 0;
+    if ((s = read_status(c, st)) != SNAP_OK) return s;
+    if (st) {
+        clear_status(c);
+        return status_to_code(c, st);
+    }
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_bond_update(snap_ctx *c)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    return run_with_retry(c, [&] {
+        seq_rebuild(c);
+        seq_sweep(c, true);
+    });
+}
+
+extern "C" snap_status snap_get_forces(snap_ctx *c, double *f3)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (c->n > 0 && !f3) return fail(c, SNAP_ERR_ARG, "f3 is NULL");
+    s = run_with_retry(c, [&] {
+        seq_rebuild(c);
+        launch_force(c->P, c->A, c->fp64, false, launch(c));
+    });
+    if (s != SNAP_OK) return s;
+    double *tmp = static_cast<double *>(dalloc(c, sizeof(double) * 3 * std::max<int64_t>(c->n, 1)));
+    if (!tmp) return fail(c, SNAP_ERR_OOM, "force staging");
+    launch_force_out(tmp, c->A.force, c->fp64, c->A.rtag, c->n, launch(c));
+    cudaError_t e = cudaMemcpyAsync(f3, tmp, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dfree(c, tmp);
+    if (e != cudaSuccess) return fail(c, SNAP_ERR_CUDA, cudaGetErrorString(e));
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_get_bonds(snap_ctx *c, int32_t *pairs, int32_t *reaction, int64_t cap, int64_t *n_out)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    std::vector<BondRec> b;
+    if ((s = bonds_out(c, b)) != SNAP_OK) return s;
+    if (n_out) *n_out = (int64_t)b.size();
+    if ((int64_t)b.size() > cap) return fail(c, SNAP_ERR_ARG, "bond buffer too small");
+    if (b.size() > 0 && !pairs) return fail(c, SNAP_ERR_ARG, "tag_pairs is NULL");
+    for (size_t q = 0; q < b.size(); ++q) {
+        pairs[2 * q] = b[q].a;
+        pairs[2 * q + 1] = b[q].b;
+        if (reaction) reaction[q] = b[q].rx;
+    }
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_get_positions(snap_ctx *c, double *pos3)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (c->n > 0 && !pos3) return fail(c, SNAP_ERR_ARG, "pos3 is NULL");
+    std::vector<double> v(c->n);
+    const double *src[3] = {c->A.x, c->A.y, c->A.z};
+    double *stg[3] = {c->B.x, c->B.y, c->B.z};
+    for (int d = 0; d < 3; ++d) {
+        if ((s = download_out<double>(c, v.data(), src[d], stg[d], c->n)) != SNAP_OK) return s;
+        for (int64_t t = 0; t < c->n; ++t) pos3[3 * t + d] = v[t];
+    }
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_get_velocities(snap_ctx *c, double *vel3)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (c->n > 0 && !vel3) return fail(c, SNAP_ERR_ARG, "vel3 is NULL");
+    std::vector<double> v(c->n);
+    const double *src[3] = {c->A.vx, c->A.vy, c->A.vz};
+    double *stg[3] = {c->B.vx, c->B.vy, c->B.vz};
+    for (int d = 0; d < 3; ++d) {
+        if ((s = download_out<double>(c, v.data(), src[d], stg[d], c->n)) != SNAP_OK) return s;
+        for (int64_t t = 0; t < c->n; ++t) vel3[3 * t + d] = v[t];
+    }
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_get_images(snap_ctx *c, int32_t *img3)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (c->n > 0 && !img3) return fail(c, SNAP_ERR_ARG, "img3 is NULL");
+    std::vector<int32_t> v(c->n);
+    const int32_t *src[3] = {c->A.ix, c->A.iy, c->A.iz};
+    int32_t *stg[3] = {c->B.ix, c->B.iy, c->B.iz};
+    for (int d = 0; d < 3; ++d) {
+        if ((s = download_out<int32_t>(c, v.data(), src[d], stg[d], c->n)) != SNAP_OK) return s;
+        for (int64_t t = 0; t < c->n; ++t) img3[3 * t + d] = v[t];
+    }
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_get_neighbors(snap_ctx *c, int32_t *pairs, int64_t cap, int64_t *n_out)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    s = run_with_retry(c, [&] { seq_rebuild(c); });
+    if (s != SNAP_OK) return s;
+    const int64_t stride = c->P.nbr_stride;
+    std::vector<int32_t> nbr((size_t)stride * c->nbr_cap), nn(c->n), tag(c->n);
+    CUDA_TRY(c, cudaMemcpyAsync(nbr.data(), c->A.nbr, sizeof(int32_t) * nbr.size(), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(nn.data(), c->A.nn, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(tag.data(), c->A.tag, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    std::vector<std::pair<int32_t, int32_t>> out;
+    for (int64_t i = 0; i < c->n; ++i)
+        for (int k = 0; k < nn[i]; ++k) {
+            const int32_t a = tag[i], b = tag[nbr[(size_t)k * stride + i]];
+            if (a < b) out.emplace_back(a, b);
+        }
+    std::sort(out.begin(), out.end());
+    if (n_out) *n_out = (int64_t)out.size();
+    if ((int64_t)out.size() > cap) return fail(c, SNAP_ERR_ARG, "pair buffer too small");
+    for (size_t q = 0; q < out.size(); ++q) {
+        pairs[2 * q] = out[q].first;
+        pairs[2 * q + 1] = out[q].second;
+    }
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_get_stats(snap_ctx *c, snap_stats *out)
+{
+    if (!c || !out) return SNAP_ERR_ARG;
+    std::memset(out, 0, sizeof *out);
+    if (!c->ready || !c->particles_set) return SNAP_OK;
+    unsigned long long h[cNumCounters];
+    snap_status s = counters_out(c, h);
+    if (s != SNAP_OK) return s;
+    long long step = 0;
+    uint32_t st = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&step, c->A.step, 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(&st, c->A.status, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    out->step = step;
+    out->formed_total = (int64_t)h[cFormedTotal];
+    out->broken_total = (int64_t)h[cBrokenTotal];
+    out->n_bonds = c->bonds_base + out->formed_total - out->broken_total;
+    out->sweeps = (int64_t)h[cSweeps];
+    out->scanned = (int64_t)h[cNlistScanned];
+    out->in_window = (int64_t)h[cInWindow];
+    out->proposals = (int64_t)h[cProposals];
+    out->edges = (int64_t)h[cEdges];
+    out->survivors = (int64_t)h[cSurvivors];
+    out->formed = (int64_t)h[cFormed];
+    out->break_tested = (int64_t)h[cBreakTested];
+    out->broken = (int64_t)h[cBroken];
+    out->nlist_builds = (int64_t)h[cBuilds];
+    out->nlist_entries = (int64_t)h[cNlistEntries];
+    out->nlist_capacity = c->nbr_cap;
+    out->status = (int32_t)status_to_code(c, st);
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_get_energy(snap_ctx *c, snap_energy *out)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (!out) return fail(c, SNAP_ERR_ARG, "out is NULL");
+    s = run_with_retry(c, [&] {
+        seq_rebuild(c);
+        launch_force(c->P, c->A, c->fp64, true, launch(c));
+        launch_reduce_cols(c->A.e_part, 4, c->n, c->d_red, launch(c));
+    });
+    if (s != SNAP_OK) return s;
+    double h[4];
+    CUDA_TRY(c, cudaMemcpyAsync(h, c->d_red, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    out->e_pair = h[0];
+    out->e_bond = h[1];
+    out->virial = h[2];
+    out->kinetic = h[3];
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_get_lifetime_hist(snap_ctx *c, int64_t *bins, int32_t nbins)
+{
+    if (!c || !bins || nbins <= 0) return SNAP_ERR_ARG;
+    std::vector<unsigned long long> h(c->cfg.lifetime_bins);
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->A.life_hist, sizeof(unsigned long long) * h.size(),
+                                cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < nbins; ++k) bins[k] = 0;
+    for (size_t k = 0; k < h.size(); ++k) bins[std::min<size_t>(k, nbins - 1)] += (int64_t)h[k];
+    return SNAP_OK;
+}
+
+namespace {
+constexpr uint64_t kStateMagic = 0x31706e73ull;  // "snp1"
+}
+
+extern "C" snap_status snap_get_state(snap_ctx *c, void *buf, size_t *len)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (!len) return fail(c, SNAP_ERR_ARG, "len is NULL");
+    std::vector<BondRec> b;
+    if ((s = bonds_out(c, b)) != SNAP_OK) return s;
+    const size_t n = (size_t)c->n;
+    const size_t need = 4 * sizeof(uint64_t) + n * (6 * sizeof(double) + 3 * sizeof(int32_t)) + b.size() * sizeof(BondRec);
+    if (!buf) {
+        *len = need;
+        return SNAP_OK;
+    }
+    if (*len < need) {
+        *len = need;
+        return fail(c, SNAP_ERR_ARG, "state buffer too small");
+    }
+    long long step = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&step, c->A.step, 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    char *p = static_cast<char *>(buf);
+    const uint64_t hdr[4] = {kStateMagic, (uint64_t)n, (uint64_t)step, (uint64_t)b.size()};
+    std::memcpy(p, hdr, sizeof hdr);
+    p += sizeof hdr;
+    std::vector<double> v3(3 * n);
+    if ((s = snap_get_positions(c, v3.data())) != SNAP_OK) return s;
+    std::memcpy(p, v3.data(), sizeof(double) * 3 * n);
+    p += sizeof(double) * 3 * n;
+    if ((s = snap_get_velocities(c, v3.data())) != SNAP_OK) return s;
+    std::memcpy(p, v3.data(), sizeof(double) * 3 * n);
+    p += sizeof(double) * 3 * n;
+    std::vector<int32_t> i3(3 * n);
+    if ((s = snap_get_images(c, i3.data())) != SNAP_OK) return s;
+    std::memcpy(p, i3.data(), sizeof(int32_t) * 3 * n);
+    p += sizeof(int32_t) * 3 * n;
+    if (!b.empty()) std::memcpy(p, b.data(), sizeof(BondRec) * b.size());
+    *len = need;
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_set_state(snap_ctx *c, const void *buf, size_t len)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (!buf || len < 4 * sizeof(uint64_t)) return fail(c, SNAP_ERR_ARG, "state buffer too small");
+    uint64_t hdr[4];
+    std::memcpy(hdr, buf, sizeof hdr);
+    const size_t n = (size_t)c->n;
+    if (hdr[0] != kStateMagic || hdr[1] != (uint64_t)n) return fail(c, SNAP_ERR_ARG, "state does not match this context");
+    const size_t need = 4 * sizeof(uint64_t) + n * (6 * sizeof(double) + 3 * sizeof(int32_t)) + hdr[3] * sizeof(BondRec);
+    if (len < need) return fail(c, SNAP_ERR_ARG, "state buffer truncated");
+    const char *p = static_cast<const char *>(buf) + sizeof hdr;
+    std::vector<double> pos(3 * n), vel(3 * n);
+    std::memcpy(pos.data(), p, sizeof(double) * 3 * n);
+    p += sizeof(double) * 3 * n;
+    std::memcpy(vel.data(), p, sizeof(double) * 3 * n);
+    p += sizeof(double) * 3 * n;
+    std::vector<int32_t> img(3 * n);
+    std::memcpy(img.data(), p, sizeof(int32_t) * 3 * n);
+    p += sizeof(int32_t) * 3 * n;
+    std::vector<BondRec> b(hdr[3]);
+    if (!b.empty()) std::memcpy(b.data(), p, sizeof(BondRec) * b.size());
+    // positions are already wrapped; upload them verbatim so the run continues bit-identically
+    double *dst[3] = {c->A.x, c->A.y, c->A.z};
+    double *stg[3] = {c->B.x, c->B.y, c->B.z};
+    double *vdst[3] = {c->A.vx, c->A.vy, c->A.vz};
+    double *vstg[3] = {c->B.vx, c->B.vy, c->B.vz};
+    int32_t *idst[3] = {c->A.ix, c->A.iy, c->A.iz};
+    int32_t *istg[3] = {c->B.ix, c->B.iy, c->B.iz};
+    std::vector<double> col(n);
+    std::vector<int32_t> icol(n);
+    for (int d = 0; d < 3; ++d) {
+        for (size_t t = 0; t < n; ++t) col[t] = pos[3 * t + d];
+        if ((s = upload_in<double>(c, dst[d], stg[d], col.data(), n)) != SNAP_OK) return s;
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        for (size_t t = 0; t < n; ++t) col[t] = vel[3 * t + d];
+        if ((s = upload_in<double>(c, vdst[d], vstg[d], col.data(), n)) != SNAP_OK) return s;
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        for (size_t t = 0; t < n; ++t) icol[t] = img[3 * t + d];
+        if ((s = upload_in<int32_t>(c, idst[d], istg[d], icol.data(), n)) != SNAP_OK) return s;
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    if ((s = bonds_in(c, b)) != SNAP_OK) return s;
+    const long long step = (long long)hdr[2];
+    CUDA_TRY(c, cudaMemcpyAsync(c->A.step, &step, 8, cudaMemcpyHostToDevice, c->stream));
+    unsigned long long h[cNumCounters];
+    if ((s = counters_out(c, h)) != SNAP_OK) return s;
+    c->bonds_base = (int64_t)b.size() - (int64_t)h[cFormedTotal] + (int64_t)h[cBrokenTotal];
+    return set_need_rebuild(c);
+}
+
+extern "C" snap_status snap_sync(snap_ctx *c)
+{
+    if (!c) return SNAP_ERR_ARG;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (!c->ready || !c->particles_set) return SNAP_OK;
+    uint32_t st = 0;
+    snap_status s = read_status(c, st);
+    if (s != SNAP_OK) return s;
+    if (st) clear_status(c);
+    return status_to_code(c, st);
+}
+
+extern "C" const char *snap_last_error(const snap_ctx *c)
+{
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+extern "C" void snap_destroy(snap_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    std::vector<void *> all = c->allocs;
+    for (void *p : all) dfree(c, p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}

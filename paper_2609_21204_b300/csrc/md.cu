@@ -1,0 +1,539 @@
+// Cell list, Morton-ordered particle sort, neighbour list, pair + bond forces.
+//
+// Layout: particles live in the order of the Morton rank of their cell
+// (cells of side >= the largest neighbour cut-off), so the 27 cells around a
+// particle are nearby in memory and neighbour gathers hit L1/L2.  Positions
+// used by the force loop are stored relative to the origin of the particle's
+// cell (frozen between rebuilds) with the cell coordinates and type packed in
+// the w word; a pair's separation is (rel_j - rel_i) + (c_j - c_i) * w, which
+// keeps FP32 separations accurate to ~1e-7 in any box size.
+//
+// Pair potential: Lennard-Jones shifted to zero at its cut (WCA for the
+// default cut 2^(1/6) sigma_ij); static bonds FENE or harmonic; dynamic bonds
+// harmonic (Eq. 4 of the DyBond-v2 paper names the harmonic form).  No pair
+// exclusions: the pair potential acts on bonded pairs too.
+#include "snap_kernels.h"
+
+namespace snap {
+
+namespace {
+
+__device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+
+__device__ __forceinline__ void cell_of(const RepDev &R, double x, double y, double z, int &cx, int &cy,
+                                        int &cz)
+{
+    cx = (int)(x * R.invL[0] * (double)R.nc[0]);
+    cy = (int)(y * R.invL[1] * (double)R.nc[1]);
+    cz = (int)(z * R.invL[2] * (double)R.nc[2]);
+    cx = min(max(cx, 0), R.nc[0] - 1);
+    cy = min(max(cy, 0), R.nc[1] - 1);
+    cz = min(max(cz, 0), R.nc[2] - 1);
+}
+
+__global__ void k_cell_key(DevParams P, DevArrays A)
+{
+    const long long i = gtid();
+    if (i >= P.n) return;
+    if (!status_ok(A.status) || !*A.need_rebuild) return;
+    const RepDev &R = A.reps[A.rep[i]];
+    int cx, cy, cz;
+    cell_of(R, A.x[i], A.y[i], A.z[i], cx, cy, cz);
+    const int lin = (cz * R.nc[1] + cy) * R.nc[0] + cx;
+    const int c = A.rank_of[R.cell_off + lin];
+    A.cell_key[i] = c;
+    atomicAdd(&A.cell_count[c], 1);
+    if (i == 0) A.counters[cNlistEntries] = 0ull;
+}
+
+// three-phase exclusive scan of cell_count into cell_start[0..ncell]
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int &total)
+{
+    constexpr int NW = kScanThreads / 32;
+    __shared__ int warp_sums[NW];
+    __shared__ int tot;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int w = lane < NW ? warp_sums[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < NW) warp_sums[lane] = wi - w;
+        if (lane == NW - 1) tot = wi;
+    }
+    __syncthreads();
+    const int res = incl - v + warp_sums[wid];
+    total = tot;
+    __syncthreads();
+    return res;
+}
+
+__global__ void k_scan_tiles(const int32_t *in, int32_t *out, int32_t *bsum, int n, const int32_t *gate,
+                             const uint32_t *status)
+{
+    if (!status_ok(status) || !*gate) return;
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        s += v[k];
+    }
+    int total;
+    int run = block_exclusive_scan(s, total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void k_scan_sums(int32_t *bsum, int nb, const int32_t *gate, const uint32_t *status)
+{
+    if (!status_ok(status) || !*gate) return;
+    // one block; nb <= kScanTile
+    const int base = threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < nb) ? bsum[base + k] : 0;
+        s += v[k];
+    }
+    int total;
+    int run = block_exclusive_scan(s, total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < nb) bsum[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) bsum[nb] = total;
+}
+
+__global__ void k_scan_add(int32_t *out, const int32_t *bsum, int n, int nb, const int32_t *gate,
+                           const uint32_t *status)
+{
+    if (!status_ok(status) || !*gate) return;
+    const long long k = gtid();
+    if (k < n) out[k] += bsum[k / kScanTile];
+    if (k == 0) out[n] = bsum[nb];
+}
+
+__global__ void k_scatter(DevParams P, DevArrays A)
+{
+    const long long i = gtid();
+    if (i >= P.n) return;
+    if (!status_ok(A.status) || !*A.need_rebuild) return;
+    const int c = A.cell_key[i];
+    const int pos = A.cell_start[c] + atomicAdd(&A.cell_cursor[c], 1);
+    A.order[pos] = (int32_t)i;
+}
+
+// deterministic order inside a cell: ascending tag (insertion sort, cells are small)
+__global__ void k_cell_sort(DevArrays A, int ncell)
+{
+    const long long c = gtid();
+    if (c >= ncell) return;
+    if (!status_ok(A.status) || !*A.need_rebuild) return;
+    const int s = A.cell_start[c], e = A.cell_start[c + 1];
+    for (int k = s + 1; k < e; ++k) {
+        const int v = A.order[k];
+        const int tv = A.tag[v];
+        int m = k - 1;
+        while (m >= s && A.tag[A.order[m]] > tv) {
+            A.order[m + 1] = A.order[m];
+            --m;
+        }
+        A.order[m + 1] = v;
+    }
+    A.cell_count[c] = 0;
+    A.cell_cursor[c] = 0;
+}
+
+template <typename R>
+__global__ void k_gather(DevParams P, DevArrays A, DevArrays B)
+{
+    using V = typename Vec4<R>::T;
+    const long long k = gtid();
+    if (k >= P.n) return;
+    if (!status_ok(A.status) || !*A.need_rebuild) return;
+    const int i = A.order[k];
+    const double x = A.x[i], y = A.y[i], z = A.z[i];
+    B.x[k] = x; B.y[k] = y; B.z[k] = z;
+    B.vx[k] = A.vx[i]; B.vy[k] = A.vy[i]; B.vz[k] = A.vz[i];
+    B.ix[k] = A.ix[i]; B.iy[k] = A.iy[i]; B.iz[k] = A.iz[i];
+    const int t = A.type[i];
+    B.type[k] = t;
+    const int tag = A.tag[i];
+    B.tag[k] = tag;
+    const int rp = A.rep[i];
+    B.rep[k] = rp;
+    B.sp[k] = A.sp[i]; B.sbt[k] = A.sbt[i];
+    B.dp[k] = A.dp[i]; B.drx[k] = A.drx[i]; B.dbirth[k] = A.dbirth[i];
+    B.occ[k] = A.occ[i];
+    A.rtag[tag] = (int32_t)k;
+    const RepDev &Rp = A.reps[rp];
+    int cx, cy, cz;
+    cell_of(Rp, x, y, z, cx, cy, cz);
+    const double rx = x - (double)cx * Rp.w[0];
+    const double ry = y - (double)cy * Rp.w[1];
+    const double rz = z - (double)cz * Rp.w[2];
+    V p;
+    p.x = (R)rx; p.y = (R)ry; p.z = (R)rz;
+    set_w_bits(p, pack_bits(t, cx, cy, cz));
+    reinterpret_cast<V *>(B.pos4)[k] = p;
+    A.ref4[k] = make_float4((float)rx, (float)ry, (float)rz, 0.f);
+}
+
+template <typename R>
+__global__ void k_copyback(DevParams P, DevArrays A, DevArrays B)
+{
+    using V = typename Vec4<R>::T;
+    const long long k = gtid();
+    if (k >= P.n) return;
+    if (!status_ok(A.status) || !*A.need_rebuild) return;
+    A.x[k] = B.x[k]; A.y[k] = B.y[k]; A.z[k] = B.z[k];
+    A.vx[k] = B.vx[k]; A.vy[k] = B.vy[k]; A.vz[k] = B.vz[k];
+    A.ix[k] = B.ix[k]; A.iy[k] = B.iy[k]; A.iz[k] = B.iz[k];
+    A.type[k] = B.type[k]; A.tag[k] = B.tag[k]; A.rep[k] = B.rep[k];
+    A.sp[k] = B.sp[k]; A.sbt[k] = B.sbt[k];
+    A.dp[k] = B.dp[k]; A.drx[k] = B.drx[k]; A.dbirth[k] = B.dbirth[k];
+    A.occ[k] = B.occ[k];
+    reinterpret_cast<V *>(A.pos4)[k] = reinterpret_cast<const V *>(B.pos4)[k];
+}
+
+// Full neighbour list: every j != i in the 27 cells around i with
+// r^2 < rl2(ti, tj); column-major storage nbr[slot * stride + i].
+template <typename R>
+__global__ void k_nlist(DevParams P, DevArrays A)
+{
+    using V = typename Vec4<R>::T;
+    const long long i = gtid();
+    if (i >= P.n) return;
+    if (!status_ok(A.status) || !*A.need_rebuild) return;
+    const V *pos = reinterpret_cast<const V *>(A.pos4);
+    const V p = pos[i];
+    const uint32_t b = w_bits(p);
+    const int ti = bits_type(b), cx = bits_cx(b), cy = bits_cy(b), cz = bits_cz(b);
+    const RepDev &Rp = A.reps[A.rep[i]];
+    const int nx = Rp.nc[0], ny = Rp.nc[1], nz = Rp.nc[2];
+    const float wx = Rp.wf[0], wy = Rp.wf[1], wz = Rp.wf[2];
+    const float pxf = (float)p.x, pyf = (float)p.y, pzf = (float)p.z;
+    const int cap = P.nbr_cap;
+    const long long stride = P.nbr_stride;
+    int cnt = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+        int zz = cz + dz;
+        zz += (zz < 0) ? nz : 0;
+        zz -= (zz >= nz) ? nz : 0;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int yy = cy + dy;
+            yy += (yy < 0) ? ny : 0;
+            yy -= (yy >= ny) ? ny : 0;
+            for (int dx = -1; dx <= 1; ++dx) {
+                int xx = cx + dx;
+                xx += (xx < 0) ? nx : 0;
+                xx -= (xx >= nx) ? nx : 0;
+                const int c = A.rank_of[Rp.cell_off + (zz * ny + yy) * nx + xx];
+                const int s = A.cell_start[c], e = A.cell_start[c + 1];
+                const float ox = dx * wx, oy = dy * wy, oz = dz * wz;
+                for (int j = s; j < e; ++j) {
+                    if (j == i) continue;
+                    const V q = pos[j];
+                    const int tj = bits_type(w_bits(q));
+                    const float ddx = ((float)q.x - pxf) + ox;
+                    const float ddy = ((float)q.y - pyf) + oy;
+                    const float ddz = ((float)q.z - pzf) + oz;
+                    const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    if (r2 < P.rl2f[ti * kMaxTypes + tj]) {
+                        if (cnt < cap) A.nbr[(long long)cnt * stride + i] = j;
+                        ++cnt;
+                    }
+                }
+            }
+        }
+    }
+    A.nn[i] = min(cnt, cap);
+    warp_count(&A.counters[cNlistEntries], (unsigned long long)min(cnt, cap));
+    if (cnt > cap) {
+        atomicOr(A.status, (uint32_t)kStOverflow);
+        atomicMax(A.nbr_need, cnt);
+    }
+}
+
+__global__ void k_rebuild_done(DevArrays A)
+{
+    if (!status_ok(A.status)) return;
+    if (*A.need_rebuild) {
+        *A.need_rebuild = 0;
+        A.counters[cBuilds] += 1ull;
+    }
+}
+
+// ------------------------------------------------------------ forces
+template <typename R> struct Num;
+template <> struct Num<float> {
+    __device__ static float rc2(const DevParams &P, int k) { return P.rc2f[k]; }
+    __device__ static float sig2(const DevParams &P, int k) { return P.sig2f[k]; }
+    __device__ static float eps24(const DevParams &P, int k) { return P.eps24f[k]; }
+    __device__ static float bk(const DevParams &P, int k) { return P.bkf[k]; }
+    __device__ static float br0(const DevParams &P, int k) { return P.br0f[k]; }
+    __device__ static float w(const RepDev &R, int d) { return R.wf[d]; }
+    __device__ static float sqrt_(float v) { return sqrtf(v); }
+};
+template <> struct Num<double> {
+    __device__ static double rc2(const DevParams &P, int k) { return P.rc2d[k]; }
+    __device__ static double sig2(const DevParams &P, int k) { return P.sig2d[k]; }
+    __device__ static double eps24(const DevParams &P, int k) { return P.eps24d[k]; }
+    __device__ static double bk(const DevParams &P, int k) { return P.bk[k]; }
+    __device__ static double br0(const DevParams &P, int k) { return P.br0[k]; }
+    __device__ static double w(const RepDev &R, int d) { return R.w[d]; }
+    __device__ static double sqrt_(double v) { return sqrt(v); }
+};
+
+// separation (j - i) of two particles from their relative coords and cells
+template <typename R, typename V>
+__device__ __forceinline__ void separation(const V &pi, const V &pj, const RepDev &Rp, R &dx, R &dy,
+                                           R &dz)
+{
+    const uint32_t bi = w_bits(pi), bj = w_bits(pj);
+    const int sx = cell_delta(bits_cx(bj) - bits_cx(bi), Rp.nc[0]);
+    const int sy = cell_delta(bits_cy(bj) - bits_cy(bi), Rp.nc[1]);
+    const int sz = cell_delta(bits_cz(bj) - bits_cz(bi), Rp.nc[2]);
+    dx = (pj.x - pi.x) + (R)sx * Num<R>::w(Rp, 0);
+    dy = (pj.y - pi.y) + (R)sy * Num<R>::w(Rp, 1);
+    dz = (pj.z - pi.z) + (R)sz * Num<R>::w(Rp, 2);
+}
+
+// bond force factor (dU/dr)/r; returns false on FENE overstretch
+template <typename R>
+__device__ __forceinline__ bool bond_factor(const DevParams &P, int bt, R r2, R &fb, double &u)
+{
+    const R k = Num<R>::bk(P, bt), r0 = Num<R>::br0(P, bt);
+    if (P.bkind[bt] == 0) {
+        const R r = Num<R>::sqrt_(r2);
+        fb = k * (r - r0) / r;
+        u = 0.5 * (double)k * ((double)r - (double)r0) * ((double)r - (double)r0);
+        return true;
+    }
+    const R q = r2 / (r0 * r0);
+    if (!(q < (R)1)) {
+        fb = 0;
+        u = 0.0;
+        return false;
+    }
+    fb = k / ((R)1 - q);
+    u = -0.5 * (double)k * (double)r0 * (double)r0 * log(1.0 - (double)q);
+    return true;
+}
+
+template <typename R, bool E>
+__global__ void __launch_bounds__(256) k_force(DevParams P, DevArrays A)
+{
+    using V = typename Vec4<R>::T;
+    const long long i = gtid();
+    if (i >= P.n) return;
+    if (!status_ok(A.status)) return;
+    const V *pos = reinterpret_cast<const V *>(A.pos4);
+    const V pi = pos[i];
+    const int ti = bits_type(w_bits(pi));
+    const RepDev &Rp = A.reps[A.rep[i]];
+    R fx = 0, fy = 0, fz = 0;
+    double ep = 0.0, eb = 0.0, vir = 0.0;
+    const int nn = A.nn[i];
+    const long long stride = P.nbr_stride;
+    const int *nb = A.nbr + i;
+    for (int k = 0; k < nn; ++k) {
+        const int j = __ldg(nb + (long long)k * stride);
+        const V pj = pos[j];
+        const int tj = bits_type(w_bits(pj));
+        R dx, dy, dz;
+        separation<R>(pi, pj, Rp, dx, dy, dz);
+        const R r2 = dx * dx + dy * dy + dz * dz;
+        const int tt = ti * kMaxTypes + tj;
+        if (r2 < Num<R>::rc2(P, tt)) {
+            const R ir2 = (R)1 / r2;
+            const R s2 = Num<R>::sig2(P, tt) * ir2;
+            const R s6 = s2 * s2 * s2;
+            const R fr = Num<R>::eps24(P, tt) * (s6 * ((R)2 * s6 - (R)1)) * ir2;
+            fx -= fr * dx;
+            fy -= fr * dy;
+            fz -= fr * dz;
+            if (E) {
+                const double s6d = (double)s6;
+                ep += 0.5 * ((double)P.eps24d[tt] / 6.0 * (s6d * s6d - s6d) - P.shiftd[tt]);
+                vir += 0.5 * (double)fr * (double)r2;
+            }
+        }
+    }
+    // static bonds
+    const int4 sp = A.sp[i];
+    const int sbt = A.sbt[i];
+    const int spv[4] = {sp.x, sp.y, sp.z, sp.w};
+    bool bad = false;
+#pragma unroll
+    for (int s = 0; s < kSmax; ++s) {
+        const int ptag = spv[s];
+        if (ptag < 0) continue;
+        const int j = A.rtag[ptag];
+        const V pj = pos[j];
+        R dx, dy, dz;
+        separation<R>(pi, pj, Rp, dx, dy, dz);
+        const R r2 = dx * dx + dy * dy + dz * dz;
+        R fb;
+        double u;
+        if (!bond_factor<R>(P, (sbt >> (8 * s)) & 0xFF, r2, fb, u)) bad = true;
+        fx += fb * dx;
+        fy += fb * dy;
+        fz += fb * dz;
+        if (E) { eb += 0.5 * u; vir -= 0.5 * (double)fb * (double)r2; }
+    }
+    // dynamic bonds
+    const int4 dp = A.dp[i];
+    const int drx = A.drx[i];
+    const int dpv[4] = {dp.x, dp.y, dp.z, dp.w};
+#pragma unroll
+    for (int s = 0; s < kVmax; ++s) {
+        const int ptag = dpv[s];
+        if (ptag < 0) continue;
+        const int j = A.rtag[ptag];
+        const V pj = pos[j];
+        R dx, dy, dz;
+        separation<R>(pi, pj, Rp, dx, dy, dz);
+        const R r2 = dx * dx + dy * dy + dz * dz;
+        R fb;
+        double u;
+        const int a = (drx >> (8 * s)) & 0xFF;
+        if (!bond_factor<R>(P, P.rx_bt[a], r2, fb, u)) bad = true;
+        fx += fb * dx;
+        fy += fb * dy;
+        fz += fb * dz;
+        if (E) { eb += 0.5 * u; vir -= 0.5 * (double)fb * (double)r2; }
+    }
+    if (bad) atomicOr(A.status, (uint32_t)kStFene);
+    V f;
+    f.x = fx; f.y = fy; f.z = fz; f.w = 0;
+    reinterpret_cast<V *>(A.force)[i] = f;
+    if (E) {
+        const double vx = A.vx[i], vy = A.vy[i], vz = A.vz[i];
+        A.e_part[4 * i + 0] = ep;
+        A.e_part[4 * i + 1] = eb;
+        A.e_part[4 * i + 2] = vir;
+        A.e_part[4 * i + 3] = 0.5 * (vx * vx + vy * vy + vz * vz);
+    }
+}
+
+// deterministic column sums: one block, fixed stride order, fixed tree
+__global__ void k_reduce_cols(const double *src, int ncol, long long n, double *out)
+{
+    __shared__ double sh[1024];
+    for (int c = 0; c < ncol; ++c) {
+        double s = 0.0;
+        for (long long r = threadIdx.x; r < n; r += blockDim.x) s += src[r * ncol + c];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[c] = sh[0];
+        __syncthreads();
+    }
+}
+
+inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace
+
+void launch_cell_key(const DevParams &P, const DevArrays &A, Launch L)
+{
+    if (P.n == 0) return;
+    k_cell_key<<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A);
+}
+
+void launch_cell_scan(const DevArrays &A, int32_t *block_sums, int ncell, Launch L)
+{
+    const int nb = (ncell + kScanTile - 1) / kScanTile;
+    k_scan_tiles<<<nb, kScanThreads, 0, L.stream>>>(A.cell_count, A.cell_start, block_sums, ncell,
+                                                     A.need_rebuild, A.status);
+    k_scan_sums<<<1, kScanThreads, 0, L.stream>>>(block_sums, nb, A.need_rebuild, A.status);
+    k_scan_add<<<grid_for(ncell, 256), 256, 0, L.stream>>>(A.cell_start, block_sums, ncell, nb,
+                                                           A.need_rebuild, A.status);
+}
+
+void launch_scatter(const DevParams &P, const DevArrays &A, Launch L)
+{
+    if (P.n == 0) return;
+    k_scatter<<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A);
+}
+
+void launch_cell_sort(const DevArrays &A, int ncell, Launch L)
+{
+    k_cell_sort<<<grid_for(ncell, 128), 128, 0, L.stream>>>(A, ncell);
+}
+
+void launch_gather(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, Launch L)
+{
+    if (P.n == 0) return;
+    if (fp64)
+        k_gather<double><<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A, B);
+    else
+        k_gather<float><<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A, B);
+}
+
+void launch_copyback(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, Launch L)
+{
+    if (P.n == 0) return;
+    if (fp64)
+        k_copyback<double><<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A, B);
+    else
+        k_copyback<float><<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A, B);
+}
+
+void launch_nlist(const DevParams &P, const DevArrays &A, bool fp64, Launch L)
+{
+    if (P.n == 0) return;
+    if (fp64)
+        k_nlist<double><<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A);
+    else
+        k_nlist<float><<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A);
+}
+
+void launch_rebuild_done(const DevArrays &A, Launch L) { k_rebuild_done<<<1, 1, 0, L.stream>>>(A); }
+
+void launch_force(const DevParams &P, const DevArrays &A, bool fp64, bool energy, Launch L)
+{
+    if (P.n == 0) return;
+    const unsigned g = grid_for(P.n, L.block);
+    if (fp64) {
+        if (energy) k_force<double, true><<<g, L.block, 0, L.stream>>>(P, A);
+        else k_force<double, false><<<g, L.block, 0, L.stream>>>(P, A);
+    } else {
+        if (energy) k_force<float, true><<<g, L.block, 0, L.stream>>>(P, A);
+        else k_force<float, false><<<g, L.block, 0, L.stream>>>(P, A);
+    }
+}
+
+void launch_reduce_cols(const double *src, int ncol, long long n, double *out, Launch L)
+{
+    k_reduce_cols<<<1, 1024, 0, L.stream>>>(src, ncol, n, out);
+}
+
+}  // namespace snap

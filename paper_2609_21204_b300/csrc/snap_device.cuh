@@ -1,0 +1,250 @@
+// Device-side definitions shared by the snap kernels (sm_103a).
+//
+// Counter-based randomness (Philox-4x32-10, Salmon et al. SC'11) and the
+// exponential of the acceptance factor are implemented here from their
+// published definitions so that every stochastic decision of the bond sweep
+// is a pure function of (seed, reaction, stream, step, tag pair), as Sec. II.E
+// of the DyBond-v2 paper requires.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace snap {
+
+constexpr int kMaxTypes = 8;
+constexpr int kMaxBondTypes = 8;
+constexpr int kMaxRx = 8;
+constexpr int kVmax = 4;   // dynamic-bond slots per particle
+constexpr int kSmax = 4;   // static-bond slots per particle
+
+// Philox key streams: key word 1 = ((seed >> 32) & 0xFFFF) << 16 | reaction << 8 | stream
+enum Stream : uint32_t { kForm = 1, kBreak = 2, kMatch = 3, kOrder = 4, kLangevin = 5 };
+
+// status bits latched by kernels (mapped to snap_status on the host)
+enum StatusBit : uint32_t {
+    kStOverflow = 1u << 0,
+    kStFene = 1u << 1,
+    kStNonfinite = 1u << 2,
+};
+
+// ------------------------------------------------------------ parameters
+// Passed by value to every kernel (kernel-parameter space, broadcast reads).
+struct DevParams {
+    int32_t ntypes, nrx, period, nhist;
+    int32_t valence[kMaxTypes];
+    // pair tables, index ti*kMaxTypes+tj
+    float rc2f[kMaxTypes * kMaxTypes];      // pair cut-off squared
+    float rl2f[kMaxTypes * kMaxTypes];      // neighbour-list build cut-off squared
+    float sig2f[kMaxTypes * kMaxTypes], eps24f[kMaxTypes * kMaxTypes], shiftf[kMaxTypes * kMaxTypes];
+    double rc2d[kMaxTypes * kMaxTypes];
+    double sig2d[kMaxTypes * kMaxTypes], eps24d[kMaxTypes * kMaxTypes], shiftd[kMaxTypes * kMaxTypes];
+    // bond types
+    int32_t bkind[kMaxBondTypes];
+    double bk[kMaxBondTypes], br0[kMaxBondTypes];
+    float bkf[kMaxBondTypes], br0f[kMaxBondTypes];
+    // reactions
+    int32_t rx_ta[kMaxRx], rx_tb[kMaxRx], rx_bt[kMaxRx];
+    double rx_rmin2[kMaxRx], rx_rmax2[kMaxRx];
+    // integrator
+    double dt, half_dt, gamma, sqrt3;
+    float disp2f;           // squared displacement that triggers a rebuild
+    int32_t nbr_cap;        // neighbours per particle
+    int64_t n;              // particles (all replicas)
+    int64_t nbr_stride;     // column stride of the neighbour list
+    int32_t nrep;
+};
+
+struct RepDev {
+    double L[3], invL[3], halfL[3], w[3];
+    float wf[3];
+    int32_t nc[3];
+    int32_t cell_off;       // first global cell id of this replica
+    int32_t pad0;
+    int64_t tag_off, n;
+    double kT, noise_c;     // set-point kT and sqrt(2 gamma kT / dt)
+    uint32_t key0, key1hi;  // Philox key words derived from the seed
+    double p_on0[kMaxRx], p_off[kMaxRx];
+};
+
+// Device arrays (sorted particle order unless stated).
+struct DevArrays {
+    double *x, *y, *z, *vx, *vy, *vz;
+    int32_t *ix, *iy, *iz;          // image counters
+    int32_t *type, *tag, *rtag, *rep;
+    void *pos4;                     // float4 or double4_32a: coords relative to frozen cell origin, w = bits
+    float4 *ref4;                   // rel coords at the last rebuild (displacement test)
+    void *force;                    // float4 or double4_32a (w unused)
+    int4 *sp;                       // static partner tags (-1 empty), kSmax per particle
+    int32_t *sbt;                   // static bond types, 8 bits each, packed
+    int4 *dp;                       // dynamic partner tags, ascending, -1 last
+    int32_t *drx;                   // reaction index per dynamic slot, 8 bits each, packed
+    int4 *dbirth;                   // step (low 32 bits) at which each dynamic bond formed
+    int32_t *occ;                   // dynamic bonds held
+    int32_t *nbr, *nn;              // neighbour list (column-major) and counts
+    // cell list
+    int32_t *cell_count, *cell_start, *cell_cursor, *cell_key, *order, *rank_of;
+    // sweep scratch
+    int32_t *prop;                  // proposed partner index or -1
+    double *prop_r;
+    uint32_t *prio;
+    unsigned long long *best;
+    int32_t *fpart;                 // formed partner index or -1
+    uint32_t *brk;                  // bit s set: dynamic slot s breaks
+    int32_t *rx_order;              // processing order of the reactions this sweep
+    // bookkeeping
+    long long *step;                // device step counter
+    uint32_t *status;
+    int32_t *need_rebuild;
+    int32_t *nbr_need;              // largest neighbour count seen (overflow sizing)
+    unsigned long long *counters;   // sweep counters, see Counter
+    unsigned long long *life_hist;
+    double *e_part;                 // per-particle energy scratch
+    const RepDev *reps;
+};
+
+enum Counter {
+    cScanned = 0, cInWindow, cProposals, cEdges, cSurvivors, cFormed, cBreakTested, cBroken,
+    cSweeps, cFormedTotal, cBrokenTotal, cBuilds, cNlistScanned, cNlistEntries, cNumCounters
+};
+
+// ------------------------------------------------------------ Philox-4x32-10
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a = c.x, b = c.z;
+        const uint32_t lo0 = 0xD2511F53u * a, hi0 = __umulhi(0xD2511F53u, a);
+        const uint32_t lo1 = 0xCD9E8D57u * b, hi1 = __umulhi(0xCD9E8D57u, b);
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t rx_key1(const RepDev &R, int a, uint32_t stream)
+{
+    return R.key1hi | ((uint32_t)(a & 0xFF) << 8) | stream;
+}
+
+// draw for the unordered pair of local tags lo < hi
+__device__ __forceinline__ U4 pair_draw(const RepDev &R, int a, uint32_t stream, long long step,
+                                        uint32_t lo, uint32_t hi)
+{
+    U4 c{(uint32_t)((unsigned long long)step & 0xFFFFFFFFull),
+         (uint32_t)((unsigned long long)step >> 32), lo, hi};
+    return philox10(c, R.key0, rx_key1(R, a, stream));
+}
+
+// 53-bit uniform in [0,1): (w0 << 21 | w1 >> 11) * 2^-53, exact in FP64
+__device__ __forceinline__ double u53(uint32_t w0, uint32_t w1)
+{
+    const unsigned long long m = ((unsigned long long)w0 << 21) | (unsigned long long)(w1 >> 11);
+    return __dmul_rn((double)m, 0x1.0p-53);
+}
+
+// ------------------------------------------------------------ exp
+// exp(x) = 2^k e^r with k = rint(x log2 e), r reduced by two fused steps
+// against ln2 split as (nearest double, remainder) — the Cody–Waite reduction
+// (Cody & Waite 1980) — and e^r summed as its Taylor series through r^13 in
+// Horner form with fused multiply-adds.  2^k is applied as two exact powers of
+// two.  Written from the mathematics; every operation is correctly rounded
+// IEEE arithmetic, so the result is reproducible on any IEEE platform.
+__device__ __forceinline__ double pow2_exact(int n)
+{
+    return __longlong_as_double((long long)(n + 1023) << 52);
+}
+
+__device__ __forceinline__ double exp_cw(double x)
+{
+    if (x != x) return x;
+    if (x > 709.7) return __longlong_as_double(0x7FF0000000000000ll);
+    if (x < -745.2) return 0.0;
+    const double log2e = 0x1.71547652b82fep+0;
+    const double ln2_a = 0x1.62e42fefa39efp-1;
+    const double ln2_b = 0x1.abc9e3b39803fp-56;
+    const double k = rint(__dmul_rn(x, log2e));
+    double r = fma(-k, ln2_a, x);
+    r = fma(-k, ln2_b, r);
+    // Taylor coefficients 1/m!, m = 13 .. 0
+    double s = 1.0 / 6227020800.0;
+    s = fma(s, r, 1.0 / 479001600.0);
+    s = fma(s, r, 1.0 / 39916800.0);
+    s = fma(s, r, 1.0 / 3628800.0);
+    s = fma(s, r, 1.0 / 362880.0);
+    s = fma(s, r, 1.0 / 40320.0);
+    s = fma(s, r, 1.0 / 5040.0);
+    s = fma(s, r, 1.0 / 720.0);
+    s = fma(s, r, 1.0 / 120.0);
+    s = fma(s, r, 1.0 / 24.0);
+    s = fma(s, r, 1.0 / 6.0);
+    s = fma(s, r, 0.5);
+    s = fma(s, r, 1.0);
+    s = fma(s, r, 1.0);
+    const int ki = (int)k;
+    const int h = ki / 2;
+    return __dmul_rn(__dmul_rn(s, pow2_exact(h)), pow2_exact(ki - h));
+}
+
+// ------------------------------------------------------------ geometry
+// cell coordinates and type packed in the w word of pos4:
+// bits 0-3 type, 4-12 cx, 13-21 cy, 22-30 cz
+__device__ __forceinline__ uint32_t pack_bits(int t, int cx, int cy, int cz)
+{
+    return (uint32_t)t | ((uint32_t)cx << 4) | ((uint32_t)cy << 13) | ((uint32_t)cz << 22);
+}
+__device__ __forceinline__ int bits_type(uint32_t b) { return (int)(b & 0xF); }
+__device__ __forceinline__ int bits_cx(uint32_t b) { return (int)((b >> 4) & 0x1FF); }
+__device__ __forceinline__ int bits_cy(uint32_t b) { return (int)((b >> 13) & 0x1FF); }
+__device__ __forceinline__ int bits_cz(uint32_t b) { return (int)((b >> 22) & 0x1FF); }
+
+// minimum-image cell offset (cells frozen between rebuilds)
+__device__ __forceinline__ int cell_delta(int d, int nc)
+{
+    const int h = nc >> 1;
+    if (d > h) d -= nc;
+    else if (d < -h) d += nc;
+    return d;
+}
+
+// FP64 minimum image exactly as: k = rint(d * invL); d - L * k (no contraction)
+__device__ __forceinline__ double min_image(double d, double L, double invL)
+{
+    const double k = rint(__dmul_rn(d, invL));
+    return __dsub_rn(d, __dmul_rn(L, k));
+}
+
+template <typename R> struct Vec4;
+template <> struct Vec4<float> { using T = float4; };
+template <> struct Vec4<double> { using T = double4_32a; };
+
+__device__ __forceinline__ uint32_t w_bits(const float4 &p) { return __float_as_uint(p.w); }
+__device__ __forceinline__ uint32_t w_bits(const double4_32a &p)
+{
+    return (uint32_t)__double_as_longlong(p.w);
+}
+__device__ __forceinline__ void set_w_bits(float4 &p, uint32_t b) { p.w = __uint_as_float(b); }
+__device__ __forceinline__ void set_w_bits(double4_32a &p, uint32_t b)
+{
+    p.w = __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ bool status_ok(const uint32_t *st) { return *(volatile const uint32_t *)st == 0u; }
+
+// warp-aggregated 64-bit counter increment (one atomic per full warp)
+__device__ __forceinline__ void warp_count(unsigned long long *ctr, unsigned long long v)
+{
+    const unsigned mask = __activemask();
+    if (mask == 0xFFFFFFFFu) {
+        unsigned long long s = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, s);
+    } else if (v) {
+        atomicAdd(ctr, v);
+    }
+}
+
+}  // namespace snap

@@ -1,0 +1,43 @@
+// Kernel launchers (host side) of the snap library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "snap_device.cuh"
+
+namespace snap {
+
+struct Launch {
+    cudaStream_t stream;
+    int block;       // threads per block for particle-parallel kernels
+};
+
+// ---- neighbour-list maintenance (all early-exit unless *need_rebuild) ----
+void launch_cell_key(const DevParams &P, const DevArrays &A, Launch L);
+void launch_cell_scan(const DevArrays &A, int32_t *block_sums, int ncell, Launch L);
+void launch_scatter(const DevParams &P, const DevArrays &A, Launch L);
+void launch_cell_sort(const DevArrays &A, int ncell, Launch L);
+void launch_gather(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, Launch L);
+void launch_copyback(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, Launch L);
+void launch_nlist(const DevParams &P, const DevArrays &A, bool fp64, Launch L);
+void launch_rebuild_done(const DevArrays &A, Launch L);
+
+// ---- bond sweep (Sec. II.C), exact FP64 decisions ----
+void launch_sweep_begin(const DevParams &P, const DevArrays &A, Launch L);
+void launch_sweep_reaction(const DevParams &P, const DevArrays &A, int slot, Launch L);
+// forced: run even when step % period != 0 (snap_bond_update)
+void launch_sweep_begin_forced(const DevParams &P, const DevArrays &A, Launch L);
+void launch_sweep_reaction_forced(const DevParams &P, const DevArrays &A, int slot, Launch L);
+
+// ---- forces and integration ----
+void launch_force(const DevParams &P, const DevArrays &A, bool fp64, bool energy, Launch L);
+void launch_integrate(const DevParams &P, const DevArrays &A, bool fp64, Launch L);
+void launch_step_end(const DevArrays &A, Launch L);
+void launch_reduce_cols(const double *src, int ncol, long long n, double *out, Launch L);
+
+// ---- tag-order I/O: dst[rtag[t]] = src[t] (in), dst[t] = src[rtag[t]] (out) ----
+template <typename T> void launch_in(T *dst_sorted, const T *src_tag, const int32_t *rtag, long long n, Launch L);
+template <typename T> void launch_out(T *dst_tag, const T *src_sorted, const int32_t *rtag, long long n, Launch L);
+void launch_force_out(double *dst3, const void *force, bool fp64, const int32_t *rtag, long long n, Launch L);
+void launch_iota(int32_t *dst, long long n, Launch L);
+
+}  // namespace snap

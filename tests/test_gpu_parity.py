@@ -1,0 +1,280 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+- A bond sweep on identical positions is bit-exact: same bond table, same
+  counters (Sec. II.C; Philox draws keyed as in Sec. II.E).
+- The neighbour list contains every pair inside max(pair cut, reactive cut).
+- Forces: normwise relative error <= 1e-12 (FP64) / 1e-5 (mixed FP32 forces).
+- FP64 trajectories follow the oracle step for step.
+"""
+import math
+import struct
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import (random_frozen, colloid_linker, telechelic, assoc_ab, frozen_pairs)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def snapmod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_21204_b300 import build
+    build.build()
+    import paper_2609_21204_b300 as m
+    return m
+
+
+def make_pair(snapmod, sysdef, precision="mixed", p_on0=1.0, **kw):
+    sim = snapmod.from_system(sysdef, precision=precision, p_on0=p_on0, **kw)
+    orc = oracle.OracleSystem(sysdef, p_on0=p_on0)
+    return sim, orc
+
+
+def set_step(sim, step):
+    st = bytearray(sim.get_state())
+    struct.pack_into("<Q", st, 16, step)
+    sim.set_state(bytes(st))
+
+
+def _sweep_cases():
+    return {
+        "ab_v1": lambda: random_frozen(seed=1, n=2000, box=12.0, overlap_factor=0.6, r_max=1.4),
+        "ab_v3_2": lambda: random_frozen(seed=2, n=5000, box=16.0, overlap_factor=0.6, r_max=1.5,
+                                         valence=(3, 2), r_min=0.4),
+        "colloid_linker": lambda: colloid_linker(seed=3, n_c=2000, n_l=8000, eps=3.0),
+        "telechelic": lambda: telechelic(seed=4, n_chains=200, n_x=400),
+        "tiny_ragged": lambda: random_frozen(seed=5, n=37, box=5.3, overlap_factor=0.5, r_max=1.4),
+        "kT0": lambda: _kt0(),
+    }
+
+
+def _kt0():
+    s = random_frozen(seed=6, n=1500, box=11.0, overlap_factor=0.6, r_max=1.4)
+    s.kT = 0.0
+    return s
+
+
+SWEEP_STATS = ("in_window", "proposals", "edges", "survivors", "formed", "break_tested", "broken")
+
+
+@pytest.mark.parametrize("name", list(_sweep_cases()))
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_sweep_bit_exact(snapmod, name, precision):
+    s = _sweep_cases()[name]()
+    sim, orc = make_pair(snapmod, s, precision, p_on0=0.9)
+    assert sim.bonds().shape[0] == 0
+    for step in (0, 1, 7, 1000, 123456789012):
+        set_step(sim, step)
+        sim.bond_update()
+        st_o = orc.sweep(step=step)
+        b_g, b_o = sim.bonds(), orc.bonds()
+        assert np.array_equal(b_g, b_o), (name, step, b_g.shape, b_o.shape)
+        st_g = sim.stats()
+        for k in SWEEP_STATS:
+            assert st_g[k] == st_o[k], (name, step, k, st_g[k], st_o[k])
+    # occupancies never exceed valence
+    val = np.asarray(s.valence)[s.types]
+    occ = np.bincount(b_g[:, :2].ravel(), minlength=s.n)
+    assert np.all(occ <= val)
+
+
+def test_sweep_with_preexisting_bonds(snapmod):
+    s = random_frozen(seed=8, n=3000, box=14.0, overlap_factor=0.6, r_max=1.4, valence=(2, 2),
+                      eps=1.0)
+    sim, orc = make_pair(snapmod, s, "mixed", p_on0=1.0)
+    for step in range(0, 12):
+        sim.bond_update()
+        orc.sweep(step=0)
+    assert np.array_equal(sim.bonds(), orc.bonds())
+    assert sim.bonds().shape[0] > 100
+    # a new step: breaking with P_off = e^-1 plus new formation
+    for step in (5, 6, 99):
+        set_step(sim, step)
+        sim.bond_update()
+        orc.sweep(step=step)
+        assert np.array_equal(sim.bonds(), orc.bonds())
+
+
+def test_set_bonds_roundtrip_and_sweep(snapmod):
+    s = random_frozen(seed=9, n=1200, box=10.0, overlap_factor=0.6, r_max=1.4, valence=(1, 1))
+    sim, orc = make_pair(snapmod, s, "fp64")
+    a = np.nonzero(s.types == 0)[0][:100]
+    b = np.nonzero(s.types == 1)[0][:100]
+    pairs = np.stack([np.minimum(a, b), np.maximum(a, b)], axis=1)
+    sim.set_bonds(pairs, np.zeros(100, np.int32))
+    orc.set_bonds([(x, y, 0) for x, y in pairs])
+    assert np.array_equal(sim.bonds(), orc.bonds())
+    sim.bond_update()
+    orc.sweep(step=0)
+    assert np.array_equal(sim.bonds(), orc.bonds())
+
+
+def test_no_reactive_particles_and_empty(snapmod):
+    s = random_frozen(seed=10, n=500, box=9.0, overlap_factor=0.6, valence=(0, 0))
+    sim, orc = make_pair(snapmod, s)
+    sim.bond_update()
+    assert sim.bonds().shape[0] == 0
+    sim.step(10)
+    assert sim.stats()["step"] == 10
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_neighbor_list_contains_all_pairs(snapmod, precision):
+    s = colloid_linker(seed=11, n_c=3000, n_l=12000)
+    sim, orc = make_pair(snapmod, s, precision)
+    sim.step(30)
+    pos = sim.positions()
+    orc.set_positions(pos)
+    need = {tuple(p) for p in orc.pairs_within(extra=0.0, reactive=True)}
+    got = {tuple(p) for p in sim.neighbors()}
+    assert need <= got, len(need - got)
+    # and nothing beyond the list cut-off plus the skin margin
+    allowed = {tuple(p) for p in orc.pairs_within(extra=s.skin + 1e-3, reactive=True)}
+    assert got <= allowed
+
+
+def _force_err(f, g):
+    num = np.linalg.norm(f - g)
+    den = np.linalg.norm(g)
+    rms = den / math.sqrt(g.shape[0])
+    per = np.linalg.norm(f - g, axis=1) / np.maximum(np.linalg.norm(g, axis=1), 1e-3 * rms)
+    return num / den, per.max()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_forces_match_oracle(snapmod, precision, tol):
+    s = telechelic(seed=12, n_chains=300, n_x=600)
+    sim, orc = make_pair(snapmod, s, precision)
+    sim.step(200)  # dynamic bonds form; static FENE bonds present
+    pos = sim.positions()
+    bonds = sim.bonds()
+    assert bonds.shape[0] > 50
+    orc.set_positions(pos)
+    orc.set_bonds(bonds)
+    f_g = sim.forces()
+    f_o, _ = orc.forces()
+    norm_err, per_err = _force_err(f_g, f_o)
+    assert norm_err <= tol, (norm_err, per_err)
+    # energies through the deterministic reduction
+    e = sim.energy()
+    _, eo = orc.forces()
+    assert e["e_pair"] == pytest.approx(eo["e_pair"], rel=1e-4 if precision == "mixed" else 1e-10)
+    assert e["e_bond"] == pytest.approx(eo["e_bond"], rel=1e-4 if precision == "mixed" else 1e-10)
+
+
+def test_forces_full_colloid_gel(snapmod):
+    s = colloid_linker(seed=13, n_c=20000, n_l=80000)
+    for precision, tol in (("fp64", 1e-12), ("mixed", 1e-5)):
+        sim, orc = make_pair(snapmod, s, precision)
+        f_g = sim.forces()
+        f_o, _ = orc.forces()
+        norm_err, per_err = _force_err(f_g, f_o)
+        assert norm_err <= tol, (precision, norm_err, per_err)
+        sim.close()
+
+
+def test_fp64_trajectory_follows_oracle(snapmod):
+    s = assoc_ab(seed=14)
+    sim, orc = make_pair(snapmod, s, "fp64")
+    for _ in range(5):
+        sim.step(20)
+        orc.run(20)
+        d = sim.positions() - orc.pos
+        d -= s.box * np.rint(d / s.box)
+        assert np.abs(d).max() < 1e-9
+        assert np.array_equal(sim.bonds(), orc.bonds())
+    v = sim.velocities() - np.stack([orc.vx, orc.vy, orc.vz], axis=1)
+    assert np.abs(v).max() < 1e-7
+
+
+@pytest.mark.parametrize("block", [64, 128, 512, 1024])
+def test_results_independent_of_block_size(snapmod, block):
+    s = colloid_linker(seed=15, n_c=1000, n_l=4000, eps=3.0)
+    ref = snapmod.from_system(s, precision="mixed")
+    ref.step(120)
+    alt = snapmod.from_system(s, precision="mixed", block_size=block)
+    alt.step(120)
+    assert np.array_equal(ref.bonds(), alt.bonds())
+    assert np.array_equal(ref.positions(), alt.positions())
+
+
+def test_checkpoint_resume_is_bit_identical(snapmod):
+    s = colloid_linker(seed=16, n_c=1000, n_l=4000, eps=3.0)
+    a = snapmod.from_system(s, precision="mixed")
+    a.step(50)
+    state = a.get_state()
+    a.step(70)
+    b = snapmod.from_system(s, precision="mixed")
+    b.set_state(state)
+    b.step(70)
+    assert np.array_equal(a.positions(), b.positions())
+    assert np.array_equal(a.bonds(), b.bonds())
+    assert np.array_equal(a.velocities(), b.velocities())
+
+
+def test_neighbor_overflow_regrows_transparently(snapmod):
+    s = colloid_linker(seed=17, n_c=1000, n_l=4000, eps=3.0)
+    ref = snapmod.from_system(s, precision="mixed")
+    ref.step(60)
+    small = snapmod.from_system(s, precision="mixed", nlist_capacity=8)
+    small.step(60)
+    assert small.stats()["nlist_capacity"] > 8
+    assert np.array_equal(ref.bonds(), small.bonds())
+    assert np.array_equal(ref.positions(), small.positions())
+
+
+def test_error_paths_report_status(snapmod):
+    s = telechelic(seed=18, n_chains=50, n_x=100)
+    sim = snapmod.from_system(s, precision="mixed")
+    pos = s.pos.copy()
+    pos[0] = np.nan
+    with pytest.raises(snapmod.SnapError) as e:
+        sim.set_positions(pos)
+    assert e.value.name == "SNAP_ERR_NONFINITE"
+    # FENE bond stretched beyond R0 = 1.5
+    pos = s.pos.copy()
+    pos[1] = pos[0] + np.array([1.6, 0.0, 0.0])
+    sim.set_positions(pos % s.box)
+    with pytest.raises(snapmod.SnapError) as e:
+        sim.forces()
+    assert e.value.name == "SNAP_ERR_FENE_OVERSTRETCH"
+    # runaway velocity -> non-finite position latched on the device
+    sim2 = snapmod.from_system(s, precision="mixed")
+    vel = s.vel.copy()
+    vel[3] = 1e308
+    sim2.set_positions(s.pos, vel)
+    with pytest.raises(snapmod.SnapError) as e:
+        sim2.step(3)
+    assert e.value.name == "SNAP_ERR_NONFINITE"
+    with pytest.raises(snapmod.SnapError):
+        sim2.add_reaction(1, 2, 0, 0.0, 1.2, 1.0, 0.1)  # FENE bond type cannot react
+
+
+def test_batched_replicas_match_standalone(snapmod):
+    reps = [random_frozen(seed=30 + r, n=800 + 137 * r, box=10.0 + r, overlap_factor=0.6,
+                          r_max=1.4, eps=1.0 + r) for r in range(4)]
+    for r, s in enumerate(reps):
+        s.seed = 1000 + 17 * r
+        s.kT = 0.9 + 0.1 * r
+    sim = snapmod.from_system(reps, precision="fp64", p_on0=0.8)
+    orcs = [oracle.OracleSystem(s, p_on0=0.8) for s in reps]
+    sim.step(25)
+    for o in orcs:
+        o.run(25)
+    bonds = sim.bonds()
+    pos = sim.positions()
+    off = 0
+    for s, o in zip(reps, orcs):
+        sel = (bonds[:, 0] >= off) & (bonds[:, 0] < off + s.n)
+        mine = bonds[sel].copy()
+        mine[:, :2] -= off
+        assert np.array_equal(mine, o.bonds())
+        d = pos[off:off + s.n] - o.pos
+        d -= s.box * np.rint(d / s.box)
+        assert np.abs(d).max() < 1e-9
+        off += s.n
