@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--input-cache", default="",
+                    help="directory to keep the generated coordinates between invocations")
     return ap.parse_args()
 
 
@@ -69,6 +71,15 @@ def workload_config(args, n):
 
 def build_system(args, seed):
     from synth import colloid_linker
+    if args.input_cache:
+        import pickle
+        p = Path(args.input_cache) / f"colloid_linker_{args.n_c}_{args.n_l}_{seed}.pkl"
+        if p.exists():
+            return pickle.loads(p.read_bytes())
+        s = colloid_linker(seed=seed, n_c=args.n_c, n_l=args.n_l, eta=0.25)
+        p.parent.mkdir(parents=True, exist_ok=True)
+        p.write_bytes(pickle.dumps(s))
+        return s
     return colloid_linker(seed=seed, n_c=args.n_c, n_l=args.n_l, eta=0.25)
 
 

@@ -93,7 +93,8 @@ typedef struct {
     snap_alloc_fn alloc;     /* device allocator (NULL: cudaMalloc) */
     snap_free_fn free;       /* matching release function */
     void *alloc_user;        /* passed to alloc/free */
-    int32_t block_size;      /* threads per block for particle kernels (0: 256) */
+    int32_t block_size;      /* threads per block for particle kernels: 0 (= 256) or a
+                                multiple of 32 up to 256 */
     int32_t nlist_capacity;  /* initial neighbours per particle (0: from density) */
     int32_t lifetime_bins;   /* bins of the bond-lifetime histogram (0: 256) */
 } snap_config;
@@ -176,8 +177,11 @@ snap_status snap_set_positions(snap_ctx *, const double *pos3, const double *vel
 snap_status snap_set_bonds(snap_ctx *, int64_t nb, const int32_t *tag_pairs,
                            const int32_t *reaction);
 
-/* Advance nsteps MD steps (asynchronous on the stream except for the final
- * status poll, which waits).  Captured as CUDA graphs after the first call. */
+/* Advance nsteps MD steps (asynchronous on the stream except for a status
+ * poll every 2000 steps and at the end, which wait).  Steps run as CUDA graphs
+ * of 20 steps whose neighbour-list rebuild sits in a conditional node; the
+ * environment variable SNAP_GRAPH_MODE=plain captures every kernel instead
+ * (for per-kernel profilers), SNAP_GRAPH_MODE=none disables graphs. */
 snap_status snap_step(snap_ctx *, int64_t nsteps);
 
 /* Advance nsteps MD steps launched one kernel at a time with CUDA events

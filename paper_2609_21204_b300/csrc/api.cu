@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -37,6 +38,7 @@ struct snap_ctx {
     snap_config cfg{};
     std::string err;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;     // capture stream for conditional bodies
     bool own_stream = false;
     bool fp64 = false;
     int block = 256;
@@ -57,6 +59,7 @@ struct snap_ctx {
     // device
     bool ready = false, particles_set = false;
     int ncell_total = 0;
+    int nkeys = 0;
     DevParams P{};
     DevArrays A{}, B{};
     RepDev *d_reps = nullptr;
@@ -115,6 +118,7 @@ template <typename T> bool alloc_arr(snap_ctx *c, T *&p, size_t count)
 }
 
 Launch launch(snap_ctx *c) { return Launch{c->stream, c->block}; }
+Launch launch_on(snap_ctx *c, cudaStream_t s) { return Launch{s, c->block}; }
 
 uint32_t morton3(uint32_t x, uint32_t y, uint32_t z)
 {
@@ -165,6 +169,9 @@ snap_status upload_reps(snap_ctx *c)
         for (size_t a = 0; a < c->rx.size(); ++a) {
             D.p_on0[a] = c->rep_pon[a][r];
             D.p_off[a] = c->rep_poff[a][r];
+            // p_off * 2^53 is exact (scaling by a power of two); u53 = m 2^-53 < p_off
+            // holds exactly when the integer m is below its ceiling
+            D.off_thresh[a] = (unsigned long long)std::ceil(std::ldexp(D.p_off[a], 53));
         }
     }
     CUDA_TRY(c, cudaMemcpyAsync(c->d_reps, h.data(), sizeof(RepDev) * h.size(), cudaMemcpyHostToDevice,
@@ -225,6 +232,8 @@ void fill_params(snap_ctx *c)
     P.n = c->n;
     P.nbr_stride = ((c->n + 31) / 32) * 32;
     P.nrep = (int)c->reps.size();
+    P.screen = c->fp64 ? 0 : 1;
+    P.ncell = c->ncell_total;
 }
 
 // everything that depends on the model (cut-offs -> cell grids -> capacities)
@@ -272,12 +281,15 @@ snap_status ensure_ready(snap_ctx *c)
         for (size_t k = 0; k < codes.size(); ++k) rank_of[R.cell_off + codes[k].second] = R.cell_off + (int)k;
     }
     DevArrays &A = c->A;
-    const int nb = (off + 4095) / 4096 + 1;
-    if (!alloc_arr(c, A.cell_count, off) || !alloc_arr(c, A.cell_start, off + 1) ||
-        !alloc_arr(c, A.cell_cursor, off) || !alloc_arr(c, A.rank_of, off) || !alloc_arr(c, c->d_bsum, nb + 1))
+    const long long nkeys = (long long)off * c->ntypes;   // sort keys: type * ncell + cell
+    if (nkeys > (long long)4096 * 4096) return fail(c, SNAP_ERR_ARG, "too many cells x types");
+    c->nkeys = (int)nkeys;
+    const int nb = (int)((nkeys + 4095) / 4096) + 1;
+    if (!alloc_arr(c, A.cell_count, nkeys) || !alloc_arr(c, A.cell_start, nkeys + 1) ||
+        !alloc_arr(c, A.cell_cursor, nkeys) || !alloc_arr(c, A.rank_of, off) || !alloc_arr(c, c->d_bsum, nb + 1))
         return fail(c, SNAP_ERR_OOM, "cell arrays");
-    CUDA_TRY(c, cudaMemsetAsync(A.cell_count, 0, sizeof(int32_t) * off, c->stream));
-    CUDA_TRY(c, cudaMemsetAsync(A.cell_cursor, 0, sizeof(int32_t) * off, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(A.cell_count, 0, sizeof(int32_t) * nkeys, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(A.cell_cursor, 0, sizeof(int32_t) * nkeys, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(A.rank_of, rank_of.data(), sizeof(int32_t) * off, cudaMemcpyHostToDevice,
                                 c->stream));
     const int64_t stride = ((c->n + 31) / 32) * 32;
@@ -291,13 +303,13 @@ snap_status ensure_ready(snap_ctx *c)
 }
 
 // ---- kernel sequences -------------------------------------------------
-void seq_rebuild(snap_ctx *c)
+void seq_rebuild(snap_ctx *c, cudaStream_t stream = nullptr)
 {
-    const Launch L = launch(c);
+    const Launch L = launch_on(c, stream ? stream : c->stream);
     launch_cell_key(c->P, c->A, L);
-    launch_cell_scan(c->A, c->d_bsum, c->ncell_total, L);
+    launch_cell_scan(c->A, c->d_bsum, c->nkeys, L);
     launch_scatter(c->P, c->A, L);
-    launch_cell_sort(c->A, c->ncell_total, L);
+    launch_cell_sort(c->A, c->nkeys, L);
     launch_gather(c->P, c->A, c->B, c->fp64, L);
     launch_copyback(c->P, c->A, c->B, c->fp64, L);
     launch_nlist(c->P, c->A, c->fp64, L);
@@ -326,20 +338,106 @@ void seq_step(snap_ctx *c)
     launch_step_end(c->A, L);
 }
 
+// One captured step whose neighbour-list rebuild is the body of a conditional
+// (IF) node: between rebuilds the ten rebuild kernels are not launched at all.
+cudaError_t capture_step_conditional(snap_ctx *c)
+{
+    const Launch L = launch(c);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, &deps, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+    if (e != cudaSuccess) return e;
+    launch_set_rebuild_cond(c->A, h, L);
+    e = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, &deps, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCaptureToGraph(c->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    seq_rebuild(c, c->side);
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(c->side, &out);
+    if (e != cudaSuccess) return e;
+    seq_sweep(c, false);
+    launch_force(c->P, c->A, c->fp64, false, L);
+    launch_integrate(c->P, c->A, c->fp64, L);
+    launch_step_end(c->A, L);
+    return cudaGetLastError();
+}
+
+// Graph mode: SNAP_GRAPH_MODE=conditional (default: rebuild kernels inside an
+// IF node), plain (every kernel in the graph, rebuild kernels exit early when
+// no rebuild is due; kernels in such graphs can be profiled one by one), none
+// (no graphs, one launch per kernel).
+int graph_mode()
+{
+    const char *m = std::getenv("SNAP_GRAPH_MODE");
+    if (!m) return 0;
+    if (!std::strcmp(m, "plain")) return 1;
+    if (!std::strcmp(m, "none")) return 2;
+    return 0;
+}
+
+void end_dangling_capture(cudaStream_t s)
+{
+    if (!s) return;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamEndCapture(s, &g) == cudaSuccess && g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+}
+
 snap_status build_graph(snap_ctx *c)
 {
     if (c->graph) {
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
     }
+    const int mode = graph_mode();
+    if (!c->side) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    for (int s = 0; s < kGraphSteps; ++s) seq_step(c);
+    cudaError_t ce = cudaSuccess;
+    for (int s = 0; s < kGraphSteps && ce == cudaSuccess; ++s) {
+        if (mode == 1) {
+            seq_step(c);
+            ce = cudaGetLastError();
+        } else {
+            ce = capture_step_conditional(c);
+        }
+    }
+    if (ce != cudaSuccess) {
+        end_dangling_capture(c->side);
+        end_dangling_capture(c->stream);
+        c->graph_dirty = true;
+        return fail(c, SNAP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    }
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess) return fail(c, SNAP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) return fail(c, SNAP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, SNAP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    c->graph = ex;
     c->graph_dirty = false;
     return SNAP_OK;
 }
@@ -517,9 +615,18 @@ snap_status velocities_in(snap_ctx *c, const double *vel3)
             for (int d = 0; d < 3; ++d) vs[d][t] = vel3[3 * t + d];
     double *dst[3] = {c->A.vx, c->A.vy, c->A.vz};
     double *stg[3] = {c->B.vx, c->B.vy, c->B.vz};
-    for (int d = 0; d < 3; ++d) {
-        snap_status s = upload_in<double>(c, dst[d], stg[d], vs[d].data(), c->n);
-        if (s != SNAP_OK) return s;
+    if (c->fp64) {
+        for (int d = 0; d < 3; ++d) {
+            snap_status s = upload_in<double>(c, dst[d], stg[d], vs[d].data(), c->n);
+            if (s != SNAP_OK) return s;
+        }
+    } else {
+        // FP32 velocities in mixed mode: stage in tag order, convert and scatter
+        for (int d = 0; d < 3; ++d)
+            CUDA_TRY(c, cudaMemcpyAsync(stg[d], vs[d].data(), sizeof(double) * c->n, cudaMemcpyHostToDevice,
+                                        c->stream));
+        launch_v4_in(c->A.v4, stg[0], stg[1], stg[2], c->A.rtag, c->n, launch(c));
+        CUDA_TRY(c, cudaGetLastError());
     }
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return SNAP_OK;
@@ -585,9 +692,14 @@ snap_status bonds_out(snap_ctx *c, std::vector<BondRec> &out)
 
 snap_status counters_out(snap_ctx *c, unsigned long long *h)
 {
-    CUDA_TRY(c, cudaMemcpyAsync(h, c->A.counters, sizeof(unsigned long long) * cNumCounters,
+    std::vector<unsigned long long> raw((size_t)cNumCounters * kCopies);
+    CUDA_TRY(c, cudaMemcpyAsync(raw.data(), c->A.counters, sizeof(unsigned long long) * raw.size(),
                                 cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < cNumCounters; ++k) {
+        h[k] = 0ull;
+        for (int q = 0; q < kCopies; ++q) h[k] += raw[(size_t)k * kCopies + q];
+    }
     return SNAP_OK;
 }
 
@@ -604,7 +716,7 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
     if (!(cfg->dt > 0.0) || !(cfg->kT >= 0.0) || !(cfg->gamma >= 0.0) || !(cfg->skin > 0.0)) return SNAP_ERR_ARG;
     if (cfg->precision != SNAP_FP64 && cfg->precision != SNAP_MIXED) return SNAP_ERR_ARG;
     if (cfg->bond_period < 1) return SNAP_ERR_ARG;
-    if (cfg->block_size < 0 || cfg->block_size > 1024 || (cfg->block_size % 32) != 0) return SNAP_ERR_ARG;
+    if (cfg->block_size < 0 || cfg->block_size > 256 || (cfg->block_size % 32) != 0) return SNAP_ERR_ARG;
     if ((cfg->alloc == nullptr) != (cfg->free == nullptr)) return SNAP_ERR_ARG;
     const int nrep = cfg->n_replicas > 1 ? cfg->n_replicas : 1;
     if (cfg->n_replicas > 1 && !cfg->replica_n) return SNAP_ERR_ARG;
@@ -670,6 +782,7 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
                   alloc_arr(c, D->drx, n) && alloc_arr(c, D->dbirth, n) && alloc_arr(c, D->occ, n);
         D->pos4 = dalloc(c, v4 * n);
         if (!ok || !D->pos4) return bail(SNAP_ERR_OOM, "particles");
+        if (!c->fp64 && !alloc_arr(c, D->v4, n)) return bail(SNAP_ERR_OOM, "velocities");
     }
     DevArrays &A = c->A;
     A.force = dalloc(c, v4 * n);
@@ -678,7 +791,10 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
               alloc_arr(c, A.prop_r, n) && alloc_arr(c, A.prio, n) && alloc_arr(c, A.best, n) &&
               alloc_arr(c, A.fpart, n) && alloc_arr(c, A.brk, n) && alloc_arr(c, A.rx_order, (size_t)nrep * kMaxRx) &&
               alloc_arr(c, A.step, 1) && alloc_arr(c, A.status, 1) && alloc_arr(c, A.need_rebuild, 1) &&
-              alloc_arr(c, A.nbr_need, 1) && alloc_arr(c, A.counters, cNumCounters) &&
+              alloc_arr(c, A.nbr_need, 1) && alloc_arr(c, A.counters, (size_t)cNumCounters * kCopies) &&
+              alloc_arr(c, A.ox, n) && alloc_arr(c, A.oy, n) && alloc_arr(c, A.oz, n) &&
+              alloc_arr(c, A.site_list, n) && alloc_arr(c, A.list_count, 1) &&
+              alloc_arr(c, A.cont, n * kContenders) && alloc_arr(c, A.ncont, n) &&
               alloc_arr(c, A.life_hist, (size_t)c->cfg.lifetime_bins) && alloc_arr(c, A.e_part, 4 * n) &&
               alloc_arr(c, c->d_red, 8);
     c->d_reps = static_cast<RepDev *>(dalloc(c, sizeof(RepDev) * nrep));
@@ -692,7 +808,8 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
         cudaMemsetAsync(A.step, 0, 8, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.need_rebuild, 0, 4, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.nbr_need, 0, 4, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(A.counters, 0, sizeof(unsigned long long) * cNumCounters, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.counters, 0, sizeof(unsigned long long) * cNumCounters * kCopies, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.list_count, 0, 4, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.life_hist, 0, sizeof(unsigned long long) * c->cfg.lifetime_bins, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -854,7 +971,7 @@ extern "C" snap_status snap_set_particles(snap_ctx *c, const double *pos3, const
     c->bonds_base = 0;
     CUDA_TRY(c, cudaMemsetAsync(c->A.step, 0, 8, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->A.status, 0, 4, c->stream));
-    CUDA_TRY(c, cudaMemsetAsync(c->A.counters, 0, sizeof(unsigned long long) * cNumCounters, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->A.counters, 0, sizeof(unsigned long long) * cNumCounters * kCopies, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->A.life_hist, 0, sizeof(unsigned long long) * c->cfg.lifetime_bins, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->A.force, 0, (c->fp64 ? sizeof(double4_32a) : sizeof(float4)) * c->n, c->stream));
     c->particles_set = true;
@@ -918,7 +1035,7 @@ extern "C" snap_status snap_step(snap_ctx *c, int64_t nsteps)
     int retries = 0;
     while (cur < target) {
         long long todo = std::min<long long>(target - cur, kPollSteps);
-        long long ngraph = todo / kGraphSteps;
+        long long ngraph = graph_mode() == 2 ? 0 : todo / kGraphSteps;
         if (ngraph > 0 && c->graph_dirty) {
             if ((s = build_graph(c)) != SNAP_OK) return s;
         }
@@ -1038,19 +1155,52 @@ extern "C" snap_status snap_get_bonds(snap_ctx *c, int32_t *pairs, int32_t *reac
     return SNAP_OK;
 }
 
+// raw device positions and images in tag order (positions may lie outside
+// the box between rebuilds in mixed mode)
+snap_status raw_positions_images(snap_ctx *c, double *pos3, int32_t *img3)
+{
+    snap_status s;
+    std::vector<double> v(c->n);
+    std::vector<int32_t> w(c->n);
+    const double *src[3] = {c->A.x, c->A.y, c->A.z};
+    double *stg[3] = {c->B.x, c->B.y, c->B.z};
+    const int32_t *isrc[3] = {c->A.ix, c->A.iy, c->A.iz};
+    int32_t *istg[3] = {c->B.ix, c->B.iy, c->B.iz};
+    for (int d = 0; d < 3; ++d) {
+        if ((s = download_out<double>(c, v.data(), src[d], stg[d], c->n)) != SNAP_OK) return s;
+        if ((s = download_out<int32_t>(c, w.data(), isrc[d], istg[d], c->n)) != SNAP_OK) return s;
+        for (int64_t t = 0; t < c->n; ++t) {
+            pos3[3 * t + d] = v[t];
+            img3[3 * t + d] = w[t];
+        }
+    }
+    return SNAP_OK;
+}
+
+snap_status wrapped_positions_images(snap_ctx *c, double *pos3, int32_t *img3)
+{
+    snap_status s = raw_positions_images(c, pos3, img3);
+    if (s != SNAP_OK) return s;
+    for (int64_t t = 0; t < c->n; ++t) {
+        const RepHost &R = c->reps[rep_of_tag(c, t)];
+        for (int d = 0; d < 3; ++d) {
+            double &x = pos3[3 * t + d];
+            if (x >= 0.0 && x < R.L[d]) continue;
+            int32_t k = 0;
+            wrap_host(x, k, R.L[d]);
+            img3[3 * t + d] += k;
+        }
+    }
+    return SNAP_OK;
+}
+
 extern "C" snap_status snap_get_positions(snap_ctx *c, double *pos3)
 {
     snap_status s = check_ready(c);
     if (s != SNAP_OK) return s;
     if (c->n > 0 && !pos3) return fail(c, SNAP_ERR_ARG, "pos3 is NULL");
-    std::vector<double> v(c->n);
-    const double *src[3] = {c->A.x, c->A.y, c->A.z};
-    double *stg[3] = {c->B.x, c->B.y, c->B.z};
-    for (int d = 0; d < 3; ++d) {
-        if ((s = download_out<double>(c, v.data(), src[d], stg[d], c->n)) != SNAP_OK) return s;
-        for (int64_t t = 0; t < c->n; ++t) pos3[3 * t + d] = v[t];
-    }
-    return SNAP_OK;
+    std::vector<int32_t> img((size_t)c->n * 3);
+    return wrapped_positions_images(c, pos3, img.data());
 }
 
 extern "C" snap_status snap_get_velocities(snap_ctx *c, double *vel3)
@@ -1061,8 +1211,17 @@ extern "C" snap_status snap_get_velocities(snap_ctx *c, double *vel3)
     std::vector<double> v(c->n);
     const double *src[3] = {c->A.vx, c->A.vy, c->A.vz};
     double *stg[3] = {c->B.vx, c->B.vy, c->B.vz};
+    if (!c->fp64) {
+        launch_v4_out(stg[0], stg[1], stg[2], c->A.v4, c->A.rtag, c->n, launch(c));
+        CUDA_TRY(c, cudaGetLastError());
+    }
     for (int d = 0; d < 3; ++d) {
-        if ((s = download_out<double>(c, v.data(), src[d], stg[d], c->n)) != SNAP_OK) return s;
+        if (c->fp64) {
+            if ((s = download_out<double>(c, v.data(), src[d], stg[d], c->n)) != SNAP_OK) return s;
+        } else {
+            CUDA_TRY(c, cudaMemcpyAsync(v.data(), stg[d], sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        }
         for (int64_t t = 0; t < c->n; ++t) vel3[3 * t + d] = v[t];
     }
     return SNAP_OK;
@@ -1073,14 +1232,8 @@ extern "C" snap_status snap_get_images(snap_ctx *c, int32_t *img3)
     snap_status s = check_ready(c);
     if (s != SNAP_OK) return s;
     if (c->n > 0 && !img3) return fail(c, SNAP_ERR_ARG, "img3 is NULL");
-    std::vector<int32_t> v(c->n);
-    const int32_t *src[3] = {c->A.ix, c->A.iy, c->A.iz};
-    int32_t *stg[3] = {c->B.ix, c->B.iy, c->B.iz};
-    for (int d = 0; d < 3; ++d) {
-        if ((s = download_out<int32_t>(c, v.data(), src[d], stg[d], c->n)) != SNAP_OK) return s;
-        for (int64_t t = 0; t < c->n; ++t) img3[3 * t + d] = v[t];
-    }
-    return SNAP_OK;
+    std::vector<double> pos((size_t)c->n * 3);
+    return wrapped_positions_images(c, pos.data(), img3);
 }
 
 extern "C" snap_status snap_get_neighbors(snap_ctx *c, int32_t *pairs, int64_t cap, int64_t *n_out)
@@ -1205,20 +1358,23 @@ extern "C" snap_status snap_get_state(snap_ctx *c, void *buf, size_t *len)
     const uint64_t hdr[4] = {kStateMagic, (uint64_t)n, (uint64_t)step, (uint64_t)b.size()};
     std::memcpy(p, hdr, sizeof hdr);
     p += sizeof hdr;
+    // raw (possibly unwrapped) positions and images, so a restore continues bit-identically
     std::vector<double> v3(3 * n);
-    if ((s = snap_get_positions(c, v3.data())) != SNAP_OK) return s;
+    std::vector<int32_t> i3(3 * n);
+    if ((s = raw_positions_images(c, v3.data(), i3.data())) != SNAP_OK) return s;
     std::memcpy(p, v3.data(), sizeof(double) * 3 * n);
     p += sizeof(double) * 3 * n;
     if ((s = snap_get_velocities(c, v3.data())) != SNAP_OK) return s;
     std::memcpy(p, v3.data(), sizeof(double) * 3 * n);
     p += sizeof(double) * 3 * n;
-    std::vector<int32_t> i3(3 * n);
-    if ((s = snap_get_images(c, i3.data())) != SNAP_OK) return s;
     std::memcpy(p, i3.data(), sizeof(int32_t) * 3 * n);
     p += sizeof(int32_t) * 3 * n;
     if (!b.empty()) std::memcpy(p, b.data(), sizeof(BondRec) * b.size());
     *len = need;
-    return SNAP_OK;
+    // A restore rebuilds the cell list before its first step; rebuild here too,
+    // so that the saved run and every run restored from this state continue
+    // with the same cell origins and memory order, bit for bit.
+    return set_need_rebuild(c);
 }
 
 extern "C" snap_status snap_set_state(snap_ctx *c, const void *buf, size_t len)
@@ -1246,8 +1402,6 @@ extern "C" snap_status snap_set_state(snap_ctx *c, const void *buf, size_t len)
     // positions are already wrapped; upload them verbatim so the run continues bit-identically
     double *dst[3] = {c->A.x, c->A.y, c->A.z};
     double *stg[3] = {c->B.x, c->B.y, c->B.z};
-    double *vdst[3] = {c->A.vx, c->A.vy, c->A.vz};
-    double *vstg[3] = {c->B.vx, c->B.vy, c->B.vz};
     int32_t *idst[3] = {c->A.ix, c->A.iy, c->A.iz};
     int32_t *istg[3] = {c->B.ix, c->B.iy, c->B.iz};
     std::vector<double> col(n);
@@ -1256,13 +1410,11 @@ extern "C" snap_status snap_set_state(snap_ctx *c, const void *buf, size_t len)
         for (size_t t = 0; t < n; ++t) col[t] = pos[3 * t + d];
         if ((s = upload_in<double>(c, dst[d], stg[d], col.data(), n)) != SNAP_OK) return s;
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-        for (size_t t = 0; t < n; ++t) col[t] = vel[3 * t + d];
-        if ((s = upload_in<double>(c, vdst[d], vstg[d], col.data(), n)) != SNAP_OK) return s;
-        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
         for (size_t t = 0; t < n; ++t) icol[t] = img[3 * t + d];
         if ((s = upload_in<int32_t>(c, idst[d], istg[d], icol.data(), n)) != SNAP_OK) return s;
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     }
+    if ((s = velocities_in(c, vel.data())) != SNAP_OK) return s;
     if ((s = bonds_in(c, b)) != SNAP_OK) return s;
     const long long step = (long long)hdr[2];
     CUDA_TRY(c, cudaMemcpyAsync(c->A.step, &step, 8, cudaMemcpyHostToDevice, c->stream));
@@ -1298,5 +1450,6 @@ extern "C" void snap_destroy(snap_ctx *c)
     std::vector<void *> all = c->allocs;
     for (void *p : all) dfree(c, p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->side) cudaStreamDestroy(c->side);
     delete c;
 }

@@ -31,8 +31,34 @@ __global__ void k_iota(int32_t *dst, long long n)
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) dst[t] = (int32_t)t;
 }
+__global__ void k_v4_in(float4 *v4, const double *vx, const double *vy, const double *vz, const int32_t *rtag,
+                        long long n)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) v4[rtag[t]] = make_float4((float)vx[t], (float)vy[t], (float)vz[t], 0.f);
+}
+__global__ void k_v4_out(double *vx, double *vy, double *vz, const float4 *v4, const int32_t *rtag, long long n)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const float4 v = v4[rtag[t]];
+    vx[t] = v.x;
+    vy[t] = v.y;
+    vz[t] = v.z;
+}
 inline unsigned grid_for(long long n) { return (unsigned)((n + 255) / 256); }
 }  // namespace
+
+void launch_v4_in(float4 *v4, const double *vx, const double *vy, const double *vz, const int32_t *rtag,
+                  long long n, Launch L)
+{
+    if (n > 0) k_v4_in<<<grid_for(n), 256, 0, L.stream>>>(v4, vx, vy, vz, rtag, n);
+}
+void launch_v4_out(double *vx, double *vy, double *vz, const float4 *v4, const int32_t *rtag, long long n,
+                   Launch L)
+{
+    if (n > 0) k_v4_out<<<grid_for(n), 256, 0, L.stream>>>(vx, vy, vz, v4, rtag, n);
+}
 
 template <typename T>
 void launch_in(T *dst, const T *src, const int32_t *rtag, long long n, Launch L)

@@ -1,8 +1,10 @@
 // Cell list, Morton-ordered particle sort, neighbour list, pair + bond forces.
 //
-// Layout: particles live in the order of the Morton rank of their cell
-// (cells of side >= the largest neighbour cut-off), so the 27 cells around a
-// particle are nearby in memory and neighbour gathers hit L1/L2.  Positions
+// Layout: particles are sorted by (type, Morton rank of their cell, tag),
+// with cells of side >= the largest neighbour cut-off.  Within one type the
+// 27 cells around a particle are nearby in memory, so neighbour gathers hit
+// L1/L2, and a warp holds particles of one type, so its lanes do similar work
+// (a colloid has ~2x the neighbours of a linker).  Positions
 // used by the force loop are stored relative to the origin of the particle's
 // cell (frozen between rebuilds) with the cell coordinates and type packed in
 // the w word; a pair's separation is (rel_j - rel_i) + (c_j - c_i) * w, which
@@ -31,19 +33,45 @@ __device__ __forceinline__ void cell_of(const RepDev &R, double x, double y, dou
     cz = min(max(cz, 0), R.nc[2] - 1);
 }
 
+// wrap into [0, L) and count the crossing in the image counter
+__device__ __forceinline__ double wrap_img(double x, double L, int &img)
+{
+    if (x >= L) {
+        x -= L;
+        img += 1;
+    } else if (x < 0.0) {
+        x += L;
+        img -= 1;
+        if (x >= L) {
+            x -= L;
+            img += 1;
+        }
+    }
+    return x;
+}
+
 __global__ void k_cell_key(DevParams P, DevArrays A)
 {
     const long long i = gtid();
     if (i >= P.n) return;
     if (!status_ok(A.status) || !*A.need_rebuild) return;
     const RepDev &R = A.reps[A.rep[i]];
+    double x = A.x[i], y = A.y[i], z = A.z[i];
+    if (!(x >= 0.0 && x < R.L[0] && y >= 0.0 && y < R.L[1] && z >= 0.0 && z < R.L[2])) {
+        int ix = A.ix[i], iy = A.iy[i], iz = A.iz[i];
+        x = wrap_img(x, R.L[0], ix);
+        y = wrap_img(y, R.L[1], iy);
+        z = wrap_img(z, R.L[2], iz);
+        A.x[i] = x; A.y[i] = y; A.z[i] = z;
+        A.ix[i] = ix; A.iy[i] = iy; A.iz[i] = iz;
+    }
     int cx, cy, cz;
-    cell_of(R, A.x[i], A.y[i], A.z[i], cx, cy, cz);
+    cell_of(R, x, y, z, cx, cy, cz);
     const int lin = (cz * R.nc[1] + cy) * R.nc[0] + cx;
-    const int c = A.rank_of[R.cell_off + lin];
+    const int c = A.type[i] * P.ncell + A.rank_of[R.cell_off + lin];
     A.cell_key[i] = c;
     atomicAdd(&A.cell_count[c], 1);
-    if (i == 0) A.counters[cNlistEntries] = 0ull;
+    if (i == 0) counter_reset(A.counters, cNlistEntries);
 }
 
 // three-phase exclusive scan of cell_count into cell_start[0..ncell]
@@ -177,7 +205,11 @@ __global__ void k_gather(DevParams P, DevArrays A, DevArrays B)
     const int i = A.order[k];
     const double x = A.x[i], y = A.y[i], z = A.z[i];
     B.x[k] = x; B.y[k] = y; B.z[k] = z;
-    B.vx[k] = A.vx[i]; B.vy[k] = A.vy[i]; B.vz[k] = A.vz[i];
+    if (sizeof(R) == 8) {
+        B.vx[k] = A.vx[i]; B.vy[k] = A.vy[i]; B.vz[k] = A.vz[i];
+    } else {
+        B.v4[k] = A.v4[i];
+    }
     B.ix[k] = A.ix[i]; B.iy[k] = A.iy[i]; B.iz[k] = A.iz[i];
     const int t = A.type[i];
     B.type[k] = t;
@@ -192,9 +224,11 @@ __global__ void k_gather(DevParams P, DevArrays A, DevArrays B)
     const RepDev &Rp = A.reps[rp];
     int cx, cy, cz;
     cell_of(Rp, x, y, z, cx, cy, cz);
-    const double rx = x - (double)cx * Rp.w[0];
-    const double ry = y - (double)cy * Rp.w[1];
-    const double rz = z - (double)cz * Rp.w[2];
+    const double o0 = (double)cx * Rp.w[0], o1 = (double)cy * Rp.w[1], o2 = (double)cz * Rp.w[2];
+    A.ox[k] = o0; A.oy[k] = o1; A.oz[k] = o2;
+    const double rx = x - o0;
+    const double ry = y - o1;
+    const double rz = z - o2;
     V p;
     p.x = (R)rx; p.y = (R)ry; p.z = (R)rz;
     set_w_bits(p, pack_bits(t, cx, cy, cz));
@@ -210,7 +244,11 @@ __global__ void k_copyback(DevParams P, DevArrays A, DevArrays B)
     if (k >= P.n) return;
     if (!status_ok(A.status) || !*A.need_rebuild) return;
     A.x[k] = B.x[k]; A.y[k] = B.y[k]; A.z[k] = B.z[k];
-    A.vx[k] = B.vx[k]; A.vy[k] = B.vy[k]; A.vz[k] = B.vz[k];
+    if (sizeof(R) == 8) {
+        A.vx[k] = B.vx[k]; A.vy[k] = B.vy[k]; A.vz[k] = B.vz[k];
+    } else {
+        A.v4[k] = B.v4[k];
+    }
     A.ix[k] = B.ix[k]; A.iy[k] = B.iy[k]; A.iz[k] = B.iz[k];
     A.type[k] = B.type[k]; A.tag[k] = B.tag[k]; A.rep[k] = B.rep[k];
     A.sp[k] = B.sp[k]; A.sbt[k] = B.sbt[k];
@@ -221,61 +259,85 @@ __global__ void k_copyback(DevParams P, DevArrays A, DevArrays B)
 
 // Full neighbour list: every j != i in the 27 cells around i with
 // r^2 < rl2(ti, tj); column-major storage nbr[slot * stride + i].
+// Full neighbour list: every j != i with r^2 < rl2(ti, tj), column-major
+// nbr[slot * stride + i].  For each of the 27 surrounding cells and each type
+// the particle's distance to the cell box is compared with that type pair's
+// list cut-off first, so short-ranged pairs (small spheres) skip most cells.
 template <typename R>
-__global__ void k_nlist(DevParams P, DevArrays A)
+__global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A)
 {
     using V = typename Vec4<R>::T;
+    if (!status_ok(A.status) || !*A.need_rebuild) return;   // uniform
     const long long i = gtid();
-    if (i >= P.n) return;
-    if (!status_ok(A.status) || !*A.need_rebuild) return;
-    const V *pos = reinterpret_cast<const V *>(A.pos4);
-    const V p = pos[i];
-    const uint32_t b = w_bits(p);
-    const int ti = bits_type(b), cx = bits_cx(b), cy = bits_cy(b), cz = bits_cz(b);
-    const RepDev &Rp = A.reps[A.rep[i]];
-    const int nx = Rp.nc[0], ny = Rp.nc[1], nz = Rp.nc[2];
-    const float wx = Rp.wf[0], wy = Rp.wf[1], wz = Rp.wf[2];
-    const float pxf = (float)p.x, pyf = (float)p.y, pzf = (float)p.z;
-    const int cap = P.nbr_cap;
-    const long long stride = P.nbr_stride;
     int cnt = 0;
-    for (int dz = -1; dz <= 1; ++dz) {
-        int zz = cz + dz;
-        zz += (zz < 0) ? nz : 0;
-        zz -= (zz >= nz) ? nz : 0;
-        for (int dy = -1; dy <= 1; ++dy) {
-            int yy = cy + dy;
-            yy += (yy < 0) ? ny : 0;
-            yy -= (yy >= ny) ? ny : 0;
-            for (int dx = -1; dx <= 1; ++dx) {
-                int xx = cx + dx;
-                xx += (xx < 0) ? nx : 0;
-                xx -= (xx >= nx) ? nx : 0;
-                const int c = A.rank_of[Rp.cell_off + (zz * ny + yy) * nx + xx];
-                const int s = A.cell_start[c], e = A.cell_start[c + 1];
-                const float ox = dx * wx, oy = dy * wy, oz = dz * wz;
-                for (int j = s; j < e; ++j) {
-                    if (j == i) continue;
-                    const V q = pos[j];
-                    const int tj = bits_type(w_bits(q));
-                    const float ddx = ((float)q.x - pxf) + ox;
-                    const float ddy = ((float)q.y - pyf) + oy;
-                    const float ddz = ((float)q.z - pzf) + oz;
-                    const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    if (r2 < P.rl2f[ti * kMaxTypes + tj]) {
-                        if (cnt < cap) A.nbr[(long long)cnt * stride + i] = j;
-                        ++cnt;
+    const int cap = P.nbr_cap;
+    if (i < P.n) {
+        const V *pos = reinterpret_cast<const V *>(A.pos4);
+        const V p = pos[i];
+        const uint32_t b = w_bits(p);
+        const int ti = bits_type(b), cx = bits_cx(b), cy = bits_cy(b), cz = bits_cz(b);
+        const RepDev &Rp = A.reps[A.rep[i]];
+        const int nx = Rp.nc[0], ny = Rp.nc[1], nz = Rp.nc[2];
+        const float wx = Rp.wf[0], wy = Rp.wf[1], wz = Rp.wf[2];
+        const float pxf = (float)p.x, pyf = (float)p.y, pzf = (float)p.z;
+        const long long stride = P.nbr_stride;
+        // distance to the lower/upper faces of the own cell (rel in [0, w) at a build)
+        const float gxl = fmaxf(pxf, 0.f), gxu = fmaxf(wx - pxf, 0.f);
+        const float gyl = fmaxf(pyf, 0.f), gyu = fmaxf(wy - pyf, 0.f);
+        const float gzl = fmaxf(pzf, 0.f), gzu = fmaxf(wz - pzf, 0.f);
+        for (int dz = -1; dz <= 1; ++dz) {
+            int zz = cz + dz;
+            zz += (zz < 0) ? nz : 0;
+            zz -= (zz >= nz) ? nz : 0;
+            const float gz = dz < 0 ? gzl : (dz > 0 ? gzu : 0.f);
+            for (int dy = -1; dy <= 1; ++dy) {
+                int yy = cy + dy;
+                yy += (yy < 0) ? ny : 0;
+                yy -= (yy >= ny) ? ny : 0;
+                const float gy = dy < 0 ? gyl : (dy > 0 ? gyu : 0.f);
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int xx = cx + dx;
+                    xx += (xx < 0) ? nx : 0;
+                    xx -= (xx >= nx) ? nx : 0;
+                    const float gx = dx < 0 ? gxl : (dx > 0 ? gxu : 0.f);
+                    const float d2 = gx * gx + gy * gy + gz * gz;
+                    const int c = A.rank_of[Rp.cell_off + (zz * ny + yy) * nx + xx];
+                    const float ox = dx * wx - pxf, oy = dy * wy - pyf, oz = dz * wz - pzf;
+                    for (int t = 0; t < P.ntypes; ++t) {
+                        const float cut2 = P.rl2f[ti * kMaxTypes + t];
+                        if (d2 >= cut2) continue;
+                        const int key = t * P.ncell + c;
+                        const int s0 = A.cell_start[key], e = A.cell_start[key + 1];
+                        for (int j = s0; j < e; ++j) {
+                            if (j == i) continue;
+                            const V q = pos[j];
+                            const float ddx = (float)q.x + ox;
+                            const float ddy = (float)q.y + oy;
+                            const float ddz = (float)q.z + oz;
+                            const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                            if (r2 < cut2) {
+                                if (cnt < cap) A.nbr[(long long)cnt * stride + i] = j;
+                                ++cnt;
+                            }
+                        }
                     }
                 }
             }
         }
+        A.nn[i] = min(cnt, cap);
+        if (cnt > cap) {
+            atomicOr(A.status, (uint32_t)kStOverflow);
+            atomicMax(A.nbr_need, cnt);
+        }
     }
-    A.nn[i] = min(cnt, cap);
-    warp_count(&A.counters[cNlistEntries], (unsigned long long)min(cnt, cap));
-    if (cnt > cap) {
-        atomicOr(A.status, (uint32_t)kStOverflow);
-        atomicMax(A.nbr_need, cnt);
-    }
+    const int idx[1] = {cNlistEntries};
+    const unsigned long long v[1] = {(unsigned long long)min(cnt, cap)};
+    warp_counts<1>(A.counters, idx, v);
+}
+
+__global__ void k_set_rebuild_cond(DevArrays A, cudaGraphConditionalHandle h)
+{
+    cudaGraphSetConditional(h, (status_ok(A.status) && *A.need_rebuild) ? 1u : 0u);
 }
 
 __global__ void k_rebuild_done(DevArrays A)
@@ -283,7 +345,7 @@ __global__ void k_rebuild_done(DevArrays A)
     if (!status_ok(A.status)) return;
     if (*A.need_rebuild) {
         *A.need_rebuild = 0;
-        A.counters[cBuilds] += 1ull;
+        counter_add1(A.counters, cBuilds, 1ull);
     }
 }
 
@@ -297,6 +359,8 @@ template <> struct Num<float> {
     __device__ static float br0(const DevParams &P, int k) { return P.br0f[k]; }
     __device__ static float w(const RepDev &R, int d) { return R.wf[d]; }
     __device__ static float sqrt_(float v) { return sqrtf(v); }
+    // approximate reciprocal (MUFU, <= 1 ulp); well inside the FP32 force tolerance
+    __device__ static float rcp(float v) { return __fdividef(1.0f, v); }
 };
 template <> struct Num<double> {
     __device__ static double rc2(const DevParams &P, int k) { return P.rc2d[k]; }
@@ -306,6 +370,7 @@ template <> struct Num<double> {
     __device__ static double br0(const DevParams &P, int k) { return P.br0[k]; }
     __device__ static double w(const RepDev &R, int d) { return R.w[d]; }
     __device__ static double sqrt_(double v) { return sqrt(v); }
+    __device__ static double rcp(double v) { return 1.0 / v; }
 };
 
 // separation (j - i) of two particles from their relative coords and cells
@@ -360,16 +425,23 @@ __global__ void __launch_bounds__(256) k_force(DevParams P, DevArrays A)
     const int nn = A.nn[i];
     const long long stride = P.nbr_stride;
     const int *nb = A.nbr + i;
+    // the next neighbour's index and position are loaded while the current
+    // pair is evaluated; the sum runs in list order
+    int jn = nn > 0 ? __ldg(nb) : 0;
+    V pn = pos[jn];
     for (int k = 0; k < nn; ++k) {
-        const int j = __ldg(nb + (long long)k * stride);
-        const V pj = pos[j];
+        const V pj = pn;
+        if (k + 1 < nn) {
+            jn = __ldg(nb + (long long)(k + 1) * stride);
+            pn = pos[jn];
+        }
         const int tj = bits_type(w_bits(pj));
         R dx, dy, dz;
         separation<R>(pi, pj, Rp, dx, dy, dz);
         const R r2 = dx * dx + dy * dy + dz * dz;
         const int tt = ti * kMaxTypes + tj;
         if (r2 < Num<R>::rc2(P, tt)) {
-            const R ir2 = (R)1 / r2;
+            const R ir2 = Num<R>::rcp(r2);
             const R s2 = Num<R>::sig2(P, tt) * ir2;
             const R s6 = s2 * s2 * s2;
             const R fr = Num<R>::eps24(P, tt) * (s6 * ((R)2 * s6 - (R)1)) * ir2;
@@ -432,7 +504,13 @@ __global__ void __launch_bounds__(256) k_force(DevParams P, DevArrays A)
     f.x = fx; f.y = fy; f.z = fz; f.w = 0;
     reinterpret_cast<V *>(A.force)[i] = f;
     if (E) {
-        const double vx = A.vx[i], vy = A.vy[i], vz = A.vz[i];
+        double vx, vy, vz;
+        if (sizeof(R) == 8) {
+            vx = A.vx[i]; vy = A.vy[i]; vz = A.vz[i];
+        } else {
+            const float4 v = A.v4[i];
+            vx = v.x; vy = v.y; vz = v.z;
+        }
         A.e_part[4 * i + 0] = ep;
         A.e_part[4 * i + 1] = eb;
         A.e_part[4 * i + 2] = vir;
@@ -517,6 +595,11 @@ void launch_nlist(const DevParams &P, const DevArrays &A, bool fp64, Launch L)
 }
 
 void launch_rebuild_done(const DevArrays &A, Launch L) { k_rebuild_done<<<1, 1, 0, L.stream>>>(A); }
+
+void launch_set_rebuild_cond(const DevArrays &A, cudaGraphConditionalHandle h, Launch L)
+{
+    k_set_rebuild_cond<<<1, 1, 0, L.stream>>>(A, h);
+}
 
 void launch_force(const DevParams &P, const DevArrays &A, bool fp64, bool energy, Launch L)
 {

@@ -52,6 +52,8 @@ struct DevParams {
     int64_t n;              // particles (all replicas)
     int64_t nbr_stride;     // column stride of the neighbour list
     int32_t nrep;
+    int32_t screen;         // mixed mode: FP32 pre-screen of the proposal test, FP32 velocities
+    int32_t ncell;          // cells over all replicas; sort keys are type * ncell + cell
 };
 
 struct RepDev {
@@ -64,11 +66,14 @@ struct RepDev {
     double kT, noise_c;     // set-point kT and sqrt(2 gamma kT / dt)
     uint32_t key0, key1hi;  // Philox key words derived from the seed
     double p_on0[kMaxRx], p_off[kMaxRx];
+    unsigned long long off_thresh[kMaxRx];   // ceil(p_off * 2^53): break iff 53-bit draw < this
 };
 
 // Device arrays (sorted particle order unless stated).
 struct DevArrays {
-    double *x, *y, *z, *vx, *vy, *vz;
+    double *x, *y, *z, *vx, *vy, *vz;   // vx..vz: FP64 mode velocities
+    float4 *v4;                     // mixed mode velocities (w unused)
+    double *ox, *oy, *oz;           // origin of the frozen cell of each particle (set at rebuild)
     int32_t *ix, *iy, *iz;          // image counters
     int32_t *type, *tag, *rtag, *rep;
     void *pos4;                     // float4 or double4_32a: coords relative to frozen cell origin, w = bits
@@ -91,6 +96,10 @@ struct DevArrays {
     int32_t *fpart;                 // formed partner index or -1
     uint32_t *brk;                  // bit s set: dynamic slot s breaks
     int32_t *rx_order;              // processing order of the reactions this sweep
+    int32_t *site_list;             // sites with proposal work this reaction (compacted)
+    int32_t *list_count;            // length of site_list
+    int32_t *cont;                  // kContenders candidates per listed site (bit 30: window ambiguous)
+    int32_t *ncont;                 // contenders per site; kContenders + 1: screen overflowed
     // bookkeeping
     long long *step;                // device step counter
     uint32_t *status;
@@ -101,6 +110,9 @@ struct DevArrays {
     double *e_part;                 // per-particle energy scratch
     const RepDev *reps;
 };
+
+constexpr int kContenders = 4;
+constexpr int kCopies = 32;        // each counter is spread over this many words
 
 enum Counter {
     cScanned = 0, cInWindow, cProposals, cEdges, cSurvivors, cFormed, cBreakTested, cBroken,
@@ -245,6 +257,53 @@ __device__ __forceinline__ void warp_count(unsigned long long *ctr, unsigned lon
     } else if (v) {
         atomicAdd(ctr, v);
     }
+}
+
+// Warp-level counter reduction into spread copies: every lane of the warp
+// must call this (lanes without work pass zeros).  One atomic per warp and
+// counter, spread over kCopies words so that no single address serialises;
+// the host sums the copies.  No block barrier, so slow warps stall nobody.
+template <int N>
+__device__ __forceinline__ void warp_counts(unsigned long long *ctr, const int (&idx)[N],
+                                            const unsigned long long (&v)[N])
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned gw = (unsigned)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        unsigned long long x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+        if (lane == 0 && x) atomicAdd(&ctr[idx[k] * kCopies + (gw & (kCopies - 1))], x);
+    }
+}
+
+__device__ __forceinline__ void counter_reset(unsigned long long *ctr, int c)
+{
+    for (int k = 0; k < kCopies; ++k) ctr[c * kCopies + k] = 0ull;
+}
+
+__device__ __forceinline__ void counter_add1(unsigned long long *ctr, int c, unsigned long long v)
+{
+    ctr[c * kCopies] += v;
+}
+
+// Block-aggregated append of flagged items to a global list: every thread of
+// the block must call this; returns the slot of this thread's item (or -1).
+__device__ __forceinline__ int block_append(bool want, int32_t *count)
+{
+    __shared__ int s_base, s_cnt;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
+    int wbase = 0;
+    if (lane == 0 && m) wbase = atomicAdd(&s_cnt, __popc(m));
+    wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) s_base = s_cnt ? atomicAdd(count, s_cnt) : 0;
+    __syncthreads();
+    return want ? s_base + wbase + __popc(m & ((1u << lane) - 1u)) : -1;
 }
 
 }  // namespace snap

@@ -20,6 +20,8 @@ void launch_gather(const DevParams &P, const DevArrays &A, const DevArrays &B, b
 void launch_copyback(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, Launch L);
 void launch_nlist(const DevParams &P, const DevArrays &A, bool fp64, Launch L);
 void launch_rebuild_done(const DevArrays &A, Launch L);
+// sets a graph conditional to (*need_rebuild && status == 0)
+void launch_set_rebuild_cond(const DevArrays &A, cudaGraphConditionalHandle h, Launch L);
 
 // ---- bond sweep (Sec. II.C), exact FP64 decisions ----
 void launch_sweep_begin(const DevParams &P, const DevArrays &A, Launch L);
@@ -39,5 +41,10 @@ template <typename T> void launch_in(T *dst_sorted, const T *src_tag, const int3
 template <typename T> void launch_out(T *dst_tag, const T *src_sorted, const int32_t *rtag, long long n, Launch L);
 void launch_force_out(double *dst3, const void *force, bool fp64, const int32_t *rtag, long long n, Launch L);
 void launch_iota(int32_t *dst, long long n, Launch L);
+// mixed-mode FP32 velocities <-> tag-ordered FP64 columns
+void launch_v4_in(float4 *v4, const double *vx, const double *vy, const double *vz, const int32_t *rtag,
+                  long long n, Launch L);
+void launch_v4_out(double *vx, double *vy, double *vz, const float4 *v4, const int32_t *rtag, long long n,
+                   Launch L);
 
 }  // namespace snap

@@ -46,7 +46,7 @@ def test_init_rejects_bad_config_without_device(lib):
     ctx = C.c_void_p()
     good = dict(n=10, dt=0.005, kT=1.0, gamma=1.0, skin=0.3, bond_period=1, precision=1)
     bad_cases = [dict(dt=0.0), dict(kT=-1.0), dict(skin=0.0), dict(bond_period=0),
-                 dict(precision=7), dict(n=-1), dict(block_size=33)]
+                 dict(precision=7), dict(n=-1), dict(block_size=33), dict(block_size=512)]
     for bad in bad_cases:
         cfg = _abi.Config()
         for k, v in {**good, **bad}.items():
