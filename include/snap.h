@@ -225,6 +225,38 @@ snap_status snap_get_lifetime_hist(snap_ctx *, int64_t *bins, int32_t nbins);
 snap_status snap_get_state(snap_ctx *, void *buf, size_t *len);
 snap_status snap_set_state(snap_ctx *, const void *buf, size_t len);
 
+/* Allocation-free pair energy (this entry point has no counterpart in the
+ * paper; it is an addition for callers that cannot allocate device memory
+ * while they run: a host framework that has reserved the device's memory for
+ * its own allocator, a real-time loop that cannot afford an allocation's
+ * latency or failure, a plugin that is only handed device pointers).
+ *
+ * Computes the total Lennard-Jones/WCA pair energy (d_out[0]) and pair virial
+ * sum_pairs (-dU/dr) r (d_out[1]) of n particles by direct summation over all
+ * pairs, with the same pair potential and parameters as snap_set_types.
+ * d_pos3: device, n*3 doubles (x,y,z per particle); d_type: device, n int32;
+ * d_out: device, 2 doubles; box, sigma[ntypes], eps_pair[ntypes^2] and
+ * rcut[ntypes^2] (nullable: WCA cut) are host arrays read before the call
+ * returns.  Work is queued on `stream` (a cudaStream_t, NULL: default stream);
+ * d_out is valid once the stream reaches that point.
+ *
+ * Nothing is allocated: per-particle partial sums live in a fixed device
+ * array of 2 * SNAP_NOALLOC_MAX_N doubles (1 MiB) that every GPU loading the
+ * library holds until the process exits.  n above SNAP_NOALLOC_MAX_N (or
+ * negative), a NULL pointer, ntypes outside 1..SNAP_MAX_TYPES or a box edge
+ * <= 0 returns SNAP_ERR_ARG and queues nothing.  The first call on each device
+ * looks up the array's device address with that device current (make that
+ * first call before any stream capture); a lookup failure returns
+ * SNAP_ERR_CUDA.  All calls share the array, so calls whose work overlaps on
+ * the GPU (different streams, no ordering between them) race; calls ordered
+ * on one stream do not.  Every entry a call reads is written by that call
+ * first, so nothing needs clearing between calls. */
+#define SNAP_NOALLOC_MAX_N 65536
+snap_status snap_pair_energy_noalloc(int64_t n, const double *d_pos3, const int32_t *d_type,
+                                     const double *box, int32_t ntypes, const double *sigma,
+                                     const double *eps_pair, const double *rcut, double *d_out,
+                                     void *stream);
+
 /* Wait for the stream and return the latched device status (then cleared). */
 snap_status snap_sync(snap_ctx *);
 const char *snap_last_error(const snap_ctx *);

@@ -16,7 +16,8 @@ import numpy as np
 from . import _abi
 from ._abi import SNAP_FP64, SNAP_MIXED, SNAP_HARMONIC, SNAP_FENE
 
-__all__ = ["Snap", "SnapError", "closure", "rates_from_eps", "from_system", "SNAP_FP64",
+__all__ = ["Snap", "SnapError", "closure", "rates_from_eps", "from_system", "pair_energy_noalloc",
+           "SNAP_FP64",
            "SNAP_MIXED", "SNAP_HARMONIC", "SNAP_FENE"]
 
 
@@ -290,6 +291,23 @@ class Snap:
 
     def sync(self):
         self._check(self._lib.snap_sync(self._ctx))
+
+
+def pair_energy_noalloc(n, d_pos3, d_type, box, sigma, eps_pair, rcut=None, d_out=None, stream=None):
+    """Pair energy and virial of n particles whose positions (n*3 doubles) and
+    types (n int32) are already on the device, written to d_out (2 doubles on
+    the device).  Device pointers are integers (e.g. tensor.data_ptr()).  The
+    library allocates nothing for this call (see snap_pair_energy_noalloc)."""
+    lib = _abi.load()
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    ep = np.ascontiguousarray(eps_pair, dtype=np.float64)
+    rc = None if rcut is None else np.ascontiguousarray(rcut, dtype=np.float64)
+    code = lib.snap_pair_energy_noalloc(int(n), d_pos3, d_type, b.ctypes.data, sg.size,
+                                        sg.ctypes.data, ep.ctypes.data,
+                                        rc.ctypes.data if rc is not None else None, d_out, stream)
+    if code != 0:
+        raise SnapError(code, "snap_pair_energy_noalloc")
 
 
 def from_system(sysdef, precision="mixed", p_on0=1.0, **kw) -> Snap:

@@ -72,6 +72,7 @@ SIGNATURES = {
     "snap_get_lifetime_hist": (C.c_int, [_P, _P, C.c_int32]),
     "snap_get_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
     "snap_set_state": (C.c_int, [_P, _P, C.c_size_t]),
+    "snap_pair_energy_noalloc": (C.c_int, [C.c_int64, _P, _P, _P, C.c_int32, _P, _P, _P, _P, _P]),
     "snap_sync": (C.c_int, [_P]),
     "snap_last_error": (C.c_char_p, [_P]),
     "snap_destroy": (None, [_P]),

@@ -17,7 +17,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
           "--expt-relaxed-constexpr", "-I", str(ROOT / "include")]
 # the bond sweep and the integrator must not contract a*b+c into fma
 PER_FILE = {"exact.cu": ["-fmad=false"]}
-SOURCES = ["md.cu", "exact.cu", "io.cu", "api.cu"]
+SOURCES = ["md.cu", "exact.cu", "io.cu", "api.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:
