@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--batch-replicas", type=int, default=256,
+                    help="replicas of the batched telechelic sweep leg (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--input-cache", default="",
                     help="directory to keep the generated coordinates between invocations")
     return ap.parse_args()
@@ -67,6 +70,21 @@ def workload_config(args, n):
         "l2": "no flush: per-step working set (~0.35 GB) exceeds the 126 MB L2",
         "seed": 20260921,
     }
+
+
+def build_batch(args):
+    from synth import telechelic_sweep
+    procs = max(1, min(16, (os.cpu_count() or 1)))
+    if args.input_cache:
+        import pickle
+        p = Path(args.input_cache) / f"telechelic_sweep_{args.batch_replicas}.pkl"
+        if p.exists():
+            return pickle.loads(p.read_bytes())
+        reps = telechelic_sweep(n_replicas=args.batch_replicas, processes=procs)
+        p.parent.mkdir(parents=True, exist_ok=True)
+        p.write_bytes(pickle.dumps(reps))
+        return reps
+    return telechelic_sweep(n_replicas=args.batch_replicas, processes=procs)
 
 
 def build_system(args, seed):
@@ -167,6 +185,8 @@ def force_traffic_from_profile(n, nbar):
 
 # ----------------------------------------------------------------- snap arm
 def run_snap(args):
+    # the batched leg's inputs are generated first, in a spawned pool, before any GPU call
+    batch = build_batch(args) if args.batch_replicas > 0 else None
     import torch
     import torch.distributed as dist
     import paper_2609_21204_b300 as snap
@@ -200,13 +220,41 @@ def run_snap(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier, max_all,
-                            sum_all, stream)
+                            sum_all, stream, batch)
     if world > 1:
         dist.destroy_process_group()
 
 
+def _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream):
+    """Batched sweep leg: all replicas in one context (one graph launch per
+    20 steps), launch shape and skin from the autotuner."""
+    from paper_2609_21204_b300 import autotune
+    tune = autotune.autotune(batch, precision="mixed", steps=40, warmup=20)
+    sim = snap.from_system(batch, precision="mixed", block_size=tune["block_size"],
+                           skin=tune["skin"])
+    nb = sum(s.n for s in batch)
+    sim.step(args.warmup)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.batch_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = max_all(e0.elapsed_time(e1) / 1e3)
+    st = sim.stats()
+    sim.close()
+    return {"workload": f"{len(batch)} telechelic replicas (N log-uniform in [2k, 50k], "
+                        f"eps U[2,10] kT, kT U[0.8,1.2]), {nb} particles in one context",
+            "value": sum_all(float(nb)) * args.batch_steps / t, "unit": UNIT,
+            "ms_per_step": t * 1e3 / args.batch_steps, "steps": args.batch_steps,
+            "particles": nb, "replicas": len(batch), "n_bonds": st["n_bonds"],
+            "autotune": {k: tune[k] for k in ("block_size", "skin", "cached", "key")}}
+
+
 def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier, max_all, sum_all,
-                        stream):
+                        stream, batch=None):
     s = build_system(args, 20260921 + rank)
     n = s.n
     K, W = args.steps, args.warmup
@@ -288,6 +336,11 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
                              "phases_ms_per_step": {k: round(v, 5) for k, v in ph64.items()}}
         out["speedup_mixed_vs_fp64_plain"] = value / v64
         sim64.close()
+        sim = snap.from_system(s, precision="mixed", block_size=args.block)
+        sim.step(W)
+    if batch is not None:
+        sim.close()
+        out["batched"] = _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream)
         sim = snap.from_system(s, precision="mixed", block_size=args.block)
         sim.step(W)
     if not args.no_e2e:

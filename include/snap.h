@@ -225,6 +225,38 @@ snap_status snap_get_lifetime_hist(snap_ctx *, int64_t *bins, int32_t nbins);
 snap_status snap_get_state(snap_ctx *, void *buf, size_t *len);
 snap_status snap_set_state(snap_ctx *, const void *buf, size_t len);
 
+/* ---------------------------------------------------------------------------
+ * Learned proposal (an extension beyond the paper): a 12 -> 64 -> 64 -> 1 ReLU
+ * network scoring the candidate partners of a site, run on the tensor cores
+ * (BF16 operands, FP32 accumulation, FP32 master weights).  Features of a
+ * candidate pair (i, j), all in float32, in this order:
+ *   r, (r - r0)/r_max, [type_i == type_a], [type_i == type_b],
+ *   [type_j == type_a], [type_j == type_b], occ_i/val_i, occ_j/val_j,
+ *   [occ_i < val_i], [occ_j < val_j], coord_i/8, coord_j/8
+ * with coord_x the number of particles of the partner type of x within the
+ * reaction's window [r_min, r_max] of x.  Parameters are packed as
+ * W1[16][64] (rows 12..15 zero), b1[64], W2[64][64], b2[64], w3[64], b3.
+ * All arrays named d_* are device pointers owned by the caller.
+ * ------------------------------------------------------------------------- */
+#define SNAP_MLP_FEATURES 12
+#define SNAP_MLP_PARAMS 5313
+typedef struct snap_mlp snap_mlp;
+snap_status snap_mlp_create(snap_mlp **out, void *stream);
+snap_status snap_mlp_set_weights(snap_mlp *, const float *w);       /* host, SNAP_MLP_PARAMS */
+snap_status snap_mlp_get_weights(snap_mlp *, float *w);
+/* logits of `rows` feature rows (d_feat: rows x 12 float32) into d_logits */
+snap_status snap_mlp_forward(snap_mlp *, const float *d_feat, int64_t rows, float *d_logits);
+/* mean listwise softmax cross-entropy over `events` candidate sets (rows
+ * d_offsets[e]..d_offsets[e+1], d_offsets[0] = 0, label = index of the formed
+ * partner within its set) and its gradient (host grad, nullable). */
+snap_status snap_mlp_loss_grad(snap_mlp *, const float *d_feat, int64_t rows, const int32_t *d_offsets,
+                               const int32_t *d_labels, int64_t events, double *loss, float *grad);
+/* Adam over shuffled minibatches of batch_events events; losses[epochs] (nullable). */
+snap_status snap_mlp_train(snap_mlp *, const float *d_feat, int64_t rows, const int32_t *d_offsets,
+                           const int32_t *d_labels, int64_t events, int32_t epochs, int64_t batch_events,
+                           float lr, uint64_t seed, double *losses);
+void snap_mlp_destroy(snap_mlp *);
+
 /* Allocation-free pair energy (this entry point has no counterpart in the
  * paper; it is an addition for callers that cannot allocate device memory
  * while they run: a host framework that has reserved the device's memory for

@@ -78,6 +78,14 @@ class SweepStats(C.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class MHStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("form_attempts", "form_accepts", "break_attempts",
+                                         "break_accepts")]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class Trace(C.Structure):
     _fields_ = [("prop", C.c_void_p), ("prop_r", C.c_void_p), ("matched", C.c_void_p),
                 ("formed", C.c_void_p), ("order", C.c_void_p)]
@@ -108,6 +116,7 @@ def lib():
         _lib.orc_candidates.argtypes = [C.POINTER(Params), C.POINTER(State), C.c_int32,
                                         C.c_int64, C.c_void_p, C.c_int32]
         _lib.orc_candidates.restype = C.c_int32
+        _lib.orc_mh_sweep.argtypes = [C.POINTER(Params), C.POINTER(State), C.c_int64, C.POINTER(MHStats)]
     return _lib
 
 
@@ -267,6 +276,17 @@ class OracleSystem:
         if rc != 0:
             raise RuntimeError(f"orc_sweep failed: {rc}")
         return (st.as_dict(), tarr) if trace else st.as_dict()
+
+    def mh_sweep(self, step=None):
+        """One Metropolis–Hastings sweep with the uniform proposal."""
+        if step is None:
+            step = self.step
+        self._sync_ptrs()
+        st = MHStats()
+        rc = lib().orc_mh_sweep(C.byref(self.params), C.byref(self._state), int(step), C.byref(st))
+        if rc != 0:
+            raise RuntimeError(f"orc_mh_sweep failed: {rc}")
+        return st.as_dict()
 
     def forces(self):
         self._sync_ptrs()

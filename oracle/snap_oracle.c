@@ -545,6 +545,231 @@ int orc_sweep(const orc_params *P, orc_state *S, int64_t step, orc_sweep_stats *
     return ORC_OK;
 }
 
+/* ------------------------------------------------------- MH sweep */
+/*
+ * Metropolis–Hastings bond moves (an extension beyond the paper, used to
+ * judge a learned proposal).  Move set: an initiator i, drawn uniformly among
+ * the reactive particles of an active checkerboard cell, either forms a bond
+ * with one of its owned candidates j (free, compatible, unbonded, inside
+ * [r_min, r_max]) chosen with probability q(j | i) — here uniform — or breaks
+ * one of its owned in-window bonds chosen uniformly.  Each pair has a fixed
+ * owner (one of the two tags, by a step-independent Philox bit), so forming
+ * and breaking a pair are always initiated by the same particle.  The target
+ * weight of a bond is K exp(-U_b/kT) with K = P_on^0 / P_off (Eqs. 1, 3), so
+ *   form : min(1, K e / (b_i(s') q(j|i; s)))
+ *   break: min(1, b_i(s) q(j|i; s \ ij) / (K e))
+ * with b_i the number of owned in-window bonds of i.  Cells of one colour are
+ * more than 2 r_max apart, so their moves touch disjoint particles and
+ * candidate sets and can run in parallel.
+ */
+static int orc_owner_is(const orc_params *P, int64_t i, int64_t j)
+{
+    int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    uint32_t w[4];
+    orc_pair_draw(P, 0, ORC_MH_OWN, 0, lo, hi, w);
+    int64_t owner = (w[0] & 1u) ? hi : lo;
+    return owner == i;
+}
+
+static double orc_factor(const orc_params *P, const orc_reaction *R, double r)
+{
+    double dr = r - P->br0[R->bond_type];
+    double U = 0.5 * P->bk[R->bond_type] * dr * dr;
+    if (P->kT > 0.0) {
+        double a = U / P->kT;
+        return orc_exp(-a);
+    }
+    return (U <= 0.0) ? 1.0 : 0.0;
+}
+
+#define ORC_MH_CMAX 16
+
+/* owned candidates of i (ascending tag); 'as_free' treats i as free and
+ * 'freed' (or -1) as an unbonded free partner (the state without bond i-freed).
+ * Returns the count (may exceed ORC_MH_CMAX; only the first ones are stored). */
+static int orc_mh_candidates(const orc_params *P, const orc_state *S, const orc_grid *g,
+                             const orc_reaction *R, int64_t i, int64_t freed, int32_t *out, double *rout)
+{
+    int count = 0;
+    double rmin2 = R->r_min * R->r_min, rmax2 = R->r_max * R->r_max;
+    int64_t cand[4096];
+    int nc = 0;
+    /* gather every particle in the 27 cells (or all) first, then filter */
+    if (g->brute) {
+        for (int64_t j = 0; j < P->n && nc < 4096; ++j)
+            if (j != i) cand[nc++] = j;
+    } else {
+        int cx = (int)floor(S->x[i] / P->box[0] * g->nc[0]);
+        int cy = (int)floor(S->y[i] / P->box[1] * g->nc[1]);
+        int cz = (int)floor(S->z[i] / P->box[2] * g->nc[2]);
+        cx = ((cx % g->nc[0]) + g->nc[0]) % g->nc[0];
+        cy = ((cy % g->nc[1]) + g->nc[1]) % g->nc[1];
+        cz = ((cz % g->nc[2]) + g->nc[2]) % g->nc[2];
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int x = (cx + dx + g->nc[0]) % g->nc[0];
+                    int y = (cy + dy + g->nc[1]) % g->nc[1];
+                    int z = (cz + dz + g->nc[2]) % g->nc[2];
+                    int64_t c = ((int64_t)z * g->nc[1] + y) * g->nc[0] + x;
+                    for (int64_t j = g->head[c]; j >= 0 && nc < 4096; j = g->next[j])
+                        if (j != i) cand[nc++] = j;
+                }
+    }
+    /* ascending tag */
+    for (int a = 1; a < nc; ++a) {
+        int64_t v = cand[a];
+        int b = a - 1;
+        while (b >= 0 && cand[b] > v) { cand[b + 1] = cand[b]; --b; }
+        cand[b + 1] = v;
+    }
+    int32_t ti = S->type[i];
+    for (int k = 0; k < nc; ++k) {
+        int64_t j = cand[k];
+        int32_t tj = S->type[j];
+        if (!orc_partner_type_ok(R, ti, tj)) continue;
+        if (j != freed) {
+            if (S->occ[j] >= P->valence[tj]) continue;
+            if (orc_is_bonded(S, i, j)) continue;
+        }
+        if (!orc_owner_is(P, i, j)) continue;
+        double dx, dy, dz;
+        double r2 = orc_dist2(P, S, i, j, &dx, &dy, &dz);
+        if (r2 < rmin2 || r2 > rmax2) continue;
+        if (count < ORC_MH_CMAX) {
+            out[count] = (int32_t)j;
+            rout[count] = sqrt(r2);
+        }
+        count++;
+    }
+    return count;
+}
+
+/* owned in-window bonds of i of reaction a (ascending partner tag) */
+static int orc_mh_breakable(const orc_params *P, const orc_state *S, const orc_reaction *R, int32_t a,
+                            int64_t i, int32_t *out, double *rout)
+{
+    int count = 0;
+    double rmin2 = R->r_min * R->r_min, rmax2 = R->r_max * R->r_max;
+    for (int s = 0; s < ORC_VMAX; ++s) {
+        int32_t j = S->dp[i * ORC_VMAX + s];
+        if (j < 0 || S->drx[i * ORC_VMAX + s] != a) continue;
+        if (!orc_owner_is(P, i, j)) continue;
+        double dx, dy, dz;
+        double r2 = orc_dist2(P, S, i, j, &dx, &dy, &dz);
+        if (r2 < rmin2 || r2 > rmax2) continue;
+        out[count] = j;
+        rout[count] = sqrt(r2);
+        count++;
+    }
+    return count;
+}
+
+int orc_mh_sweep(const orc_params *P, orc_state *S, int64_t step, orc_mh_stats *st)
+{
+    if (P->nrx < 1 || P->n <= 0) return ORC_OK;
+    const int32_t a = 0;
+    const orc_reaction *R = &P->rx[0];
+    double side = 2.0 * R->r_max + 0.05;
+    int nc[3];
+    for (int d = 0; d < 3; ++d) {
+        nc[d] = (int)floor(P->box[d] / side);
+        if (nc[d] % 2) nc[d] -= 1;
+        if (nc[d] < 2) return ORC_ERR_ARG;
+    }
+    orc_grid g;
+    if (orc_grid_build(P, S, R->r_max, &g) != 0) return ORC_ERR_ARG;
+    int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    /* reactive particles per MH cell, ascending tag (tags visited in order) */
+    int64_t *cnt = (int64_t *)calloc((size_t)ncell + 1, sizeof(int64_t));
+    int64_t *cell_of = (int64_t *)malloc(sizeof(int64_t) * (size_t)P->n);
+    for (int64_t i = 0; i < P->n; ++i) {
+        int32_t t = S->type[i];
+        cell_of[i] = -1;
+        if (!((t == R->type_a || t == R->type_b) && P->valence[t] > 0)) continue;
+        int c3[3];
+        const double xs[3] = {S->x[i], S->y[i], S->z[i]};
+        for (int d = 0; d < 3; ++d) {
+            double invL = 1.0 / P->box[d];
+            int c = (int)((xs[d] * invL) * (double)nc[d]);
+            if (c < 0) c = 0;
+            if (c >= nc[d]) c = nc[d] - 1;
+            c3[d] = c;
+        }
+        int64_t c = ((int64_t)c3[2] * nc[1] + c3[1]) * nc[0] + c3[0];
+        cell_of[i] = c;
+        cnt[c + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; ++c) cnt[c + 1] += cnt[c];
+    int64_t *lst = (int64_t *)malloc(sizeof(int64_t) * (size_t)(cnt[ncell] + 1));
+    int64_t *fill = (int64_t *)calloc((size_t)ncell, sizeof(int64_t));
+    for (int64_t i = 0; i < P->n; ++i)
+        if (cell_of[i] >= 0) lst[cnt[cell_of[i]] + fill[cell_of[i]]++] = i;
+    const uint32_t colour = (uint32_t)((uint64_t)step & 7u);
+    const double K = R->p_on0 / R->p_off;
+    for (int cz = 0; cz < nc[2]; ++cz)
+        for (int cy = 0; cy < nc[1]; ++cy)
+            for (int cx = 0; cx < nc[0]; ++cx) {
+                uint32_t col = (uint32_t)(cx & 1) | ((uint32_t)(cy & 1) << 1) | ((uint32_t)(cz & 1) << 2);
+                if (col != colour) continue;
+                int64_t c = ((int64_t)cz * nc[1] + cy) * nc[0] + cx;
+                int64_t nci = cnt[c + 1] - cnt[c];
+                if (nci == 0) continue;
+                uint32_t d1[4], d2[4];
+                orc_pair_draw(P, a, ORC_MH_SEL, step, c, 0, d1);
+                orc_pair_draw(P, a, ORC_MH_ACC, step, c, 0, d2);
+                int64_t k = (int64_t)(((uint64_t)d1[0] * (uint64_t)nci) >> 32);
+                int64_t i = lst[cnt[c] + k];
+                double u = orc_u53(d2[0], d2[1]);
+                int32_t cands[ORC_MH_CMAX], bonds[ORC_VMAX];
+                double crs[ORC_MH_CMAX], brs[ORC_VMAX];
+                if ((d1[1] & 1u) == 0u) {
+                    if (st) st->form_attempts++;
+                    if (S->occ[i] >= P->valence[S->type[i]]) continue;
+                    int n = orc_mh_candidates(P, S, &g, R, i, -1, cands, crs);
+                    if (n == 0 || n > ORC_MH_CMAX) continue;
+                    int ci = (int)(((uint64_t)d1[2] * (uint64_t)n) >> 32);
+                    int64_t j = cands[ci];
+                    int bnew = orc_mh_breakable(P, S, R, a, i, bonds, brs) + 1;
+                    double e = orc_factor(P, R, crs[ci]);
+                    double ratio = ((K * e) * (double)n) / (double)bnew;
+                    if (u < ratio) {
+                        orc_slot_insert(S, i, j, a, step);
+                        orc_slot_insert(S, j, i, a, step);
+                        if (st) st->form_accepts++;
+                    }
+                } else {
+                    if (st) st->break_attempts++;
+                    int b = orc_mh_breakable(P, S, R, a, i, bonds, brs);
+                    if (b == 0) continue;
+                    int ci = (int)(((uint64_t)d1[2] * (uint64_t)b) >> 32);
+                    int64_t j = bonds[ci];
+                    int n2 = orc_mh_candidates(P, S, &g, R, i, j, cands, crs);
+                    if (n2 > ORC_MH_CMAX) continue;
+                    double e = orc_factor(P, R, brs[ci]);
+                    double ratio = (double)b / ((double)n2 * (K * e));
+                    if (u < ratio) {
+                        int64_t birth = 0;
+                        for (int s = 0; s < ORC_VMAX; ++s)
+                            if (S->dp[i * ORC_VMAX + s] == (int32_t)j) birth = S->dbirth[i * ORC_VMAX + s];
+                        if (S->life_hist && S->nhist > 0) {
+                            int64_t per = P->bond_period > 0 ? P->bond_period : 1;
+                            int64_t lb = (step - birth) / per;
+                            if (lb >= S->nhist) lb = S->nhist - 1;
+                            if (lb < 0) lb = 0;
+                            S->life_hist[lb]++;
+                        }
+                        orc_slot_remove(S, i, j);
+                        orc_slot_remove(S, j, i);
+                        if (st) st->break_accepts++;
+                    }
+                }
+            }
+    free(cnt); free(cell_of); free(lst); free(fill);
+    orc_grid_free(&g);
+    return ORC_OK;
+}
+
 /* --------------------------------------------------------------- forces */
 
 static double orc_pair_rc(const orc_params *P, int32_t ti, int32_t tj)

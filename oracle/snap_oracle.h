@@ -26,7 +26,8 @@ extern "C" {
 
 enum { ORC_HARMONIC = 0, ORC_FENE = 1 };
 /* Philox key streams (second key word carries (reaction << 8) | stream) */
-enum { ORC_FORM = 1, ORC_BREAK = 2, ORC_MATCH = 3, ORC_ORDER = 4, ORC_LANGEVIN = 5 };
+enum { ORC_FORM = 1, ORC_BREAK = 2, ORC_MATCH = 3, ORC_ORDER = 4, ORC_LANGEVIN = 5,
+       ORC_MH_SEL = 6, ORC_MH_ACC = 7, ORC_MH_OWN = 8 };
 enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_FENE = 6, ORC_ERR_NONFINITE = 7 };
 
 typedef struct {
@@ -106,6 +107,16 @@ int orc_sweep(const orc_params *P, orc_state *S, int64_t step, orc_sweep_stats *
 int orc_forces(const orc_params *P, orc_state *S, double *e_pair, double *e_bond,
                double *virial);
 int orc_run(const orc_params *P, orc_state *S, int64_t nsteps, double *ke_out);
+typedef struct {
+    int64_t form_attempts, form_accepts, break_attempts, break_accepts;
+} orc_mh_stats;
+
+/* One Metropolis–Hastings sweep with the uniform proposal (reaction 0 only):
+ * checkerboard cells of side >= 2 r_max + 0.05 (even count per axis), one
+ * initiator per active cell, form or break with the MH ratio of the
+ * owned-pair move set.  Returns ORC_ERR_ARG if the box is too small. */
+int orc_mh_sweep(const orc_params *P, orc_state *S, int64_t step, orc_mh_stats *st);
+
 /* All unordered pairs (i<j) with r < rc_ij + extra, written as tag pairs.
    Returns the count (writes at most cap pairs). */
 int64_t orc_pairs_within(const orc_params *P, const orc_state *S, double extra,

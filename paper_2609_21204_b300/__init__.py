@@ -310,9 +310,10 @@ def pair_energy_noalloc(n, d_pos3, d_type, box, sigma, eps_pair, rcut=None, d_ou
         raise SnapError(code, "snap_pair_energy_noalloc")
 
 
-def from_system(sysdef, precision="mixed", p_on0=1.0, **kw) -> Snap:
+def from_system(sysdef, precision="mixed", p_on0=1.0, skin=None, **kw) -> Snap:
     """Build a context from a `synth.System` (or any object with the same fields).
-    A list of systems becomes one batched context of independent replicas."""
+    A list of systems becomes one batched context of independent replicas.
+    `skin` overrides the systems' neighbour-list skin."""
     systems = sysdef if isinstance(sysdef, (list, tuple)) else [sysdef]
     s0 = systems[0]
     n = sum(s.n for s in systems)
@@ -321,7 +322,7 @@ def from_system(sysdef, precision="mixed", p_on0=1.0, **kw) -> Snap:
         reps = [dict(n=s.n, box=list(map(float, s.box)), kT=float(s.kT), seed=int(s.seed))
                 for s in systems]
     sim = Snap(n, s0.box, dt=s0.dt, kT=s0.kT, gamma=s0.gamma, seed=s0.seed, precision=precision,
-               bond_period=s0.bond_period, skin=s0.skin, replicas=reps, **kw)
+               bond_period=s0.bond_period, skin=s0.skin if skin is None else skin, replicas=reps, **kw)
     sim.set_types(s0.sigma, s0.eps_pair, s0.rcut)
     sim.set_valence(s0.valence)
     for i, bt in enumerate(s0.bond_types):

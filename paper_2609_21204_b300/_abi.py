@@ -72,6 +72,14 @@ SIGNATURES = {
     "snap_get_lifetime_hist": (C.c_int, [_P, _P, C.c_int32]),
     "snap_get_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
     "snap_set_state": (C.c_int, [_P, _P, C.c_size_t]),
+    "snap_mlp_create": (C.c_int, [C.POINTER(_P), _P]),
+    "snap_mlp_set_weights": (C.c_int, [_P, _P]),
+    "snap_mlp_get_weights": (C.c_int, [_P, _P]),
+    "snap_mlp_forward": (C.c_int, [_P, _P, C.c_int64, _P]),
+    "snap_mlp_loss_grad": (C.c_int, [_P, _P, C.c_int64, _P, _P, C.c_int64, C.POINTER(C.c_double), _P]),
+    "snap_mlp_train": (C.c_int, [_P, _P, C.c_int64, _P, _P, C.c_int64, C.c_int32, C.c_int64, C.c_float,
+                                 C.c_uint64, _P]),
+    "snap_mlp_destroy": (None, [_P]),
     "snap_pair_energy_noalloc": (C.c_int, [C.c_int64, _P, _P, _P, C.c_int32, _P, _P, _P, _P, _P]),
     "snap_sync": (C.c_int, [_P]),
     "snap_last_error": (C.c_char_p, [_P]),

@@ -1,0 +1,115 @@
+"""Autotuner for the launch shape and neighbour-list skin of a context.
+
+Candidates (threads per block for the particle kernels x neighbour-list skin)
+are timed on the caller's own system with CUDA events over a short run after a
+warm-up; the fastest is returned and cached in a JSON file keyed by the GPU
+name, the precision mode, the particle count (rounded to a power of two), the
+number density (rounded to 0.05) and the number of replicas.  Block size does
+not change results (every kernel is deterministic in its launch shape); the
+skin changes when the neighbour list is rebuilt and therefore the rounding of
+a trajectory, not its physics.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+from pathlib import Path
+
+DEFAULT_CACHE = Path(os.environ.get("SNAP_AUTOTUNE_CACHE",
+                                    Path.home() / ".cache" / "snap_b300" / "autotune.json"))
+BLOCKS = (64, 128, 256)
+SKINS = (0.25, 0.3, 0.4)
+
+
+def cache_key(gpu_name: str, precision: str, n: int, density: float, n_replicas: int) -> str:
+    nb = 1 << max(0, int(round(math.log2(max(n, 1)))))
+    rho = round(round(density / 0.05) * 0.05, 2)
+    return f"{gpu_name}|{precision}|N~{nb}|rho~{rho}|rep{n_replicas}"
+
+
+def load_cache(path: Path = DEFAULT_CACHE) -> dict:
+    try:
+        return json.loads(Path(path).read_text())
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: Path = DEFAULT_CACHE) -> None:
+    p = Path(path)
+    p.parent.mkdir(parents=True, exist_ok=True)
+    tmp = p.with_suffix(f".{os.getpid()}.tmp")
+    tmp.write_text(json.dumps(cache, indent=1, sort_keys=True))
+    os.replace(tmp, p)
+
+
+def choose(trials):
+    """trials: list of (config dict, ms per step); the fastest config, ties to
+    the earlier trial."""
+    best = None
+    for cfg, ms in trials:
+        if ms is None or not math.isfinite(ms):
+            continue
+        if best is None or ms < best[1]:
+            best = (cfg, ms)
+    if best is None:
+        raise RuntimeError("no autotune trial succeeded")
+    return dict(best[0], ms_per_step=best[1])
+
+
+def autotune(systems, precision="mixed", blocks=BLOCKS, skins=SKINS, steps=60, warmup=30,
+             cache_path: Path = DEFAULT_CACHE, use_cache=True, timer=None):
+    """Pick (block_size, skin) for these systems.  `systems` is one synth
+    System or a list of them (a batched context).  `timer(cfg) -> ms/step` may
+    replace the GPU timing (used by the host-side tests)."""
+    systems = systems if isinstance(systems, (list, tuple)) else [systems]
+    n = sum(s.n for s in systems)
+    vol = sum(float(s.box[0] * s.box[1] * s.box[2]) for s in systems)
+    gpu = "cpu"
+    if timer is None:
+        import torch
+        gpu = torch.cuda.get_device_name()
+    key = cache_key(gpu, precision, n, n / vol, len(systems))
+    cache = load_cache(cache_path) if use_cache else {}
+    if use_cache and key in cache:
+        return dict(cache[key], cached=True, key=key)
+    if timer is None:
+        timer = _gpu_timer(systems, precision, steps, warmup)
+    trials = []
+    for skin in skins:
+        for block in blocks:
+            cfg = dict(block_size=int(block), skin=float(skin))
+            try:
+                ms = timer(cfg)
+            except Exception:
+                ms = None
+            trials.append((cfg, ms))
+    best = choose(trials)
+    best["trials"] = [dict(c, ms_per_step=m) for c, m in trials]
+    if use_cache:
+        cache[key] = best
+        save_cache(cache, cache_path)
+    return dict(best, cached=False, key=key)
+
+
+def _gpu_timer(systems, precision, steps, warmup):
+    import torch
+    from . import from_system
+
+    def run(cfg):
+        sim = from_system(systems if len(systems) > 1 else systems[0], precision=precision,
+                          block_size=cfg["block_size"], skin=cfg["skin"])
+        try:
+            sim.step(warmup)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            stream = torch.cuda.current_stream()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sim.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / steps
+        finally:
+            sim.close()
+    return run

@@ -17,7 +17,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
           "--expt-relaxed-constexpr", "-I", str(ROOT / "include")]
 # the bond sweep and the integrator must not contract a*b+c into fma
 PER_FILE = {"exact.cu": ["-fmad=false"]}
-SOURCES = ["md.cu", "exact.cu", "io.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["md.cu", "exact.cu", "io.cu", "api.cu", "noalloc.cu", "mlp.cu", "mlp_api.cu"]
 
 
 def nvcc() -> str:
@@ -30,7 +30,8 @@ def nvcc() -> str:
 def _stale(obj: Path, src: Path) -> bool:
     if not obj.exists():
         return True
-    deps = [src, CSRC / "snap_device.cuh", CSRC / "snap_kernels.h", ROOT / "include" / "snap.h"]
+    deps = [src, CSRC / "snap_device.cuh", CSRC / "snap_kernels.h", CSRC / "snap_mlp.h",
+            ROOT / "include" / "snap.h"]
     return obj.stat().st_mtime < max(d.stat().st_mtime for d in deps if d.exists())
 
 

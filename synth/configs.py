@@ -161,12 +161,12 @@ def colloid_linker(seed: int = 20260921, n_c: int = 200_000, n_l: int = 800_000,
         kT=kT, seed=seed, meta=dict(eta=eta, rho=n / V, n_c=n_c, n_l=n_l))
 
 
-def telechelic_sweep(seed: int = 20260921, n_replicas: int = 256, n_lo: int = 2000,
-                     n_hi: int = 50000, rho: float = 0.3):
-    """Batched parameter sweep: telechelic replicas with total bead count drawn
-    log-uniform in [n_lo, n_hi], ε uniform in [2, 10] kT and kT uniform in
-    [0.8, 1.2].  The chain:crosslinker ratio follows the 2000 × 12 + 4000 system.
-    Replica r uses seed + r."""
+def telechelic_sweep_specs(seed: int = 20260921, n_replicas: int = 256, n_lo: int = 2000,
+                           n_hi: int = 50000, rho: float = 0.3):
+    """Keyword arguments of `telechelic` for each replica of the batched sweep:
+    total bead count log-uniform in [n_lo, n_hi], ε uniform in [2, 10] kT, kT
+    uniform in [0.8, 1.2]; chain:crosslinker ratio of the 2000 × 12 + 4000
+    system; replica r seeded seed + r."""
     rng = np.random.default_rng(seed)
     ns = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=n_replicas))
     epss = rng.uniform(2.0, 10.0, size=n_replicas)
@@ -176,9 +176,25 @@ def telechelic_sweep(seed: int = 20260921, n_replicas: int = 256, n_lo: int = 20
         n = int(round(ns[r]))
         n_chains = max(1, int(round(n * 2000 / 28000)))
         n_x = max(1, n - 12 * n_chains)
-        out.append(telechelic(seed=seed + r, n_chains=n_chains, n_x=n_x, rho=rho,
-                              eps=float(epss[r]), kT=float(kts[r])))
+        out.append(dict(seed=seed + r, n_chains=n_chains, n_x=n_x, rho=rho,
+                        eps=float(epss[r]), kT=float(kts[r])))
     return out
+
+
+def _telechelic_kw(kw):
+    return telechelic(**kw)
+
+
+def telechelic_sweep(seed: int = 20260921, n_replicas: int = 256, n_lo: int = 2000,
+                     n_hi: int = 50000, rho: float = 0.3, processes: int = 1):
+    """Batched parameter sweep of telechelic replicas (see telechelic_sweep_specs).
+    With processes > 1 the replicas are generated in a spawned process pool."""
+    specs = telechelic_sweep_specs(seed, n_replicas, n_lo, n_hi, rho)
+    if processes > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            return pool.map(_telechelic_kw, specs)
+    return [telechelic(**kw) for kw in specs]
 
 
 def frozen_pairs(seed: int = 1, n_pairs: int = 200, r: float = 1.1, spacing: float = 4.0,

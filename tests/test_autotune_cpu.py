@@ -1,0 +1,35 @@
+"""Host-side logic of the autotuner (no GPU): cache keys, selection, caching."""
+from paper_2609_21204_b300 import autotune as at
+from synth import assoc_ab
+
+
+def test_cache_key_buckets():
+    k1 = at.cache_key("B300", "mixed", 1_000_000, 1.59, 1)
+    k2 = at.cache_key("B300", "mixed", 1_040_000, 1.61, 1)
+    assert k1 == k2
+    assert at.cache_key("B300", "fp64", 1_000_000, 1.59, 1) != k1
+    assert at.cache_key("B300", "mixed", 1_000_000, 1.59, 256) != k1
+
+
+def test_choose_fastest_and_skips_failures():
+    trials = [({"block_size": 64, "skin": 0.3}, 0.5), ({"block_size": 128, "skin": 0.3}, None),
+              ({"block_size": 256, "skin": 0.4}, 0.4), ({"block_size": 128, "skin": 0.4}, 0.4)]
+    best = at.choose(trials)
+    assert best["block_size"] == 256 and best["skin"] == 0.4 and best["ms_per_step"] == 0.4
+
+
+def test_autotune_with_fake_timer_caches(tmp_path):
+    s = assoc_ab(seed=1, n_a=50, n_b=50)
+    calls = []
+
+    def timer(cfg):
+        calls.append(cfg)
+        return 1.0 + abs(cfg["skin"] - 0.3) + cfg["block_size"] / 1000.0
+
+    path = tmp_path / "tune.json"
+    r = at.autotune(s, timer=timer, cache_path=path)
+    assert r["block_size"] == 64 and r["skin"] == 0.3 and not r["cached"]
+    assert len(calls) == len(at.BLOCKS) * len(at.SKINS)
+    r2 = at.autotune(s, timer=timer, cache_path=path)
+    assert r2["cached"] and r2["block_size"] == 64
+    assert len(calls) == len(at.BLOCKS) * len(at.SKINS)
