@@ -110,6 +110,9 @@ typedef struct {
     int64_t proposals, edges, survivors, formed, break_tested, broken;
     int64_t nlist_builds;    /* neighbour-list rebuilds so far */
     int64_t nlist_entries;   /* neighbour entries written by the last rebuild */
+    int64_t mh_form_attempts, mh_form_accepts;    /* Metropolis-Hastings moves so far */
+    int64_t mh_break_attempts, mh_break_accepts;
+    int64_t events_logged;   /* bond-formation events offered to the event log */
     int32_t nlist_capacity;  /* current neighbours-per-particle capacity */
     int32_t status;          /* latched device status (snap_status value) */
 } snap_stats;
@@ -256,6 +259,35 @@ snap_status snap_mlp_train(snap_mlp *, const float *d_feat, int64_t rows, const 
                            const int32_t *d_labels, int64_t events, int32_t epochs, int64_t batch_events,
                            float lr, uint64_t seed, double *losses);
 void snap_mlp_destroy(snap_mlp *);
+
+/* Metropolis-Hastings bond moves instead of the DyBond sweep (an extension
+ * beyond the paper).  mode 0: DyBond sweep (default); 1: MH with the uniform
+ * proposal; 2: MH with the learned proposal
+ * q = (1 - eps_u) softmax(mlp) + eps_u / n.  Move set: checkerboard cells of
+ * side >= 2 r_max + 0.05 (an even number per axis, colour = step mod 8), one
+ * initiator per active cell drawn uniformly among its reactive particles,
+ * form (with one of its owned candidates) or break (one of its owned in-window
+ * bonds) with probability 1/2, accepted with the Metropolis-Hastings ratio for
+ * the bond weight K exp(-U_b/kT), K = p_on0 / p_off.  Needs exactly one
+ * reaction and one system; the network must outlive the context's use of it. */
+snap_status snap_set_mh(snap_ctx *, int32_t mode, const struct snap_mlp *mlp, double eps_u);
+/* One MH sweep at the current positions (step counter unchanged). */
+snap_status snap_mh_sweep(snap_ctx *);
+/* Sets the step counter (keys every Philox draw and the birth step of new
+ * bonds; the MH colour is step mod 8).  step < 0: SNAP_ERR_ARG. */
+snap_status snap_set_step(snap_ctx *, int64_t step);
+/* Record bond-formation events of the DyBond sweep (training data for the
+ * proposal network): for every site whose own proposal formed a bond, the
+ * features of all its candidates (at most 16) and the index of the partner.
+ * capacity 0 turns logging off; events past the capacity are counted in
+ * snap_stats.events_logged but not stored.  snap_get_events copies them out
+ * compactly (host buffers): feat[rows][12], offsets[events + 1],
+ * labels[events]; *n_events / *n_rows are always set, and buffers smaller
+ * than that return SNAP_ERR_ARG with nothing copied (a size query);
+ * clear != 0 empties the log afterwards. */
+snap_status snap_log_events(snap_ctx *, int64_t capacity);
+snap_status snap_get_events(snap_ctx *, float *feat, int32_t *offsets, int32_t *labels, int64_t cap_events,
+                            int64_t cap_rows, int64_t *n_events, int64_t *n_rows, int32_t clear);
 
 /* Allocation-free pair energy (this entry point has no counterpart in the
  * paper; it is an addition for callers that cannot allocate device memory

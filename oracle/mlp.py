@@ -110,3 +110,43 @@ def bf16_round(a):
     u = a.view(np.uint32).astype(np.uint64)
     r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
     return r.astype(np.uint32).view(np.float32)
+
+
+def forward_bf16(theta, X):
+    """Forward pass with the operands of both matrix products rounded to
+    BF16 as a BF16 tensor-core evaluation takes them (inputs, W1, W2 and the
+    first hidden layer); biases, w3 and every sum exact in FP64."""
+    p = unpack(theta)
+    rb = lambda a: bf16_round(a).astype(np.float64)
+    Xp = np.zeros((X.shape[0], KPAD))
+    Xp[:, :X.shape[1]] = X
+    Xb, W1b, W2b = rb(Xp), rb(p["W1"]), rb(p["W2"])
+    Z1 = Xb @ W1b + p["b1"]
+    H1b = rb(np.maximum(Z1, 0.0))
+    Z2 = H1b @ W2b + p["b2"]
+    H2 = np.maximum(Z2, 0.0)
+    y = H2 @ p["w3"] + p["b3"][0]
+    return y, (Xb, W2b, Z1, H1b, Z2, H2)
+
+
+def loss_and_grad_bf16(theta, X, offsets, labels):
+    """Loss and gradient of forward_bf16 with the back-propagated dZ2 and dZ1
+    rounded to BF16 as well (the operands of the backward products); the
+    listwise loss and every sum exact in FP64.  It is the reference for what
+    BF16 operands alone cost in accuracy: a device evaluation differs from it
+    only by its FP32 summation order."""
+    p = unpack(theta)
+    rb = lambda a: bf16_round(a).astype(np.float64)
+    y, (Xb, W2b, Z1, H1b, Z2, H2) = forward_bf16(theta, X)
+    loss, dy = listwise_loss(y, offsets, labels)
+    g = {}
+    g["w3"] = H2.T @ dy
+    g["b3"] = np.array([dy.sum()])
+    dZ2b = rb(np.outer(dy, p["w3"]) * (Z2 > 0))
+    g["W2"] = H1b.T @ dZ2b
+    g["b2"] = dZ2b.sum(0)
+    dZ1b = rb((dZ2b @ W2b.T) * (Z1 > 0))
+    g["W1"] = Xb.T @ dZ1b
+    g["W1"][NF:] = 0.0
+    g["b1"] = dZ1b.sum(0)
+    return loss, y, pack(g)

@@ -16,7 +16,7 @@ import numpy as np
 from . import _abi
 from ._abi import SNAP_FP64, SNAP_MIXED, SNAP_HARMONIC, SNAP_FENE
 
-__all__ = ["Snap", "SnapError", "closure", "rates_from_eps", "from_system", "pair_energy_noalloc",
+__all__ = ["Snap", "Mlp", "SnapError", "closure", "rates_from_eps", "from_system", "pair_energy_noalloc",
            "SNAP_FP64",
            "SNAP_MIXED", "SNAP_HARMONIC", "SNAP_FENE"]
 
@@ -291,6 +291,102 @@ class Snap:
 
     def sync(self):
         self._check(self._lib.snap_sync(self._ctx))
+
+    # -- Metropolis-Hastings moves and the event log -------------------------
+    def set_mh(self, mode, mlp=None, eps_u=0.05):
+        """mode 0: DyBond sweep; 1: MH, uniform proposal; 2: MH, learned proposal."""
+        self._mlp = mlp  # the network must outlive its use by this context
+        self._check(self._lib.snap_set_mh(self._ctx, int(mode), mlp._h if mlp is not None else None,
+                                          float(eps_u)))
+
+    def mh_sweep(self):
+        self._check(self._lib.snap_mh_sweep(self._ctx))
+
+    def set_step(self, step):
+        self._check(self._lib.snap_set_step(self._ctx, int(step)))
+
+    def log_events(self, capacity):
+        self._check(self._lib.snap_log_events(self._ctx, int(capacity)))
+
+    def get_events(self, clear=True):
+        """Logged bond-formation events: (features[rows, 12] float32,
+        offsets[events + 1] int32, labels[events] int32)."""
+        ne, nr = C.c_int64(0), C.c_int64(0)
+        code = self._lib.snap_get_events(self._ctx, None, None, None, 0, 0, C.byref(ne), C.byref(nr), 0)
+        if code not in (0, 1):
+            self._check(code)
+        feat = np.zeros((max(nr.value, 1), 12), dtype=np.float32)
+        off = np.zeros(ne.value + 1, dtype=np.int32)
+        lab = np.zeros(max(ne.value, 1), dtype=np.int32)
+        self._check(self._lib.snap_get_events(self._ctx, feat.ctypes.data, off.ctypes.data, lab.ctypes.data,
+                                              ne.value, nr.value, C.byref(ne), C.byref(nr), int(clear)))
+        return feat[: nr.value], off[: ne.value + 1], lab[: ne.value]
+
+
+class Mlp:
+    """The 12 -> 64 -> 64 -> 1 proposal network on the tensor cores.  Device
+    arrays are passed as integer pointers (e.g. torch tensor.data_ptr())."""
+
+    NPARAM = 5313
+
+    def __init__(self, weights=None, stream=None):
+        self._lib = _abi.load()
+        self._h = C.c_void_p()
+        s = stream if stream is not None else 0
+        code = self._lib.snap_mlp_create(C.byref(self._h), C.c_void_p(s))
+        if code != 0:
+            raise SnapError(code, "snap_mlp_create")
+        if weights is not None:
+            self.set_weights(weights)
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == self.NPARAM
+        code = self._lib.snap_mlp_set_weights(self._h, w.ctypes.data)
+        if code != 0:
+            raise SnapError(code, "snap_mlp_set_weights")
+
+    def weights(self):
+        w = np.zeros(self.NPARAM, dtype=np.float32)
+        code = self._lib.snap_mlp_get_weights(self._h, w.ctypes.data)
+        if code != 0:
+            raise SnapError(code, "snap_mlp_get_weights")
+        return w
+
+    def forward(self, d_feat, rows, d_logits):
+        code = self._lib.snap_mlp_forward(self._h, d_feat, int(rows), d_logits)
+        if code != 0:
+            raise SnapError(code, "snap_mlp_forward")
+
+    def loss_grad(self, d_feat, rows, d_offsets, d_labels, events):
+        loss = C.c_double(0.0)
+        g = np.zeros(self.NPARAM, dtype=np.float32)
+        code = self._lib.snap_mlp_loss_grad(self._h, d_feat, int(rows), d_offsets, d_labels, int(events),
+                                            C.byref(loss), g.ctypes.data)
+        if code != 0:
+            raise SnapError(code, "snap_mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, d_feat, rows, d_offsets, d_labels, events, epochs=10, batch_events=4096, lr=1e-3,
+              seed=0):
+        losses = np.zeros(int(epochs))
+        code = self._lib.snap_mlp_train(self._h, d_feat, int(rows), d_offsets, d_labels, int(events),
+                                        int(epochs), int(batch_events), float(lr), int(seed),
+                                        losses.ctypes.data)
+        if code != 0:
+            raise SnapError(code, "snap_mlp_train")
+        return losses
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.snap_mlp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def pair_energy_noalloc(n, d_pos3, d_type, box, sigma, eps_pair, rcut=None, d_out=None, stream=None):

@@ -33,7 +33,8 @@ class Stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in (
         "step", "n_bonds", "sweeps", "formed_total", "broken_total", "scanned", "in_window",
         "proposals", "edges", "survivors", "formed", "break_tested", "broken",
-        "nlist_builds", "nlist_entries")] + [("nlist_capacity", C.c_int32), ("status", C.c_int32)]
+        "nlist_builds", "nlist_entries", "mh_form_attempts", "mh_form_accepts", "mh_break_attempts",
+        "mh_break_accepts", "events_logged")] + [("nlist_capacity", C.c_int32), ("status", C.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -72,6 +73,12 @@ SIGNATURES = {
     "snap_get_lifetime_hist": (C.c_int, [_P, _P, C.c_int32]),
     "snap_get_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
     "snap_set_state": (C.c_int, [_P, _P, C.c_size_t]),
+    "snap_set_mh": (C.c_int, [_P, C.c_int32, _P, C.c_double]),
+    "snap_mh_sweep": (C.c_int, [_P]),
+    "snap_set_step": (C.c_int, [_P, C.c_int64]),
+    "snap_log_events": (C.c_int, [_P, C.c_int64]),
+    "snap_get_events": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int64, C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_int64), C.c_int32]),
     "snap_mlp_create": (C.c_int, [C.POINTER(_P), _P]),
     "snap_mlp_set_weights": (C.c_int, [_P, _P]),
     "snap_mlp_get_weights": (C.c_int, [_P, _P]),

@@ -10,6 +10,7 @@
 
 #include "../../include/snap.h"
 #include "snap_kernels.h"
+#include "snap_mlp.h"
 
 using namespace snap;
 
@@ -66,6 +67,13 @@ struct snap_ctx {
     int32_t *d_bsum = nullptr;
     double *d_red = nullptr;
     std::vector<void *> allocs;
+    // Metropolis–Hastings mode and event log
+    int mh_mode = 0;                 // 0: DyBond sweep, 1: MH uniform, 2: MH learned
+    const snap_mlp *mlp = nullptr;
+    double mh_eps = 0.05;
+    int mh_nc[3] = {0, 0, 0};
+    bool mh_alloc = false;
+    long long ev_cap = 0;
     // graphs
     cudaGraphExec_t graph = nullptr;
     bool graph_dirty = true;
@@ -166,6 +174,7 @@ snap_status upload_reps(snap_ctx *c)
         D.noise_c = std::sqrt(((2.0 * c->cfg.gamma) * R.kT) / c->cfg.dt);
         D.key0 = (uint32_t)(R.seed & 0xFFFFFFFFull);
         D.key1hi = (uint32_t)(((R.seed >> 32) & 0xFFFFull) << 16);
+        for (int d = 0; d < 3; ++d) D.mh_nc[d] = c->mh_nc[d];
         for (size_t a = 0; a < c->rx.size(); ++a) {
             D.p_on0[a] = c->rep_pon[a][r];
             D.p_off[a] = c->rep_poff[a][r];
@@ -234,6 +243,10 @@ void fill_params(snap_ctx *c)
     P.nrep = (int)c->reps.size();
     P.screen = c->fp64 ? 0 : 1;
     P.ncell = c->ncell_total;
+    P.mh_cells = c->mh_mode ? c->mh_nc[0] * c->mh_nc[1] * c->mh_nc[2] : 0;
+    P.mh_moves = c->mh_mode ? P.mh_cells / 8 : 0;
+    P.mh_eps = (float)c->mh_eps;
+    P.log_events = c->ev_cap > 0 ? 1 : 0;
 }
 
 // everything that depends on the model (cut-offs -> cell grids -> capacities)
@@ -320,6 +333,10 @@ void seq_sweep(snap_ctx *c, bool forced)
 {
     if (c->rx.empty()) return;
     const Launch L = launch(c);
+    if (c->mh_mode) {
+        launch_mh_sweep(c->P, c->A, forced, c->mh_mode == 2 ? &c->mlp->dev : nullptr, c->A.mh_bsum, L);
+        return;
+    }
     if (forced) launch_sweep_begin_forced(c->P, c->A, L);
     else launch_sweep_begin(c->P, c->A, L);
     for (int s = 0; s < (int)c->rx.size(); ++s) {
@@ -1292,6 +1309,11 @@ extern "C" snap_status snap_get_stats(snap_ctx *c, snap_stats *out)
     out->broken = (int64_t)h[cBroken];
     out->nlist_builds = (int64_t)h[cBuilds];
     out->nlist_entries = (int64_t)h[cNlistEntries];
+    out->mh_form_attempts = (int64_t)h[cMhFormAtt];
+    out->mh_form_accepts = (int64_t)h[cMhFormAcc];
+    out->mh_break_attempts = (int64_t)h[cMhBreakAtt];
+    out->mh_break_accepts = (int64_t)h[cMhBreakAcc];
+    out->events_logged = (int64_t)h[cEvents];
     out->nlist_capacity = c->nbr_cap;
     out->status = (int32_t)status_to_code(c, st);
     return SNAP_OK;
@@ -1422,6 +1444,146 @@ extern "C" snap_status snap_set_state(snap_ctx *c, const void *buf, size_t len)
     if ((s = counters_out(c, h)) != SNAP_OK) return s;
     c->bonds_base = (int64_t)b.size() - (int64_t)h[cFormedTotal] + (int64_t)h[cBrokenTotal];
     return set_need_rebuild(c);
+}
+
+extern "C" snap_status snap_set_mh(snap_ctx *c, int32_t mode, const snap_mlp *mlp, double eps_u)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (mode < 0 || mode > 2) return fail(c, SNAP_ERR_ARG, "mode must be 0, 1 or 2");
+    if (mode == 2 && !mlp) return fail(c, SNAP_ERR_ARG, "the learned proposal needs a network");
+    if (!(eps_u > 0.0 && eps_u <= 1.0)) return fail(c, SNAP_ERR_ARG, "eps_u must lie in (0, 1]");
+    if (mode != 0) {
+        if (c->rx.size() != 1 || c->reps.size() != 1)
+            return fail(c, SNAP_ERR_ARG, "Metropolis-Hastings mode supports one reaction in one system");
+        const double side = 2.0 * c->rx[0].rmax + 0.05;
+        int nc[3];
+        for (int d = 0; d < 3; ++d) {
+            nc[d] = (int)std::floor(c->reps[0].L[d] / side);
+            if (nc[d] % 2) nc[d] -= 1;
+            if (nc[d] < 2) return fail(c, SNAP_ERR_ARG, "box too small for Metropolis-Hastings cells (2 per axis)");
+        }
+        const int cells = nc[0] * nc[1] * nc[2];
+        if (!c->mh_alloc || cells != c->mh_nc[0] * c->mh_nc[1] * c->mh_nc[2]) {
+            DevArrays &A = c->A;
+            const size_t n = (size_t)std::max<int64_t>(c->n, 1);
+            const size_t moves = (size_t)std::max(cells / 8, 1);
+            const int nb = (cells + 4095) / 4096 + 1;
+            for (void *p : {(void *)A.mh_key, (void *)A.mh_count, (void *)A.mh_start, (void *)A.mh_cursor,
+                            (void *)A.mh_order, (void *)A.mh_bsum, (void *)A.mh_gate, (void *)A.mv_type,
+                            (void *)A.mv_i, (void *)A.mv_j, (void *)A.mv_n, (void *)A.mv_b, (void *)A.mv_c,
+                            (void *)A.mv_cand, (void *)A.mv_r, (void *)A.mv_feat, (void *)A.mv_logit})
+                dfree(c, p);
+            bool ok = alloc_arr(c, A.mh_key, n) && alloc_arr(c, A.mh_count, cells) &&
+                      alloc_arr(c, A.mh_start, cells + 1) && alloc_arr(c, A.mh_cursor, cells) &&
+                      alloc_arr(c, A.mh_order, n) && alloc_arr(c, A.mh_bsum, nb + 1) && alloc_arr(c, A.mh_gate, 1) &&
+                      alloc_arr(c, A.mv_type, moves) && alloc_arr(c, A.mv_i, moves) && alloc_arr(c, A.mv_j, moves) &&
+                      alloc_arr(c, A.mv_n, moves) && alloc_arr(c, A.mv_b, moves) && alloc_arr(c, A.mv_c, moves) &&
+                      alloc_arr(c, A.mv_cand, moves * kMhCand) && alloc_arr(c, A.mv_r, moves * kMhCand) &&
+                      alloc_arr(c, A.mv_feat, moves * kMhCand * kMlpFeatures) &&
+                      alloc_arr(c, A.mv_logit, moves * kMhCand);
+            if (!ok) return fail(c, SNAP_ERR_OOM, "Metropolis-Hastings arrays");
+            const int32_t one = 1;
+            CUDA_TRY(c, cudaMemsetAsync(A.mh_count, 0, sizeof(int32_t) * cells, c->stream));
+            CUDA_TRY(c, cudaMemsetAsync(A.mh_cursor, 0, sizeof(int32_t) * cells, c->stream));
+            CUDA_TRY(c, cudaMemsetAsync(A.mv_feat, 0, sizeof(float) * moves * kMhCand * kMlpFeatures, c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(A.mh_gate, &one, sizeof one, cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            c->mh_alloc = true;
+        }
+        for (int d = 0; d < 3; ++d) c->mh_nc[d] = nc[d];
+    }
+    c->mh_mode = mode;
+    c->mlp = mlp;
+    c->mh_eps = eps_u;
+    fill_params(c);
+    c->graph_dirty = true;
+    return upload_reps(c);
+}
+
+extern "C" snap_status snap_mh_sweep(snap_ctx *c)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (!c->mh_mode) return fail(c, SNAP_ERR_STATE, "Metropolis-Hastings mode is off (snap_set_mh)");
+    return run_with_retry(c, [&] {
+        seq_rebuild(c);
+        seq_sweep(c, true);
+    });
+}
+
+extern "C" snap_status snap_set_step(snap_ctx *c, int64_t step)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (step < 0) return fail(c, SNAP_ERR_ARG, "step must be >= 0");
+    const long long v = (long long)step;
+    CUDA_TRY(c, cudaMemcpyAsync(c->A.step, &v, sizeof v, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_log_events(snap_ctx *c, int64_t capacity)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (capacity < 0 || capacity > (int64_t)INT32_MAX / kMhCand) return fail(c, SNAP_ERR_ARG, "bad capacity");
+    DevArrays &A = c->A;
+    for (void *p : {(void *)A.ev_feat, (void *)A.ev_n, (void *)A.ev_label, (void *)A.ev_count}) dfree(c, p);
+    A.ev_feat = nullptr;
+    A.ev_n = A.ev_label = A.ev_count = nullptr;
+    A.ev_cap = 0;
+    c->ev_cap = 0;
+    if (capacity > 0) {
+        bool ok = alloc_arr(c, A.ev_feat, (size_t)capacity * kMhCand * kMlpFeatures) &&
+                  alloc_arr(c, A.ev_n, capacity) && alloc_arr(c, A.ev_label, capacity) && alloc_arr(c, A.ev_count, 1);
+        if (!ok) return fail(c, SNAP_ERR_OOM, "event log");
+        CUDA_TRY(c, cudaMemsetAsync(A.ev_count, 0, sizeof(int32_t), c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        A.ev_cap = (int32_t)capacity;
+        c->ev_cap = capacity;
+    }
+    fill_params(c);
+    c->graph_dirty = true;
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_get_events(snap_ctx *c, float *feat, int32_t *offsets, int32_t *labels, int64_t cap_events,
+                                       int64_t cap_rows, int64_t *n_events, int64_t *n_rows, int32_t clear)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (c->ev_cap == 0) return fail(c, SNAP_ERR_STATE, "event logging is off (snap_log_events)");
+    int32_t cnt = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&cnt, c->A.ev_count, sizeof cnt, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const long long ne = std::min<long long>(cnt, c->ev_cap);
+    std::vector<int32_t> nv(ne), lv(ne);
+    std::vector<float> fv((size_t)ne * kMhCand * kMlpFeatures);
+    if (ne > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(nv.data(), c->A.ev_n, sizeof(int32_t) * ne, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(lv.data(), c->A.ev_label, sizeof(int32_t) * ne, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(fv.data(), c->A.ev_feat, sizeof(float) * fv.size(), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    long long rows = 0;
+    for (long long e = 0; e < ne; ++e) rows += nv[e];
+    if (n_events) *n_events = ne;
+    if (n_rows) *n_rows = rows;
+    if (ne > cap_events || rows > cap_rows) return fail(c, SNAP_ERR_ARG, "event buffers too small");
+    if (ne > 0 && (!feat || !offsets || !labels)) return fail(c, SNAP_ERR_ARG, "NULL event buffer");
+    long long r = 0;
+    if (offsets) offsets[0] = 0;
+    for (long long e = 0; e < ne; ++e) {
+        std::memcpy(feat + r * kMlpFeatures, fv.data() + (size_t)e * kMhCand * kMlpFeatures,
+                    sizeof(float) * kMlpFeatures * nv[e]);
+        r += nv[e];
+        offsets[e + 1] = (int32_t)r;
+        labels[e] = lv[e];
+    }
+    if (clear) CUDA_TRY(c, cudaMemsetAsync(c->A.ev_count, 0, sizeof(int32_t), c->stream));
+    return SNAP_OK;
 }
 
 extern "C" snap_status snap_sync(snap_ctx *c)

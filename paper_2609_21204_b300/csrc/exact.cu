@@ -609,6 +609,7 @@ void sweep_reaction(const DevParams &P, const DevArrays &A, int slot, Launch L)
     }
     k_match<FORCED><<<gl, 256, 0, L.stream>>>(P, A, slot);
     k_accept<FORCED><<<gl, 256, 0, L.stream>>>(P, A, slot);
+    if (P.log_events) launch_log_events(P, A, slot, FORCED, L);
     k_break<FORCED><<<g, L.block, 0, L.stream>>>(P, A, slot);
     k_apply<FORCED><<<g, L.block, 0, L.stream>>>(P, A, slot);
 }

@@ -556,6 +556,16 @@ void launch_cell_scan(const DevArrays &A, int32_t *block_sums, int ncell, Launch
                                                            A.need_rebuild, A.status);
 }
 
+void launch_scan(const int32_t *in, int32_t *out, int32_t *bsum, int n, const int32_t *gate, const uint32_t *status,
+                 Launch L)
+{
+    if (n <= 0) return;
+    const int nb = (n + kScanTile - 1) / kScanTile;
+    k_scan_tiles<<<nb, kScanThreads, 0, L.stream>>>(in, out, bsum, n, gate, status);
+    k_scan_sums<<<1, kScanThreads, 0, L.stream>>>(bsum, nb, gate, status);
+    k_scan_add<<<grid_for(n, 256), 256, 0, L.stream>>>(out, bsum, n, nb, gate, status);
+}
+
 void launch_scatter(const DevParams &P, const DevArrays &A, Launch L)
 {
     if (P.n == 0) return;

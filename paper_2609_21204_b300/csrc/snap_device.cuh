@@ -18,7 +18,8 @@ constexpr int kVmax = 4;   // dynamic-bond slots per particle
 constexpr int kSmax = 4;   // static-bond slots per particle
 
 // Philox key streams: key word 1 = ((seed >> 32) & 0xFFFF) << 16 | reaction << 8 | stream
-enum Stream : uint32_t { kForm = 1, kBreak = 2, kMatch = 3, kOrder = 4, kLangevin = 5 };
+enum Stream : uint32_t { kForm = 1, kBreak = 2, kMatch = 3, kOrder = 4, kLangevin = 5,
+                         kMhSel = 6, kMhAcc = 7, kMhOwn = 8 };
 
 // status bits latched by kernels (mapped to snap_status on the host)
 enum StatusBit : uint32_t {
@@ -54,6 +55,9 @@ struct DevParams {
     int32_t nrep;
     int32_t screen;         // mixed mode: FP32 pre-screen of the proposal test, FP32 velocities
     int32_t ncell;          // cells over all replicas; sort keys are type * ncell + cell
+    int32_t mh_cells, mh_moves;   // MH checkerboard cells and active cells per sweep
+    float mh_eps;           // weight of the uniform component of the learned proposal
+    int32_t log_events;     // record bond-formation events in the plain sweep
 };
 
 struct RepDev {
@@ -67,6 +71,8 @@ struct RepDev {
     uint32_t key0, key1hi;  // Philox key words derived from the seed
     double p_on0[kMaxRx], p_off[kMaxRx];
     unsigned long long off_thresh[kMaxRx];   // ceil(p_off * 2^53): break iff 53-bit draw < this
+    int32_t mh_nc[3];                        // Metropolis–Hastings checkerboard cells per axis (even)
+    int32_t pad1;
 };
 
 // Device arrays (sorted particle order unless stated).
@@ -109,14 +115,26 @@ struct DevArrays {
     unsigned long long *life_hist;
     double *e_part;                 // per-particle energy scratch
     const RepDev *reps;
+    // Metropolis–Hastings mode (single system)
+    int32_t *mh_key, *mh_count, *mh_start, *mh_cursor, *mh_order, *mh_bsum, *mh_gate;
+    int32_t *mv_type, *mv_i, *mv_j, *mv_n, *mv_b, *mv_c, *mv_cand;   // per move (active cell)
+    double *mv_r;                   // kMhCand per move: separations of the candidates
+    float *mv_feat, *mv_logit;      // kMhCand x 12 features and logits per move
+    // bond-formation event log (training data)
+    float *ev_feat;                 // kMhCand x 12 per event
+    int32_t *ev_n, *ev_label, *ev_count;
+    int32_t ev_cap;
 };
+
+constexpr int kMhCand = 16;         // candidates per MH move or logged event
 
 constexpr int kContenders = 4;
 constexpr int kCopies = 32;        // each counter is spread over this many words
 
 enum Counter {
     cScanned = 0, cInWindow, cProposals, cEdges, cSurvivors, cFormed, cBreakTested, cBroken,
-    cSweeps, cFormedTotal, cBrokenTotal, cBuilds, cNlistScanned, cNlistEntries, cNumCounters
+    cSweeps, cFormedTotal, cBrokenTotal, cBuilds, cNlistScanned, cNlistEntries,
+    cMhFormAtt, cMhFormAcc, cMhBreakAtt, cMhBreakAcc, cEvents, cNumCounters
 };
 
 // ------------------------------------------------------------ Philox-4x32-10

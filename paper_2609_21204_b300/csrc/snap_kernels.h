@@ -23,6 +23,16 @@ void launch_rebuild_done(const DevArrays &A, Launch L);
 // sets a graph conditional to (*need_rebuild && status == 0)
 void launch_set_rebuild_cond(const DevArrays &A, cudaGraphConditionalHandle h, Launch L);
 
+// exclusive scan of in[0..n) into out[0..n] (runs only when *gate != 0 and status is clear)
+void launch_scan(const int32_t *in, int32_t *out, int32_t *bsum, int n, const int32_t *gate, const uint32_t *status,
+                 Launch L);
+
+// ---- Metropolis–Hastings bond moves (mh.cu); mlp == nullptr: uniform proposal ----
+struct MlpDev;
+void launch_mh_sweep(const DevParams &P, const DevArrays &A, bool forced, const MlpDev *mlp, int32_t *bsum,
+                     Launch L);
+void launch_log_events(const DevParams &P, const DevArrays &A, int slot, bool forced, Launch L);
+
 // ---- bond sweep (Sec. II.C), exact FP64 decisions ----
 void launch_sweep_begin(const DevParams &P, const DevArrays &A, Launch L);
 void launch_sweep_reaction(const DevParams &P, const DevArrays &A, int slot, Launch L);

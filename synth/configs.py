@@ -252,3 +252,41 @@ def random_frozen(seed: int, n: int, box: float, type_fracs=(0.5, 0.5), sigma=(1
         pos=pos, vel=_velocities(rng, n, kT), types=types,
         static_bonds=np.zeros((0, 2), np.int32), static_bond_types=np.zeros(0, np.int32),
         kT=kT, seed=seed)
+
+
+def frozen_stars(seed: int = 1, n_stars: int = 125, arms: int = 4, r_lo: float = 1.0, r_hi: float = 1.25,
+                 spacing: float = 5.0, eps: float = 1.0, k: float = 20.0, r0: float = 1.1,
+                 r_max: float = 1.3, kT: float = 1.0) -> System:
+    """Isolated stars: one A (valence 1) with `arms` B particles (valence 1)
+    at distinct separations spread over [r_lo, r_hi] in random directions,
+    stars on a cubic lattice of the given spacing so that no star reaches
+    another.  Every B of a star competes for the same A."""
+    rng = np.random.default_rng(seed)
+    m = int(math.ceil(n_stars ** (1.0 / 3.0)))
+    L = m * spacing
+    g = np.stack(np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij"),
+                 axis=-1).reshape(-1, 3)[:n_stars] * spacing + 0.5 * spacing
+    per = arms + 1
+    pos = np.empty((n_stars * per, 3))
+    types = np.tile(np.array([0] + [1] * arms, np.int32), n_stars)
+    for s in range(n_stars):
+        pos[s * per] = g[s]
+        radii = rng.permutation(np.linspace(r_lo, r_hi, arms))
+        for a in range(arms):
+            while True:
+                d = rng.normal(size=3)
+                d /= np.linalg.norm(d)
+                p = g[s] + radii[a] * d
+                if all(np.linalg.norm(p - pos[s * per + 1 + b]) > 0.8 for b in range(a)):
+                    break
+            pos[s * per + 1 + a] = p
+    pos %= L
+    return System(
+        name="frozen_stars", box=np.array([L, L, L]), type_names=["A", "B"],
+        sigma=np.array([1.0, 1.0]), valence=np.array([1, 1], np.int32),
+        eps_pair=np.ones((2, 2)), rcut=None,
+        bond_types=[BondType(HARMONIC, k, r0)],
+        reactions=[Reaction(0, 1, 0, 0.0, r_max, eps)],
+        pos=pos, vel=np.zeros_like(pos), types=types,
+        static_bonds=np.zeros((0, 2), np.int32), static_bond_types=np.zeros(0, np.int32),
+        kT=kT, seed=seed, meta=dict(arms=arms))

@@ -1,13 +1,17 @@
 """Pins of the oracle's Metropolis–Hastings bond moves (uniform proposal):
 isolated frozen pairs reach the two-state stationary fraction
-K e^{-U_b/kT} / (1 + K e^{-U_b/kT}) (detailed balance of the move set), and
-the valence invariants hold under MH turnover in a dense gel."""
+K e^{-U_b/kT} / (1 + K e^{-U_b/kT}) (detailed balance of the move set),
+frozen stars whose arms compete for one centre reach the Boltzmann
+populations w_q / (1 + sum w), and the valence invariants hold under MH
+turnover in a dense gel."""
 import math
 
 import numpy as np
 import pytest
 
 from synth import frozen_pairs, colloid_linker
+
+from _stars import star_arm_ranks, star_expectation, star_occupancy, stars_case, block_mean_se
 
 
 @pytest.mark.parametrize("eps,p_on0,r", [(1.0, 1.0, 1.1), (2.0, 0.5, 1.2), (-0.5, 1.0, 1.15)])
@@ -47,3 +51,21 @@ def test_mh_invariants_dense_gel(oracle_mod):
         for j in dp[i][dp[i] >= 0]:
             assert i in dp[j] and s.types[i] != s.types[j]
     assert tot["form_accepts"] > 50 and tot["break_accepts"] > 5
+
+
+def test_mh_frozen_stars_match_boltzmann(oracle_mod):
+    """Competing arms: the uniform proposal's Hastings factor n / b'
+    (n candidates, b' owned bonds after the move) is what makes the arm
+    populations follow w_q / (1 + sum w); dropping it biases them."""
+    s = stars_case()
+    K = math.exp(s.reactions[0].eps)
+    o = oracle_mod.OracleSystem(s)
+    rank = star_arm_ranks(s)
+    expect = star_expectation(s, K)
+    samples = []
+    for t in range(16000):
+        o.mh_sweep(step=t)
+        if t >= 1000 and t % 8 == 0:
+            samples.append(star_occupancy(o.dp.reshape(s.n, 4), s, rank))
+    mean, se = block_mean_se(np.array(samples))
+    assert np.all(np.abs(mean - expect) < 4 * se + 0.01), (mean, expect, se)

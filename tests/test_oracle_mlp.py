@@ -66,3 +66,47 @@ def test_bf16_rounding():
     # 1 + 2^-8 lies halfway between bf16 neighbours 1 and 1 + 2^-7: ties to even (1)
     assert mlp.bf16_round(np.float32(1 + 2 ** -8)) == 1.0
     assert mlp.bf16_round(np.float32(1 + 3 * 2 ** -8)) == np.float32(1 + 2 ** -6)
+
+
+def _representable_case(rng):
+    """Operands on which every BF16 rounding is exact: inputs in {0, +-1/2, +-1},
+    W1 in quarters, sparse W2 in {0, +-1/2}, w3 in {+-1/2, +-1}; two events of
+    two candidates that differ only in feature 11, whose W1 row is zero, so
+    both candidates tie (softmax 1/2) and the back-propagated values stay on
+    a coarse dyadic grid."""
+    p = {"W1": np.zeros((mlp.KPAD, mlp.H)), "b1": np.zeros(mlp.H), "W2": np.zeros((mlp.H, mlp.H)),
+         "b2": np.zeros(mlp.H), "w3": rng.choice([-1.0, -0.5, 0.5, 1.0], mlp.H), "b3": np.array([0.25])}
+    p["W1"][:11] = rng.integers(-4, 5, (11, mlp.H)) / 4.0
+    p["b1"][:] = rng.integers(-4, 5, mlp.H) / 8.0
+    for m in range(mlp.H):
+        cols = rng.choice(mlp.H, 4, replace=False)
+        p["W2"][m, cols] = rng.choice([-0.5, 0.5], 4)
+    X = np.zeros((4, mlp.NF))
+    for e in range(2):
+        base = rng.choice([-1.0, -0.5, 0.0, 0.5, 1.0], mlp.NF)
+        X[2 * e] = base
+        X[2 * e + 1] = base
+        X[2 * e, 11], X[2 * e + 1, 11] = 1.0, -1.0
+    return mlp.pack(p), X, np.array([0, 2, 4]), np.array([0, 1])
+
+
+def test_bf16_operand_variant_is_exact_on_representable_operands():
+    rng = np.random.default_rng(12)
+    theta, X, off, lab = _representable_case(rng)
+    loss, g = mlp.loss_and_grad(theta, X, off, lab)
+    loss_b, y_b, g_b = mlp.loss_and_grad_bf16(theta, X, off, lab)
+    y, _ = mlp.forward(theta, X)
+    assert np.array_equal(y, y_b) and loss == loss_b
+    assert np.array_equal(g, g_b)
+    assert abs(loss - np.log(2.0)) < 1e-15          # both candidates tie
+    assert np.abs(g).max() > 0.0 and np.abs(g[11 * mlp.H:12 * mlp.H]).max() > 0.0
+
+
+def test_bf16_operand_variant_error_is_of_bf16_size():
+    rng = np.random.default_rng(13)
+    X, off, lab = _data(rng, events=60)
+    theta = mlp.init(seed=2)
+    y, _ = mlp.forward(theta, X)
+    _, y_b, _ = mlp.loss_and_grad_bf16(theta, X, off, lab)
+    rel = np.abs(y_b - y).max() / np.abs(y).max()
+    assert 1e-5 < rel < 3e-2
