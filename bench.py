@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--batch-replicas", type=int, default=256,
                     help="replicas of the batched telechelic sweep leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=500)
+    ap.add_argument("--learned-events", type=int, default=1_000_000,
+                    help="formation events logged for training the proposal network (0: skip the leg)")
+    ap.add_argument("--learned-epochs", type=int, default=10)
+    ap.add_argument("--mh-steps", type=int, default=500)
     ap.add_argument("--input-cache", default="",
                     help="directory to keep the generated coordinates between invocations")
     return ap.parse_args()
@@ -87,18 +91,21 @@ def build_batch(args):
     return telechelic_sweep(n_replicas=args.batch_replicas, processes=procs)
 
 
-def build_system(args, seed):
+def build_system(args, seed, rho=None):
     from synth import colloid_linker
+    kw = dict(seed=seed, n_c=args.n_c, n_l=args.n_l)
+    kw.update(dict(rho=rho, eta=None) if rho is not None else dict(eta=0.25))
     if args.input_cache:
         import pickle
-        p = Path(args.input_cache) / f"colloid_linker_{args.n_c}_{args.n_l}_{seed}.pkl"
+        tag = f"rho{rho}" if rho is not None else "eta0.25"
+        p = Path(args.input_cache) / f"colloid_linker_{args.n_c}_{args.n_l}_{seed}_{tag}.pkl"
         if p.exists():
             return pickle.loads(p.read_bytes())
-        s = colloid_linker(seed=seed, n_c=args.n_c, n_l=args.n_l, eta=0.25)
+        s = colloid_linker(**kw)
         p.parent.mkdir(parents=True, exist_ok=True)
         p.write_bytes(pickle.dumps(s))
         return s
-    return colloid_linker(seed=seed, n_c=args.n_c, n_l=args.n_l, eta=0.25)
+    return colloid_linker(**kw)
 
 
 # ----------------------------------------------------------------- clocks
@@ -253,6 +260,119 @@ def _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream):
             "autotune": {k: tune[k] for k in ("block_size", "skin", "cached", "key")}}
 
 
+def _segment_metrics(y, off, lab):
+    """held-out listwise cross-entropy and top-1 accuracy of logits y, and of
+    a uniform choice, over candidate sets off[e]..off[e+1]."""
+    n = np.diff(off)
+    seg = np.repeat(np.arange(len(n)), n)
+    mx = np.maximum.reduceat(y, off[:-1])
+    z = np.exp(y - mx[seg])
+    lse = np.log(np.add.reduceat(z, off[:-1])) + mx
+    ce = float(np.mean(lse - y[off[:-1] + lab]))
+    top = np.maximum.reduceat(y, off[:-1])
+    hit = float(np.mean(y[off[:-1] + lab] >= top))
+    return {"cross_entropy": ce, "top1": hit, "uniform_cross_entropy": float(np.mean(np.log(n))),
+            "uniform_top1": float(np.mean(1.0 / n)), "mean_candidates": float(n.mean())}
+
+
+def _run_learned(args, torch, snap, rank, stream):
+    """Learned-proposal leg on the dense gel (number density 0.8): log the
+    plain method's formation events, train the BF16 network on the device,
+    then run Langevin dynamics with Metropolis-Hastings bond moves under the
+    uniform and the learned proposal from the same state."""
+    s = build_system(args, 20260921 + 7 + rank, rho=0.8)
+    sim = snap.from_system(s, precision="mixed", block_size=args.block)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    sim.step(args.warmup)
+    K = args.mh_steps
+    t_plain = timed(lambda: sim.step(K))
+    # log formation events of plain sweeps
+    cap = args.learned_events
+    sim.log_events(cap)
+    logged, log_steps = 0, 0
+    while logged < cap and log_steps < 20 * K:
+        sim.step(50)
+        log_steps += 50
+        logged = sim.stats()["events_logged"]
+    feat, off, lab = sim.get_events(clear=True)
+    sim.log_events(0)
+    E = len(lab)
+    Et = int(0.9 * E)
+    dX = torch.from_numpy(feat).cuda()
+    doff = torch.from_numpy(off).cuda()
+    dlab = torch.from_numpy(lab).cuda()
+    mlp = snap.Mlp(snap.mlp_init_weights(seed=1), stream=stream.cuda_stream)
+    losses = None
+
+    def train():
+        nonlocal losses
+        losses = mlp.train(dX.data_ptr(), int(off[Et]), doff.data_ptr(), dlab.data_ptr(), Et,
+                           epochs=args.learned_epochs, batch_events=4096, lr=1e-3, seed=2)
+    t_train = timed(train)
+    rows_h = int(off[E] - off[Et])
+    yh = torch.empty(max(rows_h, 1), device="cuda")
+    t_fwd = timed(lambda: mlp.forward(dX.data_ptr() + 4 * 12 * int(off[Et]), rows_h, yh.data_ptr()))
+    held = _segment_metrics(yh[:rows_h].cpu().numpy().astype(np.float64),
+                            (off[Et:] - off[Et]).astype(np.int64), lab[Et:].astype(np.int64))
+    rows_train = int(off[Et]) * args.learned_epochs
+    # forward 2 (16x64 + 64x64 + 64) flops per row; backward twice that
+    flops_row = 3 * 2 * (16 * 64 + 64 * 64 + 64)
+    state = sim.get_state()
+    mh = {}
+    for mode, name in ((1, "uniform"), (2, "learned")):
+        sim.set_state(state)
+        sim.set_mh(mode, mlp if mode == 2 else None, eps_u=0.05)
+        sim.step(50)
+        st0 = sim.stats()
+        h0 = sim.lifetime_hist()
+        t_mh = timed(lambda: sim.step(K))
+        series = []
+        for _ in range(20):
+            sim.step(50)
+            series.append(sim.stats()["n_bonds"])
+        st1 = sim.stats()
+        hist = (sim.lifetime_hist() - h0).astype(np.float64)
+        d = {k: st1["mh_" + k] - st0["mh_" + k]
+             for k in ("form_attempts", "form_accepts", "break_attempts", "break_accepts")}
+        ser = np.array(series, float)
+        blocks = ser.reshape(10, -1).mean(1)
+        mh[name] = {"ms_per_step": t_mh * 1e3 / K,
+                    "value": s.n * K / t_mh,
+                    "accepted_per_attempt": (d["form_accepts"] + d["break_accepts"]) /
+                                            max(1, d["form_attempts"] + d["break_attempts"]),
+                    **d, "n_bonds_mean": float(ser.mean()),
+                    "n_bonds_se": float(blocks.std(ddof=1) / math.sqrt(len(blocks))),
+                    "mean_lifetime_steps": float((hist * np.arange(len(hist))).sum() / max(1.0, hist.sum())),
+                    "broken_bonds": int(hist.sum()), "_hist": hist}
+        sim.set_mh(0)
+    hu, hl = mh["uniform"].pop("_hist"), mh["learned"].pop("_hist")
+    hell = None
+    if hu.sum() > 0 and hl.sum() > 0:
+        hell = float(np.sqrt(0.5 * np.sum((np.sqrt(hu / hu.sum()) - np.sqrt(hl / hl.sum())) ** 2)))
+    sim.close()
+    mlp.close()
+    return {"workload": f"dense colloid-linker gel, {s.n} particles at number density 0.8 "
+                        "(types, bonds and eps as the headline gel)",
+            "plain_ms_per_step": t_plain * 1e3 / K,
+            "events": E, "events_train": Et, "log_steps": log_steps,
+            "train": {"epochs": args.learned_epochs, "batch_events": 4096, "seconds": t_train,
+                      "rows_per_s": rows_train / t_train, "tflops": rows_train * flops_row / t_train / 1e12,
+                      "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1])},
+            "forward_rows_per_s": rows_h / t_fwd if t_fwd > 0 else None,
+            "held_out": held, "mh": mh, "lifetime_hellinger_uniform_vs_learned": hell,
+            "eps_u": 0.05}
+
+
 def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier, max_all, sum_all,
                         stream, batch=None):
     s = build_system(args, 20260921 + rank)
@@ -341,6 +461,11 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
     if batch is not None:
         sim.close()
         out["batched"] = _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream)
+        sim = snap.from_system(s, precision="mixed", block_size=args.block)
+        sim.step(W)
+    if args.learned_events > 0:
+        sim.close()
+        out["learned"] = _run_learned(args, torch, snap, rank, stream)
         sim = snap.from_system(s, precision="mixed", block_size=args.block)
         sim.step(W)
     if not args.no_e2e:

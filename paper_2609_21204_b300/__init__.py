@@ -16,7 +16,7 @@ import numpy as np
 from . import _abi
 from ._abi import SNAP_FP64, SNAP_MIXED, SNAP_HARMONIC, SNAP_FENE
 
-__all__ = ["Snap", "Mlp", "SnapError", "closure", "rates_from_eps", "from_system", "pair_energy_noalloc",
+__all__ = ["Snap", "Mlp", "mlp_init_weights", "SnapError", "closure", "rates_from_eps", "from_system", "pair_energy_noalloc",
            "SNAP_FP64",
            "SNAP_MIXED", "SNAP_HARMONIC", "SNAP_FENE"]
 
@@ -321,6 +321,20 @@ class Snap:
         self._check(self._lib.snap_get_events(self._ctx, feat.ctypes.data, off.ctypes.data, lab.ctypes.data,
                                               ne.value, nr.value, C.byref(ne), C.byref(nr), int(clear)))
         return feat[: nr.value], off[: ne.value + 1], lab[: ne.value]
+
+
+def mlp_init_weights(seed=0):
+    """Initial FP32 parameters of the proposal network in the packed layout
+    W1[16][64] (rows 12..15 zero), b1[64], W2[64][64], b2[64], w3[64], b3:
+    zero biases and normal weights with variance 2 / fan-in (1 / fan-in for
+    the linear output layer)."""
+    rng = np.random.default_rng(seed)
+    w1 = np.zeros((16, 64))
+    w1[:12] = rng.normal(0.0, math.sqrt(2.0 / 12), (12, 64))
+    w2 = rng.normal(0.0, math.sqrt(2.0 / 64), (64, 64))
+    w3 = rng.normal(0.0, math.sqrt(1.0 / 64), 64)
+    z = np.zeros(64)
+    return np.concatenate([w1.ravel(), z, w2.ravel(), z, w3, [0.0]]).astype(np.float32)
 
 
 class Mlp:

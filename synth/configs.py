@@ -256,11 +256,12 @@ def random_frozen(seed: int, n: int, box: float, type_fracs=(0.5, 0.5), sigma=(1
 
 def frozen_stars(seed: int = 1, n_stars: int = 125, arms: int = 4, r_lo: float = 1.0, r_hi: float = 1.25,
                  spacing: float = 5.0, eps: float = 1.0, k: float = 20.0, r0: float = 1.1,
-                 r_max: float = 1.3, kT: float = 1.0) -> System:
+                 r_max: float = 1.3, kT: float = 1.0, min_sep: float = 0.8) -> System:
     """Isolated stars: one A (valence 1) with `arms` B particles (valence 1)
     at distinct separations spread over [r_lo, r_hi] in random directions,
     stars on a cubic lattice of the given spacing so that no star reaches
-    another.  Every B of a star competes for the same A."""
+    another.  Every B of a star competes for the same A.  Arms of a star are
+    at least min_sep apart."""
     rng = np.random.default_rng(seed)
     m = int(math.ceil(n_stars ** (1.0 / 3.0)))
     L = m * spacing
@@ -277,7 +278,7 @@ def frozen_stars(seed: int = 1, n_stars: int = 125, arms: int = 4, r_lo: float =
                 d = rng.normal(size=3)
                 d /= np.linalg.norm(d)
                 p = g[s] + radii[a] * d
-                if all(np.linalg.norm(p - pos[s * per + 1 + b]) > 0.8 for b in range(a)):
+                if all(np.linalg.norm(p - pos[s * per + 1 + b]) > min_sep for b in range(a)):
                     break
             pos[s * per + 1 + a] = p
     pos %= L
