@@ -415,16 +415,20 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
     sweep_pairs = st2["scanned"] + st2["break_tested"]
     bond_pairs_per_s = sweep_pairs / (ph["sweep"] / 1e3) if ph["sweep"] > 0 else None
 
-    # kernels launched per step: 10 neighbour-list kernels (early exits between
-    # rebuilds), 1 + 5 per reaction for the sweep, force, integrate, step end
-    kernels_per_step = 10 + (1 + 5 * len(s.reactions)) + 3
+    # kernels launched: per step the rebuild condition, the sweep (begin + 7 per
+    # reaction: scan or push proposals in 5 kernels of which one mode's exit at
+    # once, accept/break, apply), force, integrate and step end; per rebuild 10
+    # more (cell keys, 3 scan kernels, scatter, cell sort, gather, copy back,
+    # lists, done)
+    builds = st1["nlist_builds"] - st0["nlist_builds"]
+    launches = K * (1 + (1 + 7 * len(s.reactions)) + 3) + 10 * builds
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": t_max * 1e3 / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": workload_config(args, n),
-        "gpu_launches": kernels_per_step * K,
+        "gpu_launches": launches,
         "clocks": clk,
         "phases_ms_per_step": {k: round(v, 5) for k, v in ph.items()},
         "bond_update_pairs_per_s": bond_pairs_per_s,

@@ -95,7 +95,8 @@ typedef struct {
     void *alloc_user;        /* passed to alloc/free */
     int32_t block_size;      /* threads per block for particle kernels: 0 (= 256) or a
                                 multiple of 32 up to 256 */
-    int32_t nlist_capacity;  /* initial neighbours per particle (0: from density) */
+    int32_t nlist_capacity;  /* initial force-list entries per particle (0: from density;
+                                the reactive list is always sized from density) */
     int32_t lifetime_bins;   /* bins of the bond-lifetime histogram (0: 256) */
 } snap_config;
 
@@ -109,11 +110,13 @@ typedef struct {
     int64_t in_window;       /* compatible partners inside [r_min, r_max] */
     int64_t proposals, edges, survivors, formed, break_tested, broken;
     int64_t nlist_builds;    /* neighbour-list rebuilds so far */
-    int64_t nlist_entries;   /* neighbour entries written by the last rebuild */
+    int64_t nlist_entries;   /* force-list entries written by the last rebuild */
     int64_t mh_form_attempts, mh_form_accepts;    /* Metropolis-Hastings moves so far */
     int64_t mh_break_attempts, mh_break_accepts;
     int64_t events_logged;   /* bond-formation events offered to the event log */
-    int32_t nlist_capacity;  /* current neighbours-per-particle capacity */
+    int64_t rnlist_entries;  /* reactive-list entries written by the last rebuild */
+    int64_t rebuild_launches; /* launches of the rebuild kernels (taken or skipped) so far */
+    int32_t nlist_capacity;  /* current force-list entries-per-particle capacity */
     int32_t status;          /* latched device status (snap_status value) */
 } snap_stats;
 
@@ -194,6 +197,13 @@ snap_status snap_step(snap_ctx *, int64_t nsteps);
  * integrator + step end.  Same results as snap_step; slower (no graphs). */
 #define SNAP_NPHASES 4
 snap_status snap_step_profiled(snap_ctx *, int64_t nsteps, double *ms);
+/* One neighbour-list rebuild at the current positions (forced), each kernel
+ * timed with CUDA events: ms[SNAP_NREBUILD_PHASES] = [0] cell keys, [1] scan
+ * of the cell counts, [2] scatter, [3] in-cell sort, [4] gather into sorted
+ * order, [5] copy back, [6] neighbour lists, [7] done flag.  Changes nothing
+ * but the particle order (the state is the same physical state). */
+#define SNAP_NREBUILD_PHASES 8
+snap_status snap_rebuild_profiled(snap_ctx *, double *ms);
 
 /* One bond sweep at the current positions with the current step counter as
  * its Philox counter; positions and the step counter are unchanged. */
@@ -213,7 +223,9 @@ snap_status snap_get_positions(snap_ctx *, double *pos3);
 snap_status snap_get_velocities(snap_ctx *, double *vel3);
 snap_status snap_get_images(snap_ctx *, int32_t *img3);
 
-/* Neighbour list as tag pairs (i, j), i < j, each unordered pair once. */
+/* Neighbour lists as tag pairs (i, j), i < j, each unordered pair once: the
+ * union of the force list (pairs within the pair cut-off + skin) and the
+ * reactive list (reaction-compatible pairs within r_max + skin). */
 snap_status snap_get_neighbors(snap_ctx *, int32_t *tag_pairs, int64_t cap, int64_t *n_out);
 
 snap_status snap_get_stats(snap_ctx *, snap_stats *out);

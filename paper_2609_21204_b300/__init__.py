@@ -216,6 +216,14 @@ class Snap:
         self._check(self._lib.snap_step_profiled(self._ctx, int(nsteps), ms.ctypes.data))
         return dict(rebuild=ms[0], sweep=ms[1], force=ms[2], integrate=ms[3])
 
+    REBUILD_PHASES = ("cell_key", "scan", "scatter", "cell_sort", "gather", "copyback", "nlist", "done")
+
+    def rebuild_profiled(self):
+        """Force one neighbour-list rebuild and time each of its kernels (ms)."""
+        ms = np.zeros(len(self.REBUILD_PHASES))
+        self._check(self._lib.snap_rebuild_profiled(self._ctx, ms.ctypes.data))
+        return dict(zip(self.REBUILD_PHASES, ms.tolist()))
+
     def bond_update(self):
         self._check(self._lib.snap_bond_update(self._ctx))
 

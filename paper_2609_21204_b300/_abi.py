@@ -34,7 +34,7 @@ class Stats(C.Structure):
         "step", "n_bonds", "sweeps", "formed_total", "broken_total", "scanned", "in_window",
         "proposals", "edges", "survivors", "formed", "break_tested", "broken",
         "nlist_builds", "nlist_entries", "mh_form_attempts", "mh_form_accepts", "mh_break_attempts",
-        "mh_break_accepts", "events_logged")] + [("nlist_capacity", C.c_int32), ("status", C.c_int32)]
+        "mh_break_accepts", "events_logged", "rnlist_entries", "rebuild_launches")] + [("nlist_capacity", C.c_int32), ("status", C.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -76,6 +76,7 @@ SIGNATURES = {
     "snap_set_mh": (C.c_int, [_P, C.c_int32, _P, C.c_double]),
     "snap_mh_sweep": (C.c_int, [_P]),
     "snap_set_step": (C.c_int, [_P, C.c_int64]),
+    "snap_rebuild_profiled": (C.c_int, [_P, _P]),
     "snap_log_events": (C.c_int, [_P, C.c_int64]),
     "snap_get_events": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int64, C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64), C.c_int32]),

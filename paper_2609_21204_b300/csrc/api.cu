@@ -78,6 +78,7 @@ struct snap_ctx {
     cudaGraphExec_t graph = nullptr;
     bool graph_dirty = true;
     int nbr_cap = 0;
+    int rnbr_cap = 0;
 };
 
 namespace {
@@ -205,10 +206,13 @@ void fill_params(snap_ctx *c)
             const double rc = pair_rc(c, a, b);
             const double sig = 0.5 * (c->sigma[a] + c->sigma[b]);
             const double e = c->eps[k];
-            const double rl = std::max(rc, reactive_cut(c, a, b)) + skin + 1e-4;
+            const double fl = rc + skin + 1e-4;
+            const double xc = reactive_cut(c, a, b);
+            const double xl = xc > 0.0 ? xc + skin + 1e-4 : 0.0;
             P.rc2d[k] = rc * rc;
             P.rc2f[k] = (float)(rc * rc);
-            P.rl2f[k] = (float)(rl * rl);
+            P.fl2f[k] = (float)(fl * fl);
+            P.xl2f[k] = (float)(xl * xl);
             P.sig2d[k] = sig * sig;
             P.sig2f[k] = (float)(sig * sig);
             P.eps24d[k] = 24.0 * e;
@@ -238,6 +242,7 @@ void fill_params(snap_ctx *c)
     const double dmax = 0.5 * skin - 1e-4;
     P.disp2f = (float)(dmax * dmax);
     P.nbr_cap = c->nbr_cap;
+    P.rnbr_cap = c->rnbr_cap;
     P.n = c->n;
     P.nbr_stride = ((c->n + 31) / 32) * 32;
     P.nrep = (int)c->reps.size();
@@ -247,6 +252,7 @@ void fill_params(snap_ctx *c)
     P.mh_moves = c->mh_mode ? P.mh_cells / 8 : 0;
     P.mh_eps = (float)c->mh_eps;
     P.log_events = c->ev_cap > 0 ? 1 : 0;
+    P.pdist_rows = std::max<int64_t>(c->n, 1) / 5 + 1;   // push mode needs a side 4x scarcer: <= n / 5 sites
 }
 
 // everything that depends on the model (cut-offs -> cell grids -> capacities)
@@ -254,10 +260,13 @@ snap_status ensure_ready(snap_ctx *c)
 {
     if (c->ready) return SNAP_OK;
     if (!c->types_set) return fail(c, SNAP_ERR_STATE, "snap_set_types has not been called");
-    double rl_max = 0.0;
+    double rl_max = 0.0, rf_max = 0.0, rx_max = 0.0;
     for (int a = 0; a < c->ntypes; ++a)
-        for (int b = 0; b < c->ntypes; ++b)
-            rl_max = std::max(rl_max, std::max(pair_rc(c, a, b), reactive_cut(c, a, b)));
+        for (int b = 0; b < c->ntypes; ++b) {
+            rf_max = std::max(rf_max, pair_rc(c, a, b));
+            rx_max = std::max(rx_max, reactive_cut(c, a, b));
+        }
+    rl_max = std::max(rf_max, rx_max);
     const double cell_min = rl_max + c->cfg.skin + 2e-4;
     int off = 0;
     double dens_max = 0.0;
@@ -274,13 +283,14 @@ snap_status ensure_ready(snap_ctx *c)
         dens_max = std::max(dens_max, (double)R.n / (R.L[0] * R.L[1] * R.L[2]));
     }
     c->ncell_total = off;
-    // capacity: expected neighbours within the largest list cut-off, doubled, + margin
-    if (c->nbr_cap <= 0) {
-        const double rl = rl_max + c->cfg.skin + 1e-4;
-        const double expect = dens_max * 4.0 / 3.0 * M_PI * rl * rl * rl;
-        int cap = (int)std::ceil(expect * 2.0 + 16.0);
-        c->nbr_cap = (cap + 7) & ~7;
-    }
+    // capacities: expected neighbours within each list's largest cut-off, doubled, + margin
+    auto expect_cap = [&](double cut) {
+        const double rl = cut + c->cfg.skin + 1e-4;
+        const int cap = (int)std::ceil(dens_max * 4.0 / 3.0 * M_PI * rl * rl * rl * 2.0 + 16.0);
+        return (cap + 7) & ~7;
+    };
+    if (c->nbr_cap <= 0) c->nbr_cap = expect_cap(rf_max);
+    if (c->rnbr_cap <= 0) c->rnbr_cap = rx_max > 0.0 ? expect_cap(rx_max) : 8;
     // cell tables
     std::vector<int32_t> rank_of(off);
     for (const auto &R : c->reps) {
@@ -306,7 +316,8 @@ snap_status ensure_ready(snap_ctx *c)
     CUDA_TRY(c, cudaMemcpyAsync(A.rank_of, rank_of.data(), sizeof(int32_t) * off, cudaMemcpyHostToDevice,
                                 c->stream));
     const int64_t stride = ((c->n + 31) / 32) * 32;
-    if (!alloc_arr(c, A.nbr, (size_t)stride * c->nbr_cap)) return fail(c, SNAP_ERR_OOM, "neighbour list");
+    if (!alloc_arr(c, A.nbr, (size_t)stride * c->nbr_cap) || !alloc_arr(c, A.rnbr, (size_t)stride * c->rnbr_cap))
+        return fail(c, SNAP_ERR_OOM, "neighbour lists");
     fill_params(c);
     snap_status s = upload_reps(c);
     if (s != SNAP_OK) return s;
@@ -486,16 +497,23 @@ snap_status set_need_rebuild(snap_ctx *c)
 // simply retried.
 snap_status grow_nlist(snap_ctx *c)
 {
-    int32_t need = 0;
-    CUDA_TRY(c, cudaMemcpyAsync(&need, c->A.nbr_need, sizeof need, cudaMemcpyDeviceToHost, c->stream));
+    int32_t need[2] = {0, 0};
+    CUDA_TRY(c, cudaMemcpyAsync(need, c->A.nbr_need, sizeof need, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    int cap = std::max(need + need / 4 + 8, c->nbr_cap + 8);
-    cap = (cap + 7) & ~7;
-    dfree(c, c->A.nbr);
     const int64_t stride = ((c->n + 31) / 32) * 32;
-    if (!alloc_arr(c, c->A.nbr, (size_t)stride * cap)) return fail(c, SNAP_ERR_OOM, "neighbour list regrow");
-    c->nbr_cap = cap;
-    c->P.nbr_cap = cap;
+    int *caps[2] = {&c->nbr_cap, &c->rnbr_cap};
+    int32_t **lists[2] = {&c->A.nbr, &c->A.rnbr};
+    for (int l = 0; l < 2; ++l) {
+        if (need[l] <= *caps[l]) continue;
+        int cap = std::max(need[l] + need[l] / 4 + 8, *caps[l] + 8);
+        cap = (cap + 7) & ~7;
+        dfree(c, *lists[l]);
+        *lists[l] = nullptr;
+        if (!alloc_arr(c, *lists[l], (size_t)stride * cap)) return fail(c, SNAP_ERR_OOM, "neighbour list regrow");
+        *caps[l] = cap;
+    }
+    c->P.nbr_cap = c->nbr_cap;
+    c->P.rnbr_cap = c->rnbr_cap;
     c->graph_dirty = true;
     snap_status s = clear_status(c);
     if (s != SNAP_OK) return s;
@@ -508,6 +526,7 @@ snap_status status_to_code(snap_ctx *c, uint32_t st)
     if (st & kStNonfinite) return fail(c, SNAP_ERR_NONFINITE, "non-finite position");
     if (st & kStFene) return fail(c, SNAP_ERR_FENE_OVERSTRETCH, "FENE bond stretched beyond R0");
     if (st & kStOverflow) return fail(c, SNAP_ERR_NLIST_OVERFLOW, "neighbour list overflow");
+    if (st & kStTimeout) return fail(c, SNAP_ERR_TIMEOUT, "a bounded device retry loop gave up");
     return fail(c, SNAP_ERR_STATE, "unknown device status");
 }
 
@@ -803,12 +822,15 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
     }
     DevArrays &A = c->A;
     A.force = dalloc(c, v4 * n);
-    bool ok = A.force && alloc_arr(c, A.rtag, n) && alloc_arr(c, A.ref4, n) && alloc_arr(c, A.nn, n) &&
+    bool ok = A.force && alloc_arr(c, A.rtag, n) && alloc_arr(c, A.ref4, n) && alloc_arr(c, A.nn, n) && alloc_arr(c, A.rnn, n) && alloc_arr(c, A.avail, n) && alloc_arr(c, A.avail_count, kMaxTypes) &&
+              alloc_arr(c, A.avail_list, (size_t)kMaxTypes * n) &&
+              alloc_arr(c, A.pkey, n) &&
+              alloc_arr(c, A.pdist, (n / 5 + 1) * kPushSlots) &&
               alloc_arr(c, A.cell_key, n) && alloc_arr(c, A.order, n) && alloc_arr(c, A.prop, n) &&
-              alloc_arr(c, A.prop_r, n) && alloc_arr(c, A.prio, n) && alloc_arr(c, A.best, n) &&
+              alloc_arr(c, A.prop_d, n) && alloc_arr(c, A.prio, n) && alloc_arr(c, A.best, n) &&
               alloc_arr(c, A.fpart, n) && alloc_arr(c, A.brk, n) && alloc_arr(c, A.rx_order, (size_t)nrep * kMaxRx) &&
               alloc_arr(c, A.step, 1) && alloc_arr(c, A.status, 1) && alloc_arr(c, A.need_rebuild, 1) &&
-              alloc_arr(c, A.nbr_need, 1) && alloc_arr(c, A.counters, (size_t)cNumCounters * kCopies) &&
+              alloc_arr(c, A.nbr_need, 2) && alloc_arr(c, A.counters, (size_t)cNumCounters * kCopies) &&
               alloc_arr(c, A.ox, n) && alloc_arr(c, A.oy, n) && alloc_arr(c, A.oz, n) &&
               alloc_arr(c, A.site_list, n) && alloc_arr(c, A.list_count, 1) &&
               alloc_arr(c, A.cont, n * kContenders) && alloc_arr(c, A.ncont, n) &&
@@ -824,9 +846,15 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
     if (cudaMemsetAsync(A.status, 0, 4, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.step, 0, 8, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.need_rebuild, 0, 4, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(A.nbr_need, 0, 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.nbr_need, 0, 8, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.counters, 0, sizeof(unsigned long long) * cNumCounters * kCopies, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.list_count, 0, 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.avail_count, 0, sizeof(int32_t) * kMaxTypes, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.pkey, 0xFF, sizeof(ulonglong2) * n, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.prop, 0xFF, sizeof(int32_t) * n, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.fpart, 0xFF, sizeof(int32_t) * n, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.brk, 0, sizeof(uint32_t) * n, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.best, 0, sizeof(unsigned long long) * n, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.life_hist, 0, sizeof(unsigned long long) * c->cfg.lifetime_bins, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -1125,6 +1153,59 @@ extern "C" snap_status snap_step_profiled(snap_ctx *c, int64_t nsteps, double *m
     return SNAP_OK;
 }
 
+extern "C" snap_status snap_rebuild_profiled(snap_ctx *c, double *ms)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (!ms) return fail(c, SNAP_ERR_ARG, "ms is NULL");
+    if ((s = set_need_rebuild(c)) != SNAP_OK) return s;
+    cudaEvent_t ev[SNAP_NREBUILD_PHASES + 1] = {};
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto &x : ev)
+                if (x) cudaEventDestroy(x);
+            return fail(c, SNAP_ERR_CUDA, "event create");
+        }
+    const Launch L = launch(c);
+    cudaEventRecord(ev[0], c->stream);
+    launch_cell_key(c->P, c->A, L);
+    cudaEventRecord(ev[1], c->stream);
+    launch_cell_scan(c->A, c->d_bsum, c->nkeys, L);
+    cudaEventRecord(ev[2], c->stream);
+    launch_scatter(c->P, c->A, L);
+    cudaEventRecord(ev[3], c->stream);
+    launch_cell_sort(c->A, c->nkeys, L);
+    cudaEventRecord(ev[4], c->stream);
+    launch_gather(c->P, c->A, c->B, c->fp64, L);
+    cudaEventRecord(ev[5], c->stream);
+    launch_copyback(c->P, c->A, c->B, c->fp64, L);
+    cudaEventRecord(ev[6], c->stream);
+    launch_nlist(c->P, c->A, c->fp64, L);
+    cudaEventRecord(ev[7], c->stream);
+    launch_rebuild_done(c->A, L);
+    cudaEventRecord(ev[8], c->stream);
+    cudaError_t err = cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < SNAP_NREBUILD_PHASES && err == cudaSuccess; ++k) {
+        float x = 0.f;
+        err = cudaEventElapsedTime(&x, ev[k], ev[k + 1]);
+        ms[k] = x;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (err != cudaSuccess) return fail(c, SNAP_ERR_CUDA, cudaGetErrorString(err));
+    uint32_t st = 0;
+    if ((s = read_status(c, st)) != SNAP_OK) return s;
+    if (st == kStOverflow) {
+        if ((s = grow_nlist(c)) != SNAP_OK) return s;
+        return snap_rebuild_profiled(c, ms);
+    }
+    if (st) {
+        clear_status(c);
+        return status_to_code(c, st);
+    }
+    return SNAP_OK;
+}
+
 extern "C" snap_status snap_bond_update(snap_ctx *c)
 {
     snap_status s = check_ready(c);
@@ -1259,19 +1340,28 @@ extern "C" snap_status snap_get_neighbors(snap_ctx *c, int32_t *pairs, int64_t c
     if (s != SNAP_OK) return s;
     s = run_with_retry(c, [&] { seq_rebuild(c); });
     if (s != SNAP_OK) return s;
+    // the union of the force and the reactive list
     const int64_t stride = c->P.nbr_stride;
-    std::vector<int32_t> nbr((size_t)stride * c->nbr_cap), nn(c->n), tag(c->n);
-    CUDA_TRY(c, cudaMemcpyAsync(nbr.data(), c->A.nbr, sizeof(int32_t) * nbr.size(), cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(nn.data(), c->A.nn, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<int32_t> tag(c->n);
     CUDA_TRY(c, cudaMemcpyAsync(tag.data(), c->A.tag, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     std::vector<std::pair<int32_t, int32_t>> out;
-    for (int64_t i = 0; i < c->n; ++i)
-        for (int k = 0; k < nn[i]; ++k) {
-            const int32_t a = tag[i], b = tag[nbr[(size_t)k * stride + i]];
-            if (a < b) out.emplace_back(a, b);
-        }
+    const int32_t *lists[2] = {c->A.nbr, c->A.rnbr};
+    const int32_t *counts[2] = {c->A.nn, c->A.rnn};
+    const int caps[2] = {c->nbr_cap, c->rnbr_cap};
+    for (int l = 0; l < 2; ++l) {
+        std::vector<int32_t> nbr((size_t)stride * caps[l]), nn(c->n);
+        CUDA_TRY(c, cudaMemcpyAsync(nbr.data(), lists[l], sizeof(int32_t) * nbr.size(), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(nn.data(), counts[l], sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        for (int64_t i = 0; i < c->n; ++i)
+            for (int k = 0; k < nn[i]; ++k) {
+                const int32_t a = tag[i], b = tag[nbr[(size_t)k * stride + i]];
+                if (a < b) out.emplace_back(a, b);
+            }
+    }
     std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
     if (n_out) *n_out = (int64_t)out.size();
     if ((int64_t)out.size() > cap) return fail(c, SNAP_ERR_ARG, "pair buffer too small");
     for (size_t q = 0; q < out.size(); ++q) {
@@ -1314,6 +1404,8 @@ extern "C" snap_status snap_get_stats(snap_ctx *c, snap_stats *out)
     out->mh_break_attempts = (int64_t)h[cMhBreakAtt];
     out->mh_break_accepts = (int64_t)h[cMhBreakAcc];
     out->events_logged = (int64_t)h[cEvents];
+    out->rnlist_entries = (int64_t)h[cRnlistEntries];
+    out->rebuild_launches = (int64_t)h[cRebuildLaunches];
     out->nlist_capacity = c->nbr_cap;
     out->status = (int32_t)status_to_code(c, st);
     return SNAP_OK;

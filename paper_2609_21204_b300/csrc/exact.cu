@@ -7,19 +7,23 @@
 //
 // The sweep follows Sec. II.C of the DyBond-v2 paper (Fig. 1), one kernel per
 // phase and per reaction in a random order redrawn every sweep:
-//   propose  — every free reactive site scans its neighbour list and keeps the
-//              free, type-compatible partner in [r_min, r_max] closest to the
-//              rest length (ties to the smaller tag);
-//   match    — each proposal edge gets a Philox priority; atomicMax of
-//              (priority << 32 | other tag) at both endpoints;
+//   propose  — every free reactive site scans its reactive neighbour list and
+//              keeps the free, type-compatible partner in [r_min, r_max]
+//              closest to the rest length (ties to the smaller tag); in mixed
+//              mode an FP32 screen keeps the few candidates that may win and
+//              k_exact decides among them in FP64;
+//   match    — (in k_exact) each proposal edge gets a Philox priority;
+//              atomicMax of (priority << 32 | other tag) at both endpoints;
 //   accept   — an edge survives iff it holds the maximum at both ends (a
 //              locally dominant matching, disjoint by construction, replacing
 //              the paper's compare-and-swap race with a scheduling-independent
 //              rule) and forms with probability P_on^0 exp(-U_b(r)/kT), Eq. 3;
-//   break    — every bond of this reaction present before the reaction began
-//              breaks with probability P_off;
+//   break    — (same kernel as accept) every bond of this reaction present
+//              before the reaction began breaks with probability P_off;
 //   apply    — per particle, broken slots are removed and the formed partner
 //              inserted; occupancies change before the next reaction reads them.
+#include <algorithm>
+
 #include "snap_kernels.h"
 
 namespace snap {
@@ -39,20 +43,57 @@ __device__ __forceinline__ bool sweep_active(const DevParams &P, const DevArrays
 
 // grid-stride kernels over the compacted site list use this many blocks
 constexpr int kListBlocks = 296;
+constexpr int kSweepBeginBlock = 256;
 
-// Reaction order per replica: Fisher–Yates driven by Philox(ORDER) with
-// counter (step, k), so competing reactions are treated evenhandedly.
+// Sweep start (one thread per particle): counters reset, the reaction order
+// per replica (Fisher–Yates driven by Philox(ORDER) with counter (step, k), so
+// competing reactions are treated evenhandedly), the availability byte of
+// every particle (its type while it has a free valence slot, else 0xFF) with
+// the count per type.  The per-reaction scratch (best, fpart, brk, prop, the
+// push keys) starts clear and k_apply clears it after each reaction: a sweep
+// either runs to its end or (a latched status) none of its kernels act.
 template <bool FORCED>
 __global__ void k_sweep_begin(DevParams P, DevArrays A)
 {
     long long step;
     if (!sweep_active<FORCED>(P, A, step)) return;
-    const int r = (int)gtid();
+    const long long r = gtid();
     if (r == 0) {
         for (int c = cScanned; c <= cBroken; ++c) counter_reset(A.counters, c);
         counter_reset(A.counters, cNlistScanned);
         counter_add1(A.counters, cSweeps, 1ull);
         *A.list_count = 0;
+    }
+    int av = -1;
+    if (r < P.n) {
+        const int t = A.type[r];
+        av = A.occ[r] < P.valence[t] ? t : -1;
+        A.avail[r] = av >= 0 ? (uint8_t)t : (uint8_t)0xFF;
+    }
+    // per-type counts and (single system, single reaction: the only case push
+    // mode serves) compacted lists; one global atomic per block and type
+    const bool lists = P.nrep == 1 && P.nrx == 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ int s_cnt[kMaxTypes], s_base[kMaxTypes], s_woff[kSweepBeginBlock / 32][kMaxTypes];
+    if (threadIdx.x < kMaxTypes) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = 0; t < P.ntypes; ++t) {
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, av == t);
+        if (lane == 0) s_woff[wid][t] = m ? atomicAdd(&s_cnt[t], __popc(m)) : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < P.ntypes) {
+        const int t = threadIdx.x;
+        s_base[t] = s_cnt[t] ? atomicAdd(&A.avail_count[t], s_cnt[t]) : 0;
+    }
+    __syncthreads();
+    if (lists) {
+        for (int t = 0; t < P.ntypes; ++t) {
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, av == t);
+            if (av == t)
+                A.avail_list[(long long)t * P.n + s_base[t] + s_woff[wid][t] + __popc(m & ((1u << lane) - 1u))] =
+                    (int)r;
+        }
     }
     if (r >= P.nrep) return;
     const RepDev &R = A.reps[r];
@@ -78,6 +119,29 @@ __device__ __forceinline__ double exact_r2(const DevArrays &A, const RepDev &R, 
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+// The same value with the minimum image skipped on axes where it is the
+// identity: when the two frozen cells (bits of pos4.w) are neighbours without
+// wrapping and there are at least 6 cells, |d| < 2 w + skin < L / 2, so
+// rint(d / L) = 0 and d - L * 0 = d exactly.
+__device__ __forceinline__ double exact_r2_cells(const DevArrays &A, const RepDev &R, int i, int j, uint32_t bi,
+                                                 uint32_t bj)
+{
+    double dx = __dsub_rn(A.x[j], A.x[i]);
+    double dy = __dsub_rn(A.y[j], A.y[i]);
+    double dz = __dsub_rn(A.z[j], A.z[i]);
+    if (!(R.nc[0] >= 6 && abs(bits_cx(bj) - bits_cx(bi)) <= 1)) dx = min_image(dx, R.L[0], R.invL[0]);
+    if (!(R.nc[1] >= 6 && abs(bits_cy(bj) - bits_cy(bi)) <= 1)) dy = min_image(dy, R.L[1], R.invL[1]);
+    if (!(R.nc[2] >= 6 && abs(bits_cz(bj) - bits_cz(bi)) <= 1)) dz = min_image(dz, R.L[2], R.invL[2]);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// w bits (type, frozen cell) of particle i from pos4 in either precision
+__device__ __forceinline__ uint32_t cell_bits(const DevParams &P, const DevArrays &A, int i)
+{
+    return P.screen ? w_bits(reinterpret_cast<const float4 *>(A.pos4)[i])
+                    : w_bits(reinterpret_cast<const double4_32a *>(A.pos4)[i]);
+}
+
 // keep the candidate minimising |r - r0|, ties to the smaller tag
 __device__ __forceinline__ void consider(double d, double r, int j, int tgj, int &best, int &best_tag,
                                          double &best_d, double &best_r)
@@ -101,145 +165,194 @@ __device__ __forceinline__ void consider(double d, double r, int j, int tgj, int
 constexpr float kScreenR2 = 1e-4f;
 constexpr float kScreenD = 1e-4f;
 
+// Push mode.  When one side of a reaction has far fewer available particles
+// than the other (a saturated gel: almost every colloid slot is taken), the
+// scarce side's sites both make their own proposals and push themselves, as
+// candidates, to their available partners on the abundant side; each of
+// those picks the smallest |r - r0| among what it received (ties to the
+// smaller tag) — exactly the proposal a scan of its own list would make, for
+// a small fraction of the neighbour visits.  The pushing sites come from the
+// compacted per-type list of k_sweep_begin, so their FP64 work runs in dense
+// warps.  Single system with a single reaction (the lists and counts are per
+// type and are not updated between reactions).
+constexpr int kPushRatio = 4;
+
+// the pushing type of reaction slot `slot`, or -1 for the plain (pull) scan
+__device__ __forceinline__ int push_type(const DevParams &P, const DevArrays &A, int slot)
+{
+    if (P.nrep != 1 || P.nrx != 1) return -1;
+    const int a = A.rx_order[slot];
+    const int ta = P.rx_ta[a], tb = P.rx_tb[a];
+    if (ta == tb) return -1;
+    const long long ca = A.avail_count[ta], cb = A.avail_count[tb];
+    if (ca * kPushRatio <= cb) return ta;
+    if (cb * kPushRatio <= ca) return tb;
+    return -1;
+}
+
+// Partners of site i that may be proposed: available with the partner type
+// (one byte load) and not already bonded to i (sorted indices of i's partners).
+struct SiteFilter {
+    uint8_t pt;
+    int b0, b1, b2, b3;
+    __device__ __forceinline__ bool ok(const DevArrays &A, int j) const
+    {
+        return A.avail[j] == pt && j != b0 && j != b1 && j != b2 && j != b3;
+    }
+};
+
+__device__ __forceinline__ SiteFilter site_filter(const DevArrays &A, int ti, int ta, int tb, int i)
+{
+    const int4 dp = A.dp[i];
+    SiteFilter f;
+    f.pt = (uint8_t)(ti == ta ? tb : ta);
+    f.b0 = dp.x >= 0 ? A.rtag[dp.x] : -1;
+    f.b1 = dp.y >= 0 ? A.rtag[dp.y] : -1;
+    f.b2 = dp.z >= 0 ? A.rtag[dp.z] : -1;
+    f.b3 = dp.w >= 0 ? A.rtag[dp.w] : -1;
+    return f;
+}
+
+// FP32 separation squared from cell-relative coordinates and frozen cells
+__device__ __forceinline__ float screen_r2(const float4 &pi4, const float4 &pj4, const RepDev &R)
+{
+    const uint32_t bi = w_bits(pi4), bj = w_bits(pj4);
+    const float ex = (pj4.x - pi4.x) + (float)cell_delta(bits_cx(bj) - bits_cx(bi), R.nc[0]) * R.wf[0];
+    const float ey = (pj4.y - pi4.y) + (float)cell_delta(bits_cy(bj) - bits_cy(bi), R.nc[1]) * R.wf[1];
+    const float ez = (pj4.z - pi4.z) + (float)cell_delta(bits_cz(bj) - bits_cz(bi), R.nc[2]) * R.wf[2];
+    return ex * ex + ey * ey + ez * ez;
+}
+
+// Proposal phase over the reactive list.  FP64 mode decides each site here.
+// Mixed mode screens in FP32: a first pass finds the smallest sure upper
+// bound of |r - r0| among candidates surely inside the window, a second pass
+// keeps (in list order, at most kContenders) every candidate that may still
+// win — window-ambiguous, too close for the bound, or within the margin of
+// that bound — for k_exact to decide in FP64.
 template <bool FORCED, bool SCREEN>
 __global__ void __launch_bounds__(256) k_propose(DevParams P, DevArrays A, int slot)
 {
     long long step;
     if (!sweep_active<FORCED>(P, A, step)) return;   // uniform over the grid
-    const long long i = gtid();
+    if (push_type(P, A, slot) >= 0) return;          // uniform: push mode decides this reaction
     unsigned long long scanned = 0, inwin = 0, nscan = 0, nprop = 0;
+    // grid-stride with a warp-uniform trip count (a small grid exits cheaply in push mode)
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < P.n; base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
     bool want = false;
-    int ncont = 0;
-    int cont[kContenders];
     if (i < P.n) {
-        A.best[i] = 0ull;
-        A.fpart[i] = -1;
-        A.brk[i] = 0u;
-        int best = -1;
-        double best_r = 0.0;
+        int best = -1, ncont = 0;
+        double best_d = 0.0;
         const int rp = A.rep[i];
         const int a = A.rx_order[rp * kMaxRx + slot];
         const int ti = A.type[i];
         const int ta = P.rx_ta[a], tb = P.rx_tb[a];
         if ((ti == ta || ti == tb) && A.occ[i] < P.valence[ti]) {
             const RepDev &R = A.reps[rp];
-            const int4 dp = A.dp[i];
-            const double rmin2 = P.rx_rmin2[a], rmax2 = P.rx_rmax2[a];
-            const double r0 = P.br0[P.rx_bt[a]];
-            const float rmin2f = (float)rmin2, rmax2f = (float)rmax2, r0f = (float)r0;
-            const float4 *pos4 = reinterpret_cast<const float4 *>(A.pos4);
-            float4 pi4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (SCREEN) pi4 = pos4[i];
-            const int nn = A.nn[i];
+            const SiteFilter flt = site_filter(A, ti, ta, tb, (int)i);
+            const int nn = A.rnn[i];
+            const int *nb = A.rnbr + i;
             const long long stride = P.nbr_stride;
-            int best_tag = 0;
-            double best_d = 0.0;
-            float cd[kContenders];
-            float min_upper = 3.0e38f;
-            unsigned long long sure_in = 0;
-            bool ovf = false;
-            nscan = (unsigned long long)nn;
-            for (int k0 = 0; k0 < nn; k0 += 8) {
-                int jj[8], tt[8], oo[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) jj[u] = (k0 + u < nn) ? A.nbr[(long long)(k0 + u) * stride + i] : -1;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    tt[u] = jj[u] >= 0 ? A.type[jj[u]] : -1;
-                    oo[u] = jj[u] >= 0 ? A.occ[jj[u]] : 0;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int j = jj[u];
-                    if (j < 0) continue;
-                    const int tj = tt[u];
-                    const bool compat = (ti == ta && tj == tb) || (ti == tb && tj == ta);
-                    if (!compat || oo[u] >= P.valence[tj]) continue;
-                    const int tgj = A.tag[j];
-                    if (tgj == dp.x || tgj == dp.y || tgj == dp.z || tgj == dp.w) continue;
+            nscan += (unsigned long long)nn;
+            if (SCREEN) {
+                const float4 *pos4 = reinterpret_cast<const float4 *>(A.pos4);
+                const float4 pi4 = pos4[i];
+                const float rmin2f = (float)P.rx_rmin2[a], rmax2f = (float)P.rx_rmax2[a];
+                const float r0f = (float)P.br0[P.rx_bt[a]];
+                float min_upper = 3.0e38f;
+                unsigned long long sure_in = 0;
+                for (int k = 0; k < nn; ++k) {
+                    const int j = __ldg(nb + (long long)k * stride);
+                    if (!flt.ok(A, j)) continue;
                     ++scanned;
-                    if (SCREEN) {
-                        const float4 pj4 = pos4[j];
-                        const uint32_t bi = w_bits(pi4), bj = w_bits(pj4);
-                        const float ex = (pj4.x - pi4.x) + (float)cell_delta(bits_cx(bj) - bits_cx(bi), R.nc[0]) * R.wf[0];
-                        const float ey = (pj4.y - pi4.y) + (float)cell_delta(bits_cy(bj) - bits_cy(bi), R.nc[1]) * R.wf[1];
-                        const float ez = (pj4.z - pi4.z) + (float)cell_delta(bits_cz(bj) - bits_cz(bi), R.nc[2]) * R.wf[2];
-                        const float r2f = ex * ex + ey * ey + ez * ez;
-                        if (r2f < rmin2f - kScreenR2 || r2f > rmax2f + kScreenR2) continue;  // surely outside
-                        const bool amb = !(r2f > rmin2f + kScreenR2 && r2f < rmax2f - kScreenR2);
-                        const bool small = r2f < 0.09f;
-                        const float df = fabsf(sqrtf(r2f) - r0f);
-                        if (!amb) {
-                            ++sure_in;
-                            if (!small) {
-                                if (df - kScreenD > min_upper) continue;   // surely beaten
-                                min_upper = fminf(min_upper, df + kScreenD);
-                            }
-                        }
-                        // drop kept contenders that are now surely beaten
-                        int m = 0;
-                        for (int c = 0; c < ncont; ++c) {
-                            const bool keep = (cont[c] >> 30) != 0 || cd[c] < 0.f || cd[c] - kScreenD <= min_upper;
-                            if (keep) {
-                                cont[m] = cont[c];
-                                cd[m] = cd[c];
-                                ++m;
-                            }
-                        }
-                        ncont = m;
-                        if (ncont < kContenders) {
-                            cont[ncont] = j | (amb ? (1 << 30) : 0);
-                            cd[ncont] = small ? -1.f : df;   // negative: no usable bound
-                            ++ncont;
-                        } else {
-                            ovf = true;
-                        }
-                    } else {
-                        const double r2 = exact_r2(A, R, (int)i, j);
-                        if (r2 < rmin2 || r2 > rmax2) continue;
-                        ++inwin;
-                        const double r = __dsqrt_rn(r2);
-                        consider(fabs(__dsub_rn(r, r0)), r, j, tgj, best, best_tag, best_d, best_r);
+                    const float r2f = screen_r2(pi4, pos4[j], R);
+                    if (r2f < rmin2f - kScreenR2 || r2f > rmax2f + kScreenR2) continue;  // surely outside
+                    if (r2f > rmin2f + kScreenR2 && r2f < rmax2f - kScreenR2) {          // surely inside
+                        ++sure_in;
+                        if (r2f >= 0.09f) min_upper = fminf(min_upper, fabsf(sqrtf(r2f) - r0f) + kScreenD);
                     }
                 }
-            }
-            if (SCREEN) {
-                if (ovf) ncont = kContenders + 1;          // k_exact rescans this site in full
+                if (scanned > 0) {
+                    for (int k = 0; k < nn; ++k) {
+                        const int j = __ldg(nb + (long long)k * stride);
+                        if (!flt.ok(A, j)) continue;
+                        const float r2f = screen_r2(pi4, pos4[j], R);
+                        if (r2f < rmin2f - kScreenR2 || r2f > rmax2f + kScreenR2) continue;
+                        const bool amb = !(r2f > rmin2f + kScreenR2 && r2f < rmax2f - kScreenR2);
+                        if (!amb && r2f >= 0.09f && fabsf(sqrtf(r2f) - r0f) - kScreenD > min_upper) continue;
+                        if (ncont < kContenders) A.cont[i * kContenders + ncont] = j | (amb ? (1 << 30) : 0);
+                        ++ncont;
+                    }
+                }
+                if (ncont > kContenders) ncont = kContenders + 1;   // k_exact rescans this site in full
                 else inwin += sure_in;
                 want = ncont > 0;
             } else {
-                nprop = best >= 0 ? 1ull : 0ull;
+                const double rmin2 = P.rx_rmin2[a], rmax2 = P.rx_rmax2[a];
+                const double r0 = P.br0[P.rx_bt[a]];
+                int best_tag = 0;
+                double best_r = 0.0;
+                for (int k = 0; k < nn; ++k) {
+                    const int j = __ldg(nb + (long long)k * stride);
+                    if (!flt.ok(A, j)) continue;
+                    ++scanned;
+                    const double r2 = exact_r2(A, R, (int)i, j);
+                    if (r2 < rmin2 || r2 > rmax2) continue;
+                    ++inwin;
+                    const double r = __dsqrt_rn(r2);
+                    consider(fabs(__dsub_rn(r, r0)), r, j, A.tag[j], best, best_tag, best_d, best_r);
+                }
+                nprop += best >= 0 ? 1ull : 0ull;
                 want = best >= 0;
             }
         }
         A.prop[i] = best;
-        A.prop_r[i] = best_r;
+        A.prop_d[i] = best_d;
         A.ncont[i] = ncont;
-        if (SCREEN && ncont > 0 && ncont <= kContenders)
-            for (int c = 0; c < ncont; ++c) A.cont[i * kContenders + c] = cont[c];
     }
-    const int sl = block_append(want, A.list_count);
+    const int sl = warp_append(want, A.list_count);
     if (sl >= 0) A.site_list[sl] = (int)i;
+    }
     const int idx[4] = {cNlistScanned, cScanned, cInWindow, cProposals};
     const unsigned long long v[4] = {nscan, scanned, inwin, nprop};
     warp_counts<4>(A.counters, idx, v);
 }
 
-// Exact FP64 evaluation of the screened contenders, one listed site per thread.
+// Matching: the edge i -> j gets priority w = first word of Philox(MATCH;
+// min tag, max tag); atomicMax of (w << 32 | other tag) at both endpoints.
+__device__ __forceinline__ void match_edge(DevArrays &A, const RepDev &R, int a, long long step, int i, int j)
+{
+    if (j < 0) return;
+    const uint32_t ti = (uint32_t)(A.tag[i] - R.tag_off), tj = (uint32_t)(A.tag[j] - R.tag_off);
+    const uint32_t lo = ti < tj ? ti : tj, hi = ti < tj ? tj : ti;
+    const U4 w = pair_draw(R, a, kMatch, step, lo, hi);
+    A.prio[i] = w.x;
+    const unsigned long long pr = (unsigned long long)w.x << 32;
+    atomicMax(&A.best[i], pr | tj);
+    atomicMax(&A.best[j], pr | ti);
+}
+
+// Exact FP64 evaluation of the screened contenders, one listed site per
+// thread, then the matching priority of the site's proposal edge.
 template <bool FORCED>
 __global__ void __launch_bounds__(256) k_exact(DevParams P, DevArrays A, int slot)
 {
     long long step;
     if (!sweep_active<FORCED>(P, A, step)) return;
+    if (push_type(P, A, slot) >= 0) return;
     const int nlist = *A.list_count;
     unsigned long long inwin = 0, nprop = 0;
     for (long long q = gtid(); q < nlist; q += (long long)gridDim.x * blockDim.x) {
         const int i = A.site_list[q];
         const int nc = A.ncont[i];
-        if (nc == 0) continue;                       // decided without a screen
         const int rp = A.rep[i];
         const int a = A.rx_order[rp * kMaxRx + slot];
         const RepDev &R = A.reps[rp];
+        if (nc == 0) {
+            // FP64 mode: the proposal was decided in k_propose
+            match_edge(A, R, a, step, i, A.prop[i]);
+            continue;
+        }
         const double rmin2 = P.rx_rmin2[a], rmax2 = P.rx_rmax2[a];
         const double r0 = P.br0[P.rx_bt[a]];
         int best = -1, best_tag = 0;
@@ -256,110 +369,301 @@ __global__ void __launch_bounds__(256) k_exact(DevParams P, DevArrays A, int slo
             }
         } else {
             // screen overflow: the plain exact scan
-            const int ti = A.type[i];
-            const int ta = P.rx_ta[a], tb = P.rx_tb[a];
-            const int4 dp = A.dp[i];
-            const int nn = A.nn[i];
+            const SiteFilter flt = site_filter(A, A.type[i], P.rx_ta[a], P.rx_tb[a], i);
+            const int nn = A.rnn[i];
             for (int k = 0; k < nn; ++k) {
-                const int j = A.nbr[(long long)k * P.nbr_stride + i];
-                const int tj = A.type[j];
-                const bool compat = (ti == ta && tj == tb) || (ti == tb && tj == ta);
-                if (!compat || A.occ[j] >= P.valence[tj]) continue;
-                const int tgj = A.tag[j];
-                if (tgj == dp.x || tgj == dp.y || tgj == dp.z || tgj == dp.w) continue;
+                const int j = A.rnbr[(long long)k * P.nbr_stride + i];
+                if (!flt.ok(A, j)) continue;
                 const double r2 = exact_r2(A, R, i, j);
                 if (r2 < rmin2 || r2 > rmax2) continue;
                 ++inwin;
                 const double r = __dsqrt_rn(r2);
-                consider(fabs(__dsub_rn(r, r0)), r, j, tgj, best, best_tag, best_d, best_r);
+                consider(fabs(__dsub_rn(r, r0)), r, j, A.tag[j], best, best_tag, best_d, best_r);
             }
         }
         A.prop[i] = best;
-        A.prop_r[i] = best_r;
+        A.prop_d[i] = best_d;
         if (best >= 0) ++nprop;
+        match_edge(A, R, a, step, i, best);
     }
     const int idx[2] = {cInWindow, cProposals};
     const unsigned long long v[2] = {inwin, nprop};
     warp_counts<2>(A.counters, idx, v);
 }
 
-template <bool FORCED>
-__global__ void k_match(DevParams P, DevArrays A, int slot)
+// (d, tag) keys: d = |r - r0| as FP64 bits (non-negative doubles order like
+// their bit patterns), ties to the smaller tag; lexicographic order
+__device__ __forceinline__ bool key_less(unsigned long long d, unsigned long long t, unsigned long long d2,
+                                        unsigned long long t2)
 {
-    long long step;
-    if (!sweep_active<FORCED>(P, A, step)) return;
-    const int nlist = *A.list_count;
-    for (long long q = gtid(); q < nlist; q += (long long)gridDim.x * blockDim.x) {
-        const int i = A.site_list[q];
-        const int j = A.prop[i];
-        if (j < 0) continue;
-        const int rp = A.rep[i];
-        const int a = A.rx_order[rp * kMaxRx + slot];
-        const RepDev &R = A.reps[rp];
-        const uint32_t ti = (uint32_t)(A.tag[i] - R.tag_off), tj = (uint32_t)(A.tag[j] - R.tag_off);
-        const uint32_t lo = ti < tj ? ti : tj, hi = ti < tj ? tj : ti;
-        const U4 w = pair_draw(R, a, kMatch, step, lo, hi);
-        A.prio[i] = w.x;
-        const unsigned long long pr = (unsigned long long)w.x << 32;
-        atomicMax(&A.best[i], pr | tj);
-        atomicMax(&A.best[j], pr | ti);
+    return d < d2 || (d == d2 && t < t2);
+}
+
+// (d, tag) minimum over the warp
+__device__ __forceinline__ void warp_min_key(unsigned long long &d, unsigned long long &t)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long d2 = __shfl_xor_sync(0xFFFFFFFFu, d, o);
+        const unsigned long long t2 = __shfl_xor_sync(0xFFFFFFFFu, t, o);
+        if (key_less(d2, t2, d, t)) {
+            d = d2;
+            t = t2;
+        }
     }
 }
 
-template <bool FORCED>
-__global__ void k_accept(DevParams P, DevArrays A, int slot)
+// 16-byte compare-and-swap on global memory; returns the previous value
+__device__ __forceinline__ ulonglong2 cas128(ulonglong2 *p, ulonglong2 cmp, ulonglong2 val)
 {
-    long long step;
-    if (!sweep_active<FORCED>(P, A, step)) return;
-    const int nlist = *A.list_count;
-    unsigned long long edge = 0, surv = 0, formed = 0;
-    for (long long q = gtid(); q < nlist; q += (long long)gridDim.x * blockDim.x) {
-        const int i = A.site_list[q];
-        const int j = A.prop[i];
-        if (j < 0) continue;
-        const int rp = A.rep[i];
-        const int a = A.rx_order[rp * kMaxRx + slot];
-        const RepDev &R = A.reps[rp];
-        const uint32_t ti = (uint32_t)(A.tag[i] - R.tag_off), tj = (uint32_t)(A.tag[j] - R.tag_off);
-        // a mutual proposal is one edge, handled by its smaller tag
-        if (A.prop[j] == i && tj < ti) continue;
-        ++edge;
-        const unsigned long long pr = (unsigned long long)A.prio[i] << 32;
-        if (A.best[i] != (pr | tj) || A.best[j] != (pr | ti)) continue;
-        ++surv;
-        const uint32_t lo = ti < tj ? ti : tj, hi = ti < tj ? tj : ti;
-        const U4 w = pair_draw(R, a, kForm, step, lo, hi);
-        const double u = u53(w.x, w.y);
-        const int bt = P.rx_bt[a];
-        const double dr = __dsub_rn(A.prop_r[i], P.br0[bt]);
-        const double U = __dmul_rn(__dmul_rn(__dmul_rn(0.5, P.bk[bt]), dr), dr);
-        double pon;
-        if (R.kT > 0.0) {
-            const double e = __ddiv_rn(U, R.kT);
-            pon = __dmul_rn(R.p_on0[a], exp_cw(-e));
-        } else {
-            pon = (U <= 0.0) ? R.p_on0[a] : 0.0;
-        }
-        if (u < pon) {
-            ++formed;
-            A.fpart[i] = j;
-            A.fpart[j] = i;
-        }
-    }
-    const int idx[4] = {cEdges, cSurvivors, cFormed, cFormedTotal};
-    const unsigned long long v[4] = {edge, surv, formed, formed};
-    warp_counts<4>(A.counters, idx, v);
+    ulonglong2 old;
+    asm volatile(
+        "{\n\t.reg .b128 c, v, d;\n\t"
+        "mov.b128 c, {%2, %3};\n\t"
+        "mov.b128 v, {%4, %5};\n\t"
+        "atom.global.cas.b128 d, [%6], c, v;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t}"
+        : "=l"(old.x), "=l"(old.y)
+        : "l"(cmp.x), "l"(cmp.y), "l"(val.x), "l"(val.y), "l"(p)
+        : "memory");
+    return old;
 }
 
+// Lowers *p to (d, t) if smaller.  Lock-free: a failed exchange means another
+// pusher lowered the key; the retries are bounded by the pushers of one site
+// (the cap only guards against a defect, and latches a status bit).
+__device__ __forceinline__ void atomic_min_key(ulonglong2 *p, unsigned long long d, unsigned long long t,
+                                               uint32_t *status)
+{
+    ulonglong2 cur = *p;
+    for (int it = 0; it < (1 << 16); ++it) {
+        if (!key_less(d, t, cur.x, cur.y)) return;
+        const ulonglong2 old = cas128(p, cur, make_ulonglong2(d, t));
+        if (old.x == cur.x && old.y == cur.y) return;
+        cur = old;
+    }
+    atomicOr(status, (uint32_t)kStTimeout);
+}
+
+// Push mode, pass 1: one warp per pushing site (from the compacted list),
+// its lanes over the site's reactive list.  Every in-window pair lowers the
+// candidate's (d, tag) key by a 16-byte atomic; the pushing site's own
+// proposal is the warp minimum, made here with its matching priority.  The
+// pair distances are kept for pass 2.
 template <bool FORCED>
-__global__ void k_break(DevParams P, DevArrays A, int slot)
+__global__ void __launch_bounds__(256) k_push(DevParams P, DevArrays A, int slot)
 {
     long long step;
     if (!sweep_active<FORCED>(P, A, step)) return;
-    const long long i = gtid();
-    unsigned long long tested = 0;
-    const int4 dp = i < P.n ? A.dp[i] : make_int4(-1, -1, -1, -1);
+    const int s = push_type(P, A, slot);
+    if (s < 0) return;
+    const int a = A.rx_order[slot];
+    const int ta = P.rx_ta[a], tb = P.rx_tb[a];
+    const RepDev &R = A.reps[0];
+    const double rmin2 = P.rx_rmin2[a], rmax2 = P.rx_rmax2[a];
+    const double r0 = P.br0[P.rx_bt[a]];
+    const long long stride = P.nbr_stride;
+    const int lane = threadIdx.x & 31;
+    unsigned long long scanned = 0, inwin = 0, nscan = 0, nprop = 0;
+    const int ns = A.avail_count[s];
+    const int32_t *list = A.avail_list + (long long)s * P.n;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const float rmin2f = (float)rmin2, rmax2f = (float)rmax2;
+    const float4 *pos4 = reinterpret_cast<const float4 *>(A.pos4);
+    for (long long q = gtid() >> 5; q < ns; q += warps) {
+        const int i = list[q];
+        const SiteFilter flt = site_filter(A, s, ta, tb, i);
+        const int nn = A.rnn[i];
+        if (lane == 0) nscan += (unsigned long long)nn;
+        const uint32_t bi = cell_bits(P, A, i);
+        const float4 pi4 = P.screen ? pos4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const unsigned long long me = (unsigned long long)(uint32_t)A.tag[i];
+        unsigned long long bd = ~0ull, bt = ~0ull;     // this site's best (d, partner tag)
+        for (int k = lane; k < nn; k += 32) {
+            const int j = __ldg(A.rnbr + (long long)k * stride + i);
+            unsigned long long d = ~0ull;                // not a candidate
+            if (flt.ok(A, j)) {
+                scanned += 2;                            // the pair, as both of its sites see it
+                bool maybe = true;
+                uint32_t bj;
+                if (P.screen) {                          // mixed mode: FP32 pre-screen of the window
+                    const float4 pj4 = pos4[j];
+                    bj = w_bits(pj4);
+                    const float r2f = screen_r2(pi4, pj4, R);
+                    maybe = !(r2f < rmin2f - kScreenR2 || r2f > rmax2f + kScreenR2);
+                } else {
+                    bj = cell_bits(P, A, j);
+                }
+                const double r2 = maybe ? exact_r2_cells(A, R, i, j, bi, bj) : -1.0;
+                if (maybe && r2 >= rmin2 && r2 <= rmax2) {
+                    inwin += 2;
+                    d = (unsigned long long)__double_as_longlong(fabs(__dsub_rn(__dsqrt_rn(r2), r0)));
+                    atomic_min_key(&A.pkey[j], d, me, A.status);
+                    const unsigned long long tj = (unsigned long long)(uint32_t)A.tag[j];
+                    if (key_less(d, tj, bd, bt)) {
+                        bd = d;
+                        bt = tj;
+                    }
+                }
+            }
+            if (q < P.pdist_rows && k < kPushSlots) A.pdist[q * kPushSlots + k] = d;
+        }
+        warp_min_key(bd, bt);
+        if (lane == 0 && bd != ~0ull) {
+            const int c = A.rtag[(uint32_t)bt];
+            A.prop[i] = c;
+            A.prop_d[i] = __longlong_as_double((long long)bd);
+            match_edge(A, R, a, step, i, c);
+            ++nprop;
+        }
+    }
+    const int idx[5] = {cNlistScanned, cScanned, cInWindow, cProposals, cEdges};
+    const unsigned long long v[5] = {nscan, scanned, inwin, nprop, nprop};
+    warp_counts<5>(A.counters, idx, v);
+}
+
+// Push mode, pass 2 (same mapping): the winning pusher of each candidate (its
+// (d, tag) is the candidate's key) sets the candidate's proposal and matching
+// priority.  The edge is new unless the pushing site proposed it too.  The
+// keys are cleared by k_apply.
+template <bool FORCED>
+__global__ void __launch_bounds__(256) k_push_win(DevParams P, DevArrays A, int slot)
+{
+    long long step;
+    if (!sweep_active<FORCED>(P, A, step)) return;
+    const int s = push_type(P, A, slot);
+    if (s < 0) return;
+    const int a = A.rx_order[slot];
+    const int ta = P.rx_ta[a], tb = P.rx_tb[a];
+    const RepDev &R = A.reps[0];
+    const double rmin2 = P.rx_rmin2[a], rmax2 = P.rx_rmax2[a];
+    const double r0 = P.br0[P.rx_bt[a]];
+    const long long stride = P.nbr_stride;
+    const int lane = threadIdx.x & 31;
+    const int ns = A.avail_count[s];
+    const int32_t *list = A.avail_list + (long long)s * P.n;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    unsigned long long nprop = 0, nedge = 0;
+    for (long long q = gtid() >> 5; q < ns; q += warps) {
+        const int i = list[q];
+        if (A.prop[i] < 0) continue;                     // warp-uniform: no candidate in window
+        const SiteFilter flt = site_filter(A, s, ta, tb, i);
+        const int nn = A.rnn[i];
+        const unsigned long long me = (unsigned long long)(uint32_t)A.tag[i];
+        const int pi = A.prop[i];
+        for (int k = lane; k < nn; k += 32) {
+            const int j = __ldg(A.rnbr + (long long)k * stride + i);
+            unsigned long long d;
+            if (q < P.pdist_rows && k < kPushSlots) {
+                d = A.pdist[q * kPushSlots + k];
+                if (d == ~0ull) continue;
+            } else {
+                if (!flt.ok(A, j)) continue;
+                const double r2 = exact_r2(A, R, i, j);
+                if (r2 < rmin2 || r2 > rmax2) continue;
+                d = (unsigned long long)__double_as_longlong(fabs(__dsub_rn(__dsqrt_rn(r2), r0)));
+            }
+            const ulonglong2 kj = A.pkey[j];
+            if (kj.x != d || kj.y != me) continue;
+            A.prop[j] = i;
+            A.prop_d[j] = __longlong_as_double((long long)d);
+            match_edge(A, R, a, step, j, i);
+            ++nprop;
+            if (pi != j) ++nedge;
+        }
+    }
+    const int idx[2] = {cProposals, cEdges};
+    const unsigned long long v[2] = {nprop, nedge};
+    warp_counts<2>(A.counters, idx, v);
+}
+
+// Acceptance of the listed sites' edges (thread q < list length) and the
+// breaking draws of the bonds of particle i (thread i < n) in one launch: both
+// read the state as it was before this reaction and write disjoint outputs
+// (fpart; the brk bits).
+template <bool FORCED>
+__global__ void k_accept_break(DevParams P, DevArrays A, int slot)
+{
+    long long step;
+    if (!sweep_active<FORCED>(P, A, step)) return;
+    const long long g = gtid();
+    unsigned long long edge = 0, surv = 0, formed = 0, tested = 0;
+    const int ps = push_type(P, A, slot);
+    if (ps >= 0) {
+        // push mode: every edge has a pushing end; the edge that can survive at
+        // pushing site c is the one its best[] names (its low word is the
+        // other end's tag)
+        if (g < A.avail_count[ps]) {
+            const int c = A.avail_list[(long long)ps * P.n + g];
+            const unsigned long long bc = A.best[c];
+            if (bc != 0ull) {
+                const int a = A.rx_order[slot];
+                const RepDev &R = A.reps[0];
+                const uint32_t tc = (uint32_t)(A.tag[c] - R.tag_off), tj = (uint32_t)bc;
+                const int j = A.rtag[tj + R.tag_off];
+                const unsigned long long pr = bc & 0xFFFFFFFF00000000ull;
+                if (A.best[j] == (pr | tc)) {
+                    ++surv;
+                    const uint32_t lo = tc < tj ? tc : tj, hi = tc < tj ? tj : tc;
+                    const U4 w = pair_draw(R, a, kForm, step, lo, hi);
+                    const double u = u53(w.x, w.y);
+                    const int bt = P.rx_bt[a];
+                    // U = k (r - r0)^2 / 2 from d = |r - r0| of whichever end proposed the edge
+                    const double d = A.prop[c] == j ? A.prop_d[c] : A.prop_d[j];
+                    const double U = __dmul_rn(__dmul_rn(__dmul_rn(0.5, P.bk[bt]), d), d);
+                    double pon;
+                    if (R.kT > 0.0) pon = __dmul_rn(R.p_on0[a], exp_cw(-__ddiv_rn(U, R.kT)));
+                    else pon = (U <= 0.0) ? R.p_on0[a] : 0.0;
+                    if (u < pon) {
+                        ++formed;
+                        A.fpart[c] = j;
+                        A.fpart[j] = c;
+                    }
+                }
+            }
+        }
+    }
+    const int nlist = ps >= 0 ? 0 : *A.list_count;
+    if (g < nlist) {
+        const int i = A.site_list[g];
+        const int j = A.prop[i];
+        if (j >= 0) {
+            const int rp = A.rep[i];
+            const int a = A.rx_order[rp * kMaxRx + slot];
+            const RepDev &R = A.reps[rp];
+            const uint32_t ti = (uint32_t)(A.tag[i] - R.tag_off), tj = (uint32_t)(A.tag[j] - R.tag_off);
+            // a mutual proposal is one edge, handled by its smaller tag
+            if (!(A.prop[j] == i && tj < ti)) {
+                ++edge;
+                const unsigned long long pr = (unsigned long long)A.prio[i] << 32;
+                if (A.best[i] == (pr | tj) && A.best[j] == (pr | ti)) {
+                    ++surv;
+                    const uint32_t lo = ti < tj ? ti : tj, hi = ti < tj ? tj : ti;
+                    const U4 w = pair_draw(R, a, kForm, step, lo, hi);
+                    const double u = u53(w.x, w.y);
+                    const int bt = P.rx_bt[a];
+                    // U = k (r - r0)^2 / 2 from d = |r - r0| (the sign of r - r0 cancels exactly)
+                    const double d = A.prop_d[i];
+                    const double U = __dmul_rn(__dmul_rn(__dmul_rn(0.5, P.bk[bt]), d), d);
+                    double pon;
+                    if (R.kT > 0.0) {
+                        const double e = __ddiv_rn(U, R.kT);
+                        pon = __dmul_rn(R.p_on0[a], exp_cw(-e));
+                    } else {
+                        pon = (U <= 0.0) ? R.p_on0[a] : 0.0;
+                    }
+                    if (u < pon) {
+                        ++formed;
+                        A.fpart[i] = j;
+                        A.fpart[j] = i;
+                    }
+                }
+            }
+        }
+    }
+    const int4 dp = g < P.n ? A.dp[g] : make_int4(-1, -1, -1, -1);
     if (dp.x >= 0) {
+        const long long i = g;
         const int rp = A.rep[i];
         const int a = A.rx_order[rp * kMaxRx + slot];
         const RepDev &R = A.reps[rp];
@@ -389,9 +693,9 @@ __global__ void k_break(DevParams P, DevArrays A, int slot)
             }
         }
     }
-    const int idx[1] = {cBreakTested};
-    const unsigned long long v[1] = {tested};
-    warp_counts<1>(A.counters, idx, v);
+    const int idx[5] = {cEdges, cSurvivors, cFormed, cFormedTotal, cBreakTested};
+    const unsigned long long v[5] = {edge, surv, formed, formed, tested};
+    warp_counts<5>(A.counters, idx, v);
 }
 
 template <bool FORCED>
@@ -401,8 +705,18 @@ __global__ void k_apply(DevParams P, DevArrays A, int slot)
     if (!sweep_active<FORCED>(P, A, step)) return;
     const long long i = gtid();
     if (i == 0) *A.list_count = 0;   // next reaction starts an empty list
+    if (i < kMaxTypes && slot == P.nrx - 1) A.avail_count[i] = 0;   // the next sweep recounts
     const uint32_t b = i < P.n ? A.brk[i] : 0u;
     const int f = i < P.n ? A.fpart[i] : -1;
+    if (i < P.n) {
+        // scratch for the next reaction
+        A.brk[i] = 0u;
+        A.fpart[i] = -1;
+        A.best[i] = 0ull;
+        A.prop[i] = -1;
+        const ulonglong2 k = A.pkey[i];
+        if (k.x != ~0ull || k.y != ~0ull) A.pkey[i] = make_ulonglong2(~0ull, ~0ull);
+    }
     unsigned long long nbroken = 0;
     if (b != 0u || f >= 0) {
         const int me = A.tag[i];
@@ -444,6 +758,8 @@ __global__ void k_apply(DevParams P, DevArrays A, int slot)
         A.dbirth[i] = make_int4(nb[0], nb[1], nb[2], nb[3]);
         A.drx[i] = (nr[0] & 0xFF) | ((nr[1] & 0xFF) << 8) | ((nr[2] & 0xFF) << 16) | ((nr[3] & 0xFF) << 24);
         A.occ[i] = m;
+        const int t = A.type[i];
+        A.avail[i] = m < P.valence[t] ? (uint8_t)t : (uint8_t)0xFF;
     }
     const int idx[2] = {cBroken, cBrokenTotal};
     const unsigned long long v[2] = {nbroken, nbroken};
@@ -592,7 +908,8 @@ inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block 
 template <bool FORCED>
 void sweep_begin(const DevParams &P, const DevArrays &A, Launch L)
 {
-    k_sweep_begin<FORCED><<<grid_for(P.nrep, 128), 128, 0, L.stream>>>(P, A);
+    k_sweep_begin<FORCED><<<grid_for(std::max<long long>(P.n, P.nrep), kSweepBeginBlock), kSweepBeginBlock, 0,
+                            L.stream>>>(P, A);
 }
 
 template <bool FORCED>
@@ -601,16 +918,15 @@ void sweep_reaction(const DevParams &P, const DevArrays &A, int slot, Launch L)
     if (P.n == 0) return;
     const unsigned g = grid_for(P.n, L.block);
     const unsigned gl = kListBlocks;
-    if (P.screen) {
-        k_propose<FORCED, true><<<g, L.block, 0, L.stream>>>(P, A, slot);
-        k_exact<FORCED><<<gl, 256, 0, L.stream>>>(P, A, slot);
-    } else {
-        k_propose<FORCED, false><<<g, L.block, 0, L.stream>>>(P, A, slot);
-    }
-    k_match<FORCED><<<gl, 256, 0, L.stream>>>(P, A, slot);
-    k_accept<FORCED><<<gl, 256, 0, L.stream>>>(P, A, slot);
+    const unsigned gprop = (unsigned)std::min<long long>(g, 8LL * sm_count() * (256 / L.block));
+    if (P.screen) k_propose<FORCED, true><<<gprop, L.block, 0, L.stream>>>(P, A, slot);
+    else k_propose<FORCED, false><<<gprop, L.block, 0, L.stream>>>(P, A, slot);
+    k_exact<FORCED><<<gl, 256, 0, L.stream>>>(P, A, slot);
+    const unsigned gp = (unsigned)std::min<long long>(grid_for(P.n, 256), 4LL * sm_count());
+    k_push<FORCED><<<gp, 256, 0, L.stream>>>(P, A, slot);
+    k_push_win<FORCED><<<gp, 256, 0, L.stream>>>(P, A, slot);
+    k_accept_break<FORCED><<<g, L.block, 0, L.stream>>>(P, A, slot);
     if (P.log_events) launch_log_events(P, A, slot, FORCED, L);
-    k_break<FORCED><<<g, L.block, 0, L.stream>>>(P, A, slot);
     k_apply<FORCED><<<g, L.block, 0, L.stream>>>(P, A, slot);
 }
 

@@ -68,10 +68,10 @@ __device__ __forceinline__ int partner_type(const DevParams &P, int a, int t)
 __device__ int coord_count(const DevParams &P, const DevArrays &A, const RepDev &R, int a, int x)
 {
     const int pt = partner_type(P, a, A.type[x]);
-    const int nn = A.nn[x];
+    const int nn = A.rnn[x];
     int c = 0;
     for (int k = 0; k < nn; ++k) {
-        const int y = A.nbr[(long long)k * P.nbr_stride + x];
+        const int y = A.rnbr[(long long)k * P.nbr_stride + x];
         if (A.type[y] != pt) continue;
         const double r2 = exact_r2(A, R, x, y);
         if (r2 >= P.rx_rmin2[a] && r2 <= P.rx_rmax2[a]) ++c;
@@ -110,10 +110,10 @@ __device__ int candidates(const DevParams &P, const DevArrays &A, const RepDev &
     const int ti = A.type[i];
     const int4 dp = A.dp[i];
     const int tag_i = A.tag[i];
-    const int nn = A.nn[i];
+    const int nn = A.rnn[i];
     int n = 0;
     for (int k = 0; k < nn; ++k) {
-        const int j = A.nbr[(long long)k * P.nbr_stride + i];
+        const int j = A.rnbr[(long long)k * P.nbr_stride + i];
         const int tj = A.type[j];
         const bool compat = (ti == P.rx_ta[a] && tj == P.rx_tb[a]) || (ti == P.rx_tb[a] && tj == P.rx_ta[a]);
         if (!compat) continue;
@@ -463,11 +463,9 @@ __global__ void k_log_events(DevParams P, DevArrays A, int slot)
 {
     long long step;
     if (!mh_active<FORCED>(P, A, step)) return;
-    const int nlist = *A.list_count;
     unsigned long long logged = 0;
-    for (long long q = gtid(); q < nlist; q += (long long)gridDim.x * blockDim.x) {
-        const int i = A.site_list[q];
-        const int j = A.prop[i];
+    for (long long i = gtid(); i < P.n; i += (long long)gridDim.x * blockDim.x) {
+        const int j = A.prop[(int)i];
         if (j < 0 || A.fpart[i] != j) continue;
         const int rp = A.rep[i];
         const int a = A.rx_order[rp * kMaxRx + slot];

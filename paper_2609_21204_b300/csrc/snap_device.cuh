@@ -26,6 +26,7 @@ enum StatusBit : uint32_t {
     kStOverflow = 1u << 0,
     kStFene = 1u << 1,
     kStNonfinite = 1u << 2,
+    kStTimeout = 1u << 3,   // a bounded retry loop gave up (a defect; the step is not trusted)
 };
 
 // ------------------------------------------------------------ parameters
@@ -35,7 +36,8 @@ struct DevParams {
     int32_t valence[kMaxTypes];
     // pair tables, index ti*kMaxTypes+tj
     float rc2f[kMaxTypes * kMaxTypes];      // pair cut-off squared
-    float rl2f[kMaxTypes * kMaxTypes];      // neighbour-list build cut-off squared
+    float fl2f[kMaxTypes * kMaxTypes];      // force-list cut-off squared: (pair cut + skin)^2
+    float xl2f[kMaxTypes * kMaxTypes];      // reactive-list cut-off squared: (r_max + skin)^2, 0: none
     float sig2f[kMaxTypes * kMaxTypes], eps24f[kMaxTypes * kMaxTypes], shiftf[kMaxTypes * kMaxTypes];
     double rc2d[kMaxTypes * kMaxTypes];
     double sig2d[kMaxTypes * kMaxTypes], eps24d[kMaxTypes * kMaxTypes], shiftd[kMaxTypes * kMaxTypes];
@@ -49,15 +51,17 @@ struct DevParams {
     // integrator
     double dt, half_dt, gamma, sqrt3;
     float disp2f;           // squared displacement that triggers a rebuild
-    int32_t nbr_cap;        // neighbours per particle
+    int32_t nbr_cap;        // force-list entries per particle
+    int32_t rnbr_cap;       // reactive-list entries per particle
     int64_t n;              // particles (all replicas)
-    int64_t nbr_stride;     // column stride of the neighbour list
+    int64_t nbr_stride;     // column stride of both neighbour lists
     int32_t nrep;
     int32_t screen;         // mixed mode: FP32 pre-screen of the proposal test, FP32 velocities
     int32_t ncell;          // cells over all replicas; sort keys are type * ncell + cell
     int32_t mh_cells, mh_moves;   // MH checkerboard cells and active cells per sweep
     float mh_eps;           // weight of the uniform component of the learned proposal
     int32_t log_events;     // record bond-formation events in the plain sweep
+    int64_t pdist_rows;     // pushing sites whose pair distances fit the pdist scratch
 };
 
 struct RepDev {
@@ -91,12 +95,18 @@ struct DevArrays {
     int32_t *drx;                   // reaction index per dynamic slot, 8 bits each, packed
     int4 *dbirth;                   // step (low 32 bits) at which each dynamic bond formed
     int32_t *occ;                   // dynamic bonds held
-    int32_t *nbr, *nn;              // neighbour list (column-major) and counts
+    uint8_t *avail;                 // type if occ < valence, else 0xFF (set per sweep)
+    int32_t *avail_count;           // available particles per type (this sweep; kMaxTypes)
+    int32_t *avail_list;            // push mode: available particles of type t at t * n + k
+    ulonglong2 *pkey;               // push mode: smallest (|r - r0| as FP64 bits, pusher tag) pushed to a site
+    unsigned long long *pdist;      // push mode: pair distances of pass 1, kPushSlots per pushing site
+    int32_t *nbr, *nn;              // force list (column-major): pairs within pair cut + skin
+    int32_t *rnbr, *rnn;            // reactive list: compatible pairs within r_max + skin
     // cell list
     int32_t *cell_count, *cell_start, *cell_cursor, *cell_key, *order, *rank_of;
     // sweep scratch
     int32_t *prop;                  // proposed partner index or -1
-    double *prop_r;
+    double *prop_d;                 // |r - r0| of the proposal (FP64)
     uint32_t *prio;
     unsigned long long *best;
     int32_t *fpart;                 // formed partner index or -1
@@ -110,7 +120,7 @@ struct DevArrays {
     long long *step;                // device step counter
     uint32_t *status;
     int32_t *need_rebuild;
-    int32_t *nbr_need;              // largest neighbour count seen (overflow sizing)
+    int32_t *nbr_need;              // largest [force, reactive] count seen (overflow sizing)
     unsigned long long *counters;   // sweep counters, see Counter
     unsigned long long *life_hist;
     double *e_part;                 // per-particle energy scratch
@@ -129,12 +139,13 @@ struct DevArrays {
 constexpr int kMhCand = 16;         // candidates per MH move or logged event
 
 constexpr int kContenders = 4;
+constexpr int kPushSlots = 64;     // push mode: pair distances kept per pushing site
 constexpr int kCopies = 32;        // each counter is spread over this many words
 
 enum Counter {
     cScanned = 0, cInWindow, cProposals, cEdges, cSurvivors, cFormed, cBreakTested, cBroken,
     cSweeps, cFormedTotal, cBrokenTotal, cBuilds, cNlistScanned, cNlistEntries,
-    cMhFormAtt, cMhFormAcc, cMhBreakAtt, cMhBreakAcc, cEvents, cNumCounters
+    cMhFormAtt, cMhFormAcc, cMhBreakAtt, cMhBreakAcc, cEvents, cRnlistEntries, cRebuildLaunches, cNumCounters
 };
 
 // ------------------------------------------------------------ Philox-4x32-10
@@ -304,6 +315,19 @@ __device__ __forceinline__ void counter_reset(unsigned long long *ctr, int c)
 __device__ __forceinline__ void counter_add1(unsigned long long *ctr, int c, unsigned long long v)
 {
     ctr[c * kCopies] += v;
+}
+
+// Warp-aggregated append of flagged items to a global list: every lane of the
+// warp must call this; returns the slot of this lane's item (or -1).  One
+// atomic per warp with work and no block barrier.
+__device__ __forceinline__ int warp_append(bool want, int32_t *count)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    return want ? base + __popc(m & ((1u << lane) - 1u)) : -1;
 }
 
 // Block-aggregated append of flagged items to a global list: every thread of

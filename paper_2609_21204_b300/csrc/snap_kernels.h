@@ -11,6 +11,9 @@ struct Launch {
     int block;       // threads per block for particle-parallel kernels
 };
 
+// multiprocessors of the current device (cached per device)
+int sm_count();
+
 // ---- neighbour-list maintenance (all early-exit unless *need_rebuild) ----
 void launch_cell_key(const DevParams &P, const DevArrays &A, Launch L);
 void launch_cell_scan(const DevArrays &A, int32_t *block_sums, int ncell, Launch L);

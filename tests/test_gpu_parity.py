@@ -49,6 +49,9 @@ def _sweep_cases():
         "colloid_linker": lambda: colloid_linker(seed=3, n_c=2000, n_l=8000, eps=3.0),
         "telechelic": lambda: telechelic(seed=4, n_chains=200, n_x=400),
         "tiny_ragged": lambda: random_frozen(seed=5, n=37, box=5.3, overlap_factor=0.5, r_max=1.4),
+        # one side scarce (10% A): proposals by push from the scarce side
+        "scarce_push": lambda: random_frozen(seed=7, n=5000, box=15.0, type_fracs=(0.1, 0.9),
+                                             overlap_factor=0.6, r_max=1.4, valence=(2, 1)),
         "kT0": lambda: _kt0(),
     }
 
