@@ -229,12 +229,9 @@ __device__ __forceinline__ float screen_r2(const float4 &pi4, const float4 &pj4,
 // keeps (in list order, at most kContenders) every candidate that may still
 // win — window-ambiguous, too close for the bound, or within the margin of
 // that bound — for k_exact to decide in FP64.
-template <bool FORCED, bool SCREEN>
-__global__ void __launch_bounds__(256) k_propose(DevParams P, DevArrays A, int slot)
+template <bool SCREEN>
+__device__ __forceinline__ void pull_propose(const DevParams &P, DevArrays &A, int slot)
 {
-    long long step;
-    if (!sweep_active<FORCED>(P, A, step)) return;   // uniform over the grid
-    if (push_type(P, A, slot) >= 0) return;          // uniform: push mode decides this reaction
     unsigned long long scanned = 0, inwin = 0, nscan = 0, nprop = 0;
     // grid-stride with a warp-uniform trip count (a small grid exits cheaply in push mode)
     for (long long base = (long long)blockIdx.x * blockDim.x; base < P.n; base += (long long)gridDim.x * blockDim.x) {
@@ -334,12 +331,8 @@ __device__ __forceinline__ void match_edge(DevArrays &A, const RepDev &R, int a,
 
 // Exact FP64 evaluation of the screened contenders, one listed site per
 // thread, then the matching priority of the site's proposal edge.
-template <bool FORCED>
-__global__ void __launch_bounds__(256) k_exact(DevParams P, DevArrays A, int slot)
+__device__ __forceinline__ void pull_exact(const DevParams &P, DevArrays &A, int slot, long long step)
 {
-    long long step;
-    if (!sweep_active<FORCED>(P, A, step)) return;
-    if (push_type(P, A, slot) >= 0) return;
     const int nlist = *A.list_count;
     unsigned long long inwin = 0, nprop = 0;
     for (long long q = gtid(); q < nlist; q += (long long)gridDim.x * blockDim.x) {
@@ -450,13 +443,8 @@ __device__ __forceinline__ void atomic_min_key(ulonglong2 *p, unsigned long long
 // candidate's (d, tag) key by a 16-byte atomic; the pushing site's own
 // proposal is the warp minimum, made here with its matching priority.  The
 // pair distances are kept for pass 2.
-template <bool FORCED>
-__global__ void __launch_bounds__(256) k_push(DevParams P, DevArrays A, int slot)
+__device__ __forceinline__ void push_pass1(const DevParams &P, DevArrays &A, int slot, long long step, int s)
 {
-    long long step;
-    if (!sweep_active<FORCED>(P, A, step)) return;
-    const int s = push_type(P, A, slot);
-    if (s < 0) return;
     const int a = A.rx_order[slot];
     const int ta = P.rx_ta[a], tb = P.rx_tb[a];
     const RepDev &R = A.reps[0];
@@ -526,13 +514,8 @@ __global__ void __launch_bounds__(256) k_push(DevParams P, DevArrays A, int slot
 // (d, tag) is the candidate's key) sets the candidate's proposal and matching
 // priority.  The edge is new unless the pushing site proposed it too.  The
 // keys are cleared by k_apply.
-template <bool FORCED>
-__global__ void __launch_bounds__(256) k_push_win(DevParams P, DevArrays A, int slot)
+__device__ __forceinline__ void push_pass2(const DevParams &P, DevArrays &A, int slot, long long step, int s)
 {
-    long long step;
-    if (!sweep_active<FORCED>(P, A, step)) return;
-    const int s = push_type(P, A, slot);
-    if (s < 0) return;
     const int a = A.rx_order[slot];
     const int ta = P.rx_ta[a], tb = P.rx_tb[a];
     const RepDev &R = A.reps[0];
@@ -575,6 +558,29 @@ __global__ void __launch_bounds__(256) k_push_win(DevParams P, DevArrays A, int 
     const int idx[2] = {cProposals, cEdges};
     const unsigned long long v[2] = {nprop, nedge};
     warp_counts<2>(A.counters, idx, v);
+}
+
+// The two proposal kernels of a reaction: each runs the scan (pull) or the
+// push version of its phase, as push_type decides for this reaction, so the
+// mode that is not used costs no launch.
+template <bool FORCED, bool SCREEN>
+__global__ void __launch_bounds__(256, 4) k_proposals(DevParams P, DevArrays A, int slot)
+{
+    long long step;
+    if (!sweep_active<FORCED>(P, A, step)) return;   // uniform over the grid
+    const int s = push_type(P, A, slot);
+    if (s >= 0) push_pass1(P, A, slot, step, s);
+    else pull_propose<SCREEN>(P, A, slot);
+}
+
+template <bool FORCED>
+__global__ void __launch_bounds__(256) k_resolve(DevParams P, DevArrays A, int slot)
+{
+    long long step;
+    if (!sweep_active<FORCED>(P, A, step)) return;
+    const int s = push_type(P, A, slot);
+    if (s >= 0) push_pass2(P, A, slot, step, s);
+    else pull_exact(P, A, slot, step);
 }
 
 // Acceptance of the listed sites' edges (thread q < list length) and the
@@ -918,13 +924,13 @@ void sweep_reaction(const DevParams &P, const DevArrays &A, int slot, Launch L)
     if (P.n == 0) return;
     const unsigned g = grid_for(P.n, L.block);
     const unsigned gl = kListBlocks;
+    // grid-stride kernels: enough resident blocks for the scan, and one warp
+    // per pushing site in push mode
     const unsigned gprop = (unsigned)std::min<long long>(g, 8LL * sm_count() * (256 / L.block));
-    if (P.screen) k_propose<FORCED, true><<<gprop, L.block, 0, L.stream>>>(P, A, slot);
-    else k_propose<FORCED, false><<<gprop, L.block, 0, L.stream>>>(P, A, slot);
-    k_exact<FORCED><<<gl, 256, 0, L.stream>>>(P, A, slot);
-    const unsigned gp = (unsigned)std::min<long long>(grid_for(P.n, 256), 4LL * sm_count());
-    k_push<FORCED><<<gp, 256, 0, L.stream>>>(P, A, slot);
-    k_push_win<FORCED><<<gp, 256, 0, L.stream>>>(P, A, slot);
+    if (P.screen) k_proposals<FORCED, true><<<gprop, L.block, 0, L.stream>>>(P, A, slot);
+    else k_proposals<FORCED, false><<<gprop, L.block, 0, L.stream>>>(P, A, slot);
+    k_resolve<FORCED><<<std::max<unsigned>(gl, (unsigned)std::min<long long>(grid_for(P.n, 256), 4LL * sm_count())),
+                        256, 0, L.stream>>>(P, A, slot);
     k_accept_break<FORCED><<<g, L.block, 0, L.stream>>>(P, A, slot);
     if (P.log_events) launch_log_events(P, A, slot, FORCED, L);
     k_apply<FORCED><<<g, L.block, 0, L.stream>>>(P, A, slot);
