@@ -415,13 +415,12 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
     sweep_pairs = st2["scanned"] + st2["break_tested"]
     bond_pairs_per_s = sweep_pairs / (ph["sweep"] / 1e3) if ph["sweep"] > 0 else None
 
-    # kernels launched: per step the rebuild condition, the sweep (begin + 7 per
-    # reaction: scan or push proposals in 5 kernels of which one mode's exit at
-    # once, accept/break, apply), force, integrate and step end; per rebuild 10
-    # more (cell keys, 3 scan kernels, scatter, cell sort, gather, copy back,
-    # lists, done)
+    # kernels launched: per step the rebuild condition, the sweep (begin + 4 per
+    # reaction: proposals, resolution, accept/break, apply), force, integrate
+    # and step end; per rebuild 10 more (cell keys, 3 scan kernels, scatter,
+    # cell sort, gather, copy back, lists, done)
     builds = st1["nlist_builds"] - st0["nlist_builds"]
-    launches = K * (1 + (1 + 7 * len(s.reactions)) + 3) + 10 * builds
+    launches = K * (1 + (1 + 4 * len(s.reactions)) + 3) + 10 * builds
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,

@@ -25,6 +25,7 @@
 #include <algorithm>
 
 #include "snap_kernels.h"
+#include "apply.cuh"
 
 namespace snap {
 
@@ -155,10 +156,11 @@ __device__ __forceinline__ void consider(double d, double r, int j, int tgj, int
 }
 
 // Conservative single-precision screen for the exact FP64 proposal test.
-// With cell-relative FP32 coordinates (|rel| < 4, each rounded once), the
-// FP32 separation of a listed pair differs from the exact one by less than
-// 1.3e-6 per component, so r^2 by less than 1.2e-5 (r < 2) and |r - r0| by
-// less than 2e-5 when r^2 >= 0.09.  With margins of 1e-4 a candidate is
+// The cell-relative FP32 coordinates (|rel| < 4) are within 2e-6 of the FP64
+// ones (rounded from them at most kMixedResync = 8 steps ago, advanced by FP32
+// steps since), so the FP32 separation of a listed pair is within 4.2e-6 per
+// component (7.3e-6 in length), r^2 within 3e-5 (r < 2) and |r - r0| within
+// 1e-5 when r^2 >= 0.09.  With margins of 1e-4 a candidate is
 // dropped in FP32 only when the exact test would reject it or when another
 // candidate surely beats it; every candidate that may win is re-evaluated in
 // FP64 by k_exact, in dense warps.
@@ -709,64 +711,8 @@ __global__ void k_apply(DevParams P, DevArrays A, int slot)
 {
     long long step;
     if (!sweep_active<FORCED>(P, A, step)) return;
-    const long long i = gtid();
-    if (i == 0) *A.list_count = 0;   // next reaction starts an empty list
-    if (i < kMaxTypes && slot == P.nrx - 1) A.avail_count[i] = 0;   // the next sweep recounts
-    const uint32_t b = i < P.n ? A.brk[i] : 0u;
-    const int f = i < P.n ? A.fpart[i] : -1;
-    if (i < P.n) {
-        // scratch for the next reaction
-        A.brk[i] = 0u;
-        A.fpart[i] = -1;
-        A.best[i] = 0ull;
-        A.prop[i] = -1;
-        const ulonglong2 k = A.pkey[i];
-        if (k.x != ~0ull || k.y != ~0ull) A.pkey[i] = make_ulonglong2(~0ull, ~0ull);
-    }
     unsigned long long nbroken = 0;
-    if (b != 0u || f >= 0) {
-        const int me = A.tag[i];
-        const int4 dp = A.dp[i];
-        const int4 db = A.dbirth[i];
-        const int drx = A.drx[i];
-        const int pv[4] = {dp.x, dp.y, dp.z, dp.w};
-        const int bv[4] = {db.x, db.y, db.z, db.w};
-        int np[4] = {-1, -1, -1, -1}, nb[4] = {0, 0, 0, 0}, nr[4] = {0, 0, 0, 0};
-        int m = 0;
-        for (int s = 0; s < kVmax; ++s) {
-            const int p = pv[s];
-            if (p < 0) continue;
-            if ((b >> s) & 1u) {
-                if (me < p) {
-                    ++nbroken;
-                    long long life = (long long)((uint32_t)step - (uint32_t)bv[s]) / P.period;
-                    if (life >= P.nhist) life = P.nhist - 1;
-                    atomicAdd(&A.life_hist[life], 1ull);
-                }
-                continue;
-            }
-            np[m] = p; nb[m] = bv[s]; nr[m] = (drx >> (8 * s)) & 0xFF;
-            ++m;
-        }
-        if (f >= 0) {
-            const int rp = A.rep[i];
-            const int a = A.rx_order[rp * kMaxRx + slot];
-            const int pt = A.tag[f];
-            int s = m;
-            while (s > 0 && np[s - 1] > pt) {
-                np[s] = np[s - 1]; nb[s] = nb[s - 1]; nr[s] = nr[s - 1];
-                --s;
-            }
-            np[s] = pt; nb[s] = (int)(uint32_t)step; nr[s] = a;
-            ++m;
-        }
-        A.dp[i] = make_int4(np[0], np[1], np[2], np[3]);
-        A.dbirth[i] = make_int4(nb[0], nb[1], nb[2], nb[3]);
-        A.drx[i] = (nr[0] & 0xFF) | ((nr[1] & 0xFF) << 8) | ((nr[2] & 0xFF) << 16) | ((nr[3] & 0xFF) << 24);
-        A.occ[i] = m;
-        const int t = A.type[i];
-        A.avail[i] = m < P.valence[t] ? (uint8_t)t : (uint8_t)0xFF;
-    }
+    apply_particle(P, A, slot, step, gtid(), nbroken);
     const int idx[2] = {cBroken, cBrokenTotal};
     const unsigned long long v[2] = {nbroken, nbroken};
     warp_counts<2>(A.counters, idx, v);
@@ -853,10 +799,13 @@ __global__ void __launch_bounds__(256) k_integrate(DevParams P, DevArrays A)
 }
 
 // Mixed-precision Langevin step: the kick and the velocity in FP32, the
-// position accumulated in FP64 (x += dt v), the cell-relative FP32 coordinate
-// as (float)(x - origin) with the FP64 origin of the frozen cell.  Four FP64
-// operations per axis; positions stay unwrapped between neighbour-list
-// rebuilds (the rebuild wraps them).
+// position accumulated in FP64 (x += dt v, one FP64 fma and one conversion per
+// axis).  The cell-relative FP32 coordinate used by the force loop advances
+// by the same FP32 displacement (one FP32 fma), and every kMixedResync steps
+// (and at every rebuild) it is reset to (float)(x - origin) from the FP64
+// position, so it never drifts by more than kMixedResync roundings of a
+// coordinate below 4 (8 x 2.4e-7 < 2e-6).  Positions stay unwrapped between
+// neighbour-list rebuilds (the rebuild wraps them).
 __global__ void __launch_bounds__(256) k_integrate_mixed(DevParams P, DevArrays A)
 {
     const long long i = gtid();
@@ -882,9 +831,15 @@ __global__ void __launch_bounds__(256) k_integrate_mixed(DevParams P, DevArrays 
     const double x1 = fma(P.dt, (double)v.x, A.x[i]);
     const double y1 = fma(P.dt, (double)v.y, A.y[i]);
     const double z1 = fma(P.dt, (double)v.z, A.z[i]);
-    p.x = (float)(x1 - A.ox[i]);
-    p.y = (float)(y1 - A.oy[i]);
-    p.z = (float)(z1 - A.oz[i]);
+    if ((step & (kMixedResync - 1)) == 0) {          // uniform over the grid
+        p.x = (float)(x1 - A.ox[i]);
+        p.y = (float)(y1 - A.oy[i]);
+        p.z = (float)(z1 - A.oz[i]);
+    } else {
+        p.x = fmaf(dt, v.x, p.x);
+        p.y = fmaf(dt, v.y, p.y);
+        p.z = fmaf(dt, v.z, p.z);
+    }
     // finiteness from the exponent bits (no FP64 compare)
     const unsigned long long bad = 0x7FF0000000000000ull;
     if (((unsigned long long)__double_as_longlong(x1) & bad) == bad ||

@@ -655,6 +655,7 @@ void launch_force(const DevParams &P, const DevArrays &A, bool fp64, bool energy
     }
 }
 
+
 void launch_reduce_cols(const double *src, int ncol, long long n, double *out, Launch L)
 {
     k_reduce_cols<<<1, 1024, 0, L.stream>>>(src, ncol, n, out);

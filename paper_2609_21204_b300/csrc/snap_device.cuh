@@ -140,6 +140,7 @@ constexpr int kMhCand = 16;         // candidates per MH move or logged event
 
 constexpr int kContenders = 4;
 constexpr int kPushSlots = 64;     // push mode: pair distances kept per pushing site
+constexpr int kMixedResync = 8;    // mixed mode: FP32 coordinates re-rounded from FP64 this often (power of 2)
 constexpr int kCopies = 32;        // each counter is spread over this many words
 
 enum Counter {
