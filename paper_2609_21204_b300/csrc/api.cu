@@ -56,6 +56,7 @@ struct snap_ctx {
     std::vector<std::vector<double>> rep_pon, rep_poff;  // [reaction][replica]
     std::vector<RepHost> reps;
     std::vector<int32_t> sp_host, sbt_host;  // tag-indexed static slots
+    int64_t n_static = 0;                     // static bonds added
     int64_t bonds_base = 0;                  // dynamic bonds set explicitly
     // device
     bool ready = false, particles_set = false;
@@ -167,6 +168,7 @@ snap_status upload_reps(snap_ctx *c)
             D.nc[d] = R.nc[d];
             D.w[d] = R.nc[d] > 0 ? R.L[d] / (double)R.nc[d] : R.L[d];
             D.wf[d] = (float)D.w[d];
+            D.cscale[d] = (float)((double)R.nc[d] / R.L[d]);
         }
         D.cell_off = R.cell_off;
         D.tag_off = R.tag_off;
@@ -252,7 +254,8 @@ void fill_params(snap_ctx *c)
     P.mh_moves = c->mh_mode ? P.mh_cells / 8 : 0;
     P.mh_eps = (float)c->mh_eps;
     P.log_events = c->ev_cap > 0 ? 1 : 0;
-    P.pdist_rows = std::max<int64_t>(c->n, 1) / 5 + 1;   // push mode needs a side 4x scarcer: <= n / 5 sites
+    P.pdist_rows = std::max<int64_t>(c->n, 1) / 5 + 1;
+    P.has_static = c->n_static > 0 ? 1 : 0;   // push mode needs a side 4x scarcer: <= n / 5 sites
 }
 
 // everything that depends on the model (cut-offs -> cell grids -> capacities)
@@ -267,7 +270,9 @@ snap_status ensure_ready(snap_ctx *c)
             rx_max = std::max(rx_max, reactive_cut(c, a, b));
         }
     rl_max = std::max(rf_max, rx_max);
-    const double cell_min = rl_max + c->cfg.skin + 2e-4;
+    // the 1e-3 margin covers the FP32 cell assignment (a particle may sit up to
+    // ~1e-4 outside the cell it is filed under)
+    const double cell_min = rl_max + c->cfg.skin + 1e-3;
     int off = 0;
     double dens_max = 0.0;
     for (auto &R : c->reps) {
@@ -831,7 +836,6 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
               alloc_arr(c, A.fpart, n) && alloc_arr(c, A.brk, n) && alloc_arr(c, A.rx_order, (size_t)nrep * kMaxRx) &&
               alloc_arr(c, A.step, 1) && alloc_arr(c, A.status, 1) && alloc_arr(c, A.need_rebuild, 1) &&
               alloc_arr(c, A.nbr_need, 2) && alloc_arr(c, A.counters, (size_t)cNumCounters * kCopies) &&
-              alloc_arr(c, A.ox, n) && alloc_arr(c, A.oy, n) && alloc_arr(c, A.oz, n) &&
               alloc_arr(c, A.site_list, n) && alloc_arr(c, A.list_count, 1) &&
               alloc_arr(c, A.cont, n * kContenders) && alloc_arr(c, A.ncont, n) &&
               alloc_arr(c, A.life_hist, (size_t)c->cfg.lifetime_bins) && alloc_arr(c, A.e_part, 4 * n) &&
@@ -946,6 +950,9 @@ extern "C" snap_status snap_add_static_bonds(snap_ctx *c, int64_t nb, const int3
     }
     c->sp_host.swap(sp);
     c->sbt_host.swap(sbt);
+    c->n_static += nb;
+    c->P.has_static = c->n_static > 0 ? 1 : 0;
+    c->graph_dirty = true;
     if (c->particles_set) return upload_static(c);
     return SNAP_OK;
 }

@@ -832,9 +832,11 @@ __global__ void __launch_bounds__(256) k_integrate_mixed(DevParams P, DevArrays 
     const double y1 = fma(P.dt, (double)v.y, A.y[i]);
     const double z1 = fma(P.dt, (double)v.z, A.z[i]);
     if ((step & (kMixedResync - 1)) == 0) {          // uniform over the grid
-        p.x = (float)(x1 - A.ox[i]);
-        p.y = (float)(y1 - A.oy[i]);
-        p.z = (float)(z1 - A.oz[i]);
+        // origin of the frozen cell, as the rebuild computed it
+        const uint32_t b = w_bits(p);
+        p.x = (float)(x1 - (double)bits_cx(b) * Rp.w[0]);
+        p.y = (float)(y1 - (double)bits_cy(b) * Rp.w[1]);
+        p.z = (float)(z1 - (double)bits_cz(b) * Rp.w[2]);
     } else {
         p.x = fmaf(dt, v.x, p.x);
         p.y = fmaf(dt, v.y, p.y);

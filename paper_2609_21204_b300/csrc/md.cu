@@ -24,12 +24,16 @@ namespace {
 
 __device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 
+// Cell of a wrapped position, in FP32 (one conversion per axis on the FP64
+// pipe instead of five FP64 operations): the cell may be off by one within
+// ~1e-4 of a cell face, which the cell size margin absorbs.  The rebuild uses
+// this one function for the sort key and for the frozen cell bits.
 __device__ __forceinline__ void cell_of(const RepDev &R, double x, double y, double z, int &cx, int &cy,
                                         int &cz)
 {
-    cx = (int)(x * R.invL[0] * (double)R.nc[0]);
-    cy = (int)(y * R.invL[1] * (double)R.nc[1]);
-    cz = (int)(z * R.invL[2] * (double)R.nc[2]);
+    cx = (int)((float)x * R.cscale[0]);
+    cy = (int)((float)y * R.cscale[1]);
+    cz = (int)((float)z * R.cscale[2]);
     cx = min(max(cx, 0), R.nc[0] - 1);
     cy = min(max(cy, 0), R.nc[1] - 1);
     cz = min(max(cz, 0), R.nc[2] - 1);
@@ -60,7 +64,10 @@ __global__ void k_cell_key(DevParams P, DevArrays A)
     if (!status_ok(A.status) || !*A.need_rebuild) return;
     const RepDev &R = A.reps[A.rep[i]];
     double x = A.x[i], y = A.y[i], z = A.z[i];
-    if (!(x >= 0.0 && x < R.L[0] && y >= 0.0 && y < R.L[1] && z >= 0.0 && z < R.L[2])) {
+    // inside [0, L) on every axis? (non-negative doubles order like their bits)
+    const long long bx = __double_as_longlong(x), by = __double_as_longlong(y), bz = __double_as_longlong(z);
+    if (!(bx >= 0 && bx < __double_as_longlong(R.L[0]) && by >= 0 && by < __double_as_longlong(R.L[1]) &&
+          bz >= 0 && bz < __double_as_longlong(R.L[2]))) {
         int ix = A.ix[i], iy = A.iy[i], iz = A.iz[i];
         x = wrap_img(x, R.L[0], ix);
         y = wrap_img(y, R.L[1], iy);
@@ -73,7 +80,10 @@ __global__ void k_cell_key(DevParams P, DevArrays A)
     const int lin = (cz * R.nc[1] + cy) * R.nc[0] + cx;
     const int c = A.type[i] * P.ncell + A.rank_of[R.cell_off + lin];
     A.cell_key[i] = c;
-    atomicAdd(&A.cell_count[c], 1);
+    // particles are still nearly sorted: lanes of a warp mostly share a key,
+    // so one atomic per distinct key and warp
+    const unsigned peers = __match_any_sync(__activemask(), c);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&A.cell_count[c], __popc(peers));
     if (i == 0) {
         counter_reset(A.counters, cNlistEntries);
         counter_reset(A.counters, cRnlistEntries);
@@ -176,7 +186,13 @@ __global__ void k_scatter(DevParams P, DevArrays A)
     if (i >= P.n) return;
     if (!status_ok(A.status) || !*A.need_rebuild) return;
     const int c = A.cell_key[i];
-    const int pos = A.cell_start[c] + atomicAdd(&A.cell_cursor[c], 1);
+    // one atomic per distinct key and warp; lanes take consecutive slots
+    const unsigned peers = __match_any_sync(__activemask(), c);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&A.cell_cursor[c], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const int pos = A.cell_start[c] + base + __popc(peers & ((1u << lane) - 1u));
     A.order[pos] = (int32_t)i;
 }
 
@@ -222,8 +238,11 @@ __global__ void k_gather(DevParams P, DevArrays A, DevArrays B)
     const int tag = A.tag[i];
     B.tag[k] = tag;
     const int rp = A.rep[i];
-    B.rep[k] = rp;
-    B.sp[k] = A.sp[i]; B.sbt[k] = A.sbt[i];
+    if (P.nrep > 1) B.rep[k] = rp;                  // one system: rep is all zeros and stays so
+    if (P.has_static) {
+        B.sp[k] = A.sp[i];
+        B.sbt[k] = A.sbt[i];
+    }
     B.dp[k] = A.dp[i]; B.drx[k] = A.drx[i]; B.dbirth[k] = A.dbirth[i];
     B.occ[k] = A.occ[i];
     A.rtag[tag] = (int32_t)k;
@@ -231,7 +250,6 @@ __global__ void k_gather(DevParams P, DevArrays A, DevArrays B)
     int cx, cy, cz;
     cell_of(Rp, x, y, z, cx, cy, cz);
     const double o0 = (double)cx * Rp.w[0], o1 = (double)cy * Rp.w[1], o2 = (double)cz * Rp.w[2];
-    A.ox[k] = o0; A.oy[k] = o1; A.oz[k] = o2;
     const double rx = x - o0;
     const double ry = y - o1;
     const double rz = z - o2;
@@ -256,8 +274,12 @@ __global__ void k_copyback(DevParams P, DevArrays A, DevArrays B)
         A.v4[k] = B.v4[k];
     }
     A.ix[k] = B.ix[k]; A.iy[k] = B.iy[k]; A.iz[k] = B.iz[k];
-    A.type[k] = B.type[k]; A.tag[k] = B.tag[k]; A.rep[k] = B.rep[k];
-    A.sp[k] = B.sp[k]; A.sbt[k] = B.sbt[k];
+    A.type[k] = B.type[k]; A.tag[k] = B.tag[k];
+    if (P.nrep > 1) A.rep[k] = B.rep[k];
+    if (P.has_static) {
+        A.sp[k] = B.sp[k];
+        A.sbt[k] = B.sbt[k];
+    }
     A.dp[k] = B.dp[k]; A.drx[k] = B.drx[k]; A.dbirth[k] = B.dbirth[k];
     A.occ[k] = B.occ[k];
     reinterpret_cast<V *>(A.pos4)[k] = reinterpret_cast<const V *>(B.pos4)[k];
@@ -473,26 +495,28 @@ __global__ void __launch_bounds__(256) k_force(DevParams P, DevArrays A)
         }
     }
     // static bonds
-    const int4 sp = A.sp[i];
-    const int sbt = A.sbt[i];
-    const int spv[4] = {sp.x, sp.y, sp.z, sp.w};
     bool bad = false;
+    if (P.has_static) {
+        const int4 sp = A.sp[i];
+        const int sbt = A.sbt[i];
+        const int spv[4] = {sp.x, sp.y, sp.z, sp.w};
 #pragma unroll
-    for (int s = 0; s < kSmax; ++s) {
-        const int ptag = spv[s];
-        if (ptag < 0) continue;
-        const int j = A.rtag[ptag];
-        const V pj = pos[j];
-        R dx, dy, dz;
-        separation<R>(pi, pj, Rp, dx, dy, dz);
-        const R r2 = dx * dx + dy * dy + dz * dz;
-        R fb;
-        double u;
-        if (!bond_factor<R>(P, (sbt >> (8 * s)) & 0xFF, r2, fb, u)) bad = true;
-        fx += fb * dx;
-        fy += fb * dy;
-        fz += fb * dz;
-        if (E) { eb += 0.5 * u; vir -= 0.5 * (double)fb * (double)r2; }
+        for (int s = 0; s < kSmax; ++s) {
+            const int ptag = spv[s];
+            if (ptag < 0) continue;
+            const int j = A.rtag[ptag];
+            const V pj = pos[j];
+            R dx, dy, dz;
+            separation<R>(pi, pj, Rp, dx, dy, dz);
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            R fb;
+            double u;
+            if (!bond_factor<R>(P, (sbt >> (8 * s)) & 0xFF, r2, fb, u)) bad = true;
+            fx += fb * dx;
+            fy += fb * dy;
+            fz += fb * dz;
+            if (E) { eb += 0.5 * u; vir -= 0.5 * (double)fb * (double)r2; }
+        }
     }
     // dynamic bonds
     const int4 dp = A.dp[i];

@@ -62,11 +62,13 @@ struct DevParams {
     float mh_eps;           // weight of the uniform component of the learned proposal
     int32_t log_events;     // record bond-formation events in the plain sweep
     int64_t pdist_rows;     // pushing sites whose pair distances fit the pdist scratch
+    int32_t has_static;     // any static bonds (else their slots are neither gathered nor read)
 };
 
 struct RepDev {
     double L[3], invL[3], halfL[3], w[3];
     float wf[3];
+    float cscale[3];        // cells per unit length (nc / L) in FP32, for cell assignment
     int32_t nc[3];
     int32_t cell_off;       // first global cell id of this replica
     int32_t pad0;
@@ -83,7 +85,6 @@ struct RepDev {
 struct DevArrays {
     double *x, *y, *z, *vx, *vy, *vz;   // vx..vz: FP64 mode velocities
     float4 *v4;                     // mixed mode velocities (w unused)
-    double *ox, *oy, *oz;           // origin of the frozen cell of each particle (set at rebuild)
     int32_t *ix, *iy, *iz;          // image counters
     int32_t *type, *tag, *rtag, *rep;
     void *pos4;                     // float4 or double4_32a: coords relative to frozen cell origin, w = bits
