@@ -449,7 +449,7 @@ __device__ __forceinline__ bool bond_factor(const DevParams &P, int bt, R r2, R 
 }
 
 template <typename R, bool E>
-__global__ void __launch_bounds__(256) k_force(DevParams P, DevArrays A)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_force(DevParams P, DevArrays A)
 {
     using V = typename Vec4<R>::T;
     const long long i = gtid();
@@ -464,33 +464,40 @@ __global__ void __launch_bounds__(256) k_force(DevParams P, DevArrays A)
     const int nn = A.nn[i];
     const long long stride = P.nbr_stride;
     const int *nb = A.nbr + i;
-    // the next neighbour's index and position are loaded while the current
-    // pair is evaluated; the sum runs in list order
-    int jn = nn > 0 ? __ldg(nb) : 0;
-    V pn = pos[jn];
-    for (int k = 0; k < nn; ++k) {
-        const V pj = pn;
-        if (k + 1 < nn) {
-            jn = __ldg(nb + (long long)(k + 1) * stride);
-            pn = pos[jn];
-        }
-        const int tj = bits_type(w_bits(pj));
-        R dx, dy, dz;
-        separation<R>(pi, pj, Rp, dx, dy, dz);
-        const R r2 = dx * dx + dy * dy + dz * dz;
-        const int tt = ti * kMaxTypes + tj;
-        if (r2 < Num<R>::rc2(P, tt)) {
-            const R ir2 = Num<R>::rcp(r2);
-            const R s2 = Num<R>::sig2(P, tt) * ir2;
-            const R s6 = s2 * s2 * s2;
-            const R fr = Num<R>::eps24(P, tt) * (s6 * ((R)2 * s6 - (R)1)) * ir2;
-            fx -= fr * dx;
-            fy -= fr * dy;
-            fz -= fr * dz;
-            if (E) {
-                const double s6d = (double)s6;
-                ep += 0.5 * ((double)P.eps24d[tt] / 6.0 * (s6d * s6d - s6d) - P.shiftd[tt]);
-                vir += 0.5 * (double)fr * (double)r2;
+    // bond partners first: their slot words are independent of the pair loop
+    const int4 dp = A.dp[i];
+    const int drx = A.drx[i];
+    // pairs in batches of four: four independent index loads, then four
+    // independent position loads, then the arithmetic in list order
+    for (int k0 = 0; k0 < nn; k0 += 4) {
+        int jj[4];
+        V pp[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) jj[u] = k0 + u < nn ? __ldg(nb + (long long)(k0 + u) * stride) : (int)i;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pp[u] = pos[jj[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (k0 + u >= nn) break;
+            const V pj = pp[u];
+            const int tj = bits_type(w_bits(pj));
+            R dx, dy, dz;
+            separation<R>(pi, pj, Rp, dx, dy, dz);
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            const int tt = ti * kMaxTypes + tj;
+            if (r2 < Num<R>::rc2(P, tt)) {
+                const R ir2 = Num<R>::rcp(r2);
+                const R s2 = Num<R>::sig2(P, tt) * ir2;
+                const R s6 = s2 * s2 * s2;
+                const R fr = Num<R>::eps24(P, tt) * (s6 * ((R)2 * s6 - (R)1)) * ir2;
+                fx -= fr * dx;
+                fy -= fr * dy;
+                fz -= fr * dz;
+                if (E) {
+                    const double s6d = (double)s6;
+                    ep += 0.5 * ((double)P.eps24d[tt] / 6.0 * (s6d * s6d - s6d) - P.shiftd[tt]);
+                    vir += 0.5 * (double)fr * (double)r2;
+                }
             }
         }
     }
@@ -519,8 +526,6 @@ __global__ void __launch_bounds__(256) k_force(DevParams P, DevArrays A)
         }
     }
     // dynamic bonds
-    const int4 dp = A.dp[i];
-    const int drx = A.drx[i];
     const int dpv[4] = {dp.x, dp.y, dp.z, dp.w};
 #pragma unroll
     for (int s = 0; s < kVmax; ++s) {
