@@ -51,7 +51,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0,
+                    help="threads per block of the particle kernels (0 with --skin 0: autotuned)")
+    ap.add_argument("--skin", type=float, default=0.0,
+                    help="neighbour-list skin (0 with --block 0: autotuned)")
     ap.add_argument("--batch-replicas", type=int, default=256,
                     help="replicas of the batched telechelic sweep leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=500)
@@ -378,7 +381,18 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
     s = build_system(args, 20260921 + rank)
     n = s.n
     K, W = args.steps, args.warmup
-    sim = snap.from_system(s, precision="mixed", block_size=args.block)
+    if args.block or args.skin:
+        tune = {"block_size": args.block or 128, "skin": args.skin or s.skin, "cached": None,
+                "key": "set by flags"}
+    else:
+        from paper_2609_21204_b300 import autotune
+        tune = autotune.autotune(s, precision="mixed", blocks=(128, 256), skins=(0.3, 0.4, 0.5), steps=150,
+                                 warmup=50)
+
+    def make(precision):
+        return snap.from_system(s, precision=precision, block_size=tune["block_size"], skin=tune["skin"])
+
+    sim = make("mixed")
 
     sim.step(W)
     st0 = sim.stats()
@@ -402,12 +416,15 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
 
     # per-phase times over an instrumented window right after the timed region
     ph = sim.step_profiled(args.profile_steps)
+    reb = [sim.rebuild_profiled() for _ in range(3)]
+    rebuild_ms = {k: round(float(np.mean([r[k] for r in reb])), 5) for k in reb[0]}
     st2 = sim.stats()
     nbar = st2["nlist_entries"] / n
     force_ms = ph["force"]
     # algorithmic bytes of the force kernel per particle: own pos4 16, replica id 4,
-    # count 4, 4 per neighbour index, static + dynamic slots 2 x (16 + 4), force 16
-    bytes_pp = 16 + 4 + 4 + 4 * nbar + 40 + 16
+    # count 4, 4 per neighbour index, dynamic slots 16 + 4 (static slots 16 + 4
+    # when there are static bonds), force 16
+    bytes_pp = 16 + 4 + 4 + 4 * nbar + 20 + (20 if len(s.static_bonds) else 0) + 16
     alg_bytes = bytes_pp * n
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (force_ms / 1e3) / 1e9
@@ -426,10 +443,12 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": t_max * 1e3 / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": workload_config(args, n),
+        "config": dict(workload_config(args, n), block_size=tune["block_size"], skin=tune["skin"]),
+        "autotune": {k: tune.get(k) for k in ("block_size", "skin", "cached", "key", "ms_per_step")},
         "gpu_launches": launches,
         "clocks": clk,
         "phases_ms_per_step": {k: round(v, 5) for k, v in ph.items()},
+        "rebuild_ms_per_kernel": rebuild_ms,
         "bond_update_pairs_per_s": bond_pairs_per_s,
         "sweep": {"scanned_nlist_entries": st2["scanned"], "break_tested": st2["break_tested"],
                   "proposals": st2["proposals"], "formed": st2["formed"], "broken": st2["broken"],
@@ -443,7 +462,7 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
     }
     if not args.no_fp64:
         sim.close()
-        sim64 = snap.from_system(s, precision="fp64", block_size=args.block)
+        sim64 = make("fp64")
         sim64.step(W)
         barrier()
         torch.cuda.synchronize()
@@ -459,17 +478,17 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
                              "phases_ms_per_step": {k: round(v, 5) for k, v in ph64.items()}}
         out["speedup_mixed_vs_fp64_plain"] = value / v64
         sim64.close()
-        sim = snap.from_system(s, precision="mixed", block_size=args.block)
+        sim = make("mixed")
         sim.step(W)
     if batch is not None:
         sim.close()
         out["batched"] = _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream)
-        sim = snap.from_system(s, precision="mixed", block_size=args.block)
+        sim = make("mixed")
         sim.step(W)
     if args.learned_events > 0:
         sim.close()
         out["learned"] = _run_learned(args, torch, snap, rank, stream)
-        sim = snap.from_system(s, precision="mixed", block_size=args.block)
+        sim = make("mixed")
         sim.step(W)
     if not args.no_e2e:
         # end to end through the C ABI with host buffers: upload the state, one
