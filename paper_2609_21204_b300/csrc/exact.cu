@@ -562,9 +562,49 @@ __device__ __forceinline__ void push_pass2(const DevParams &P, DevArrays &A, int
     warp_counts<2>(A.counters, idx, v);
 }
 
+// Breaking (Fig. 1d) of particle i's bonds of the reaction in slot `slot`:
+// each bond present when the reaction began, owned by its smaller tag,
+// breaks iff Philox(BREAK; tags) gives u53 < P_off.  Reads the slots as they
+// were before the reaction; writes only the break bits, which k_apply reads.
+__device__ __forceinline__ void break_particle(const DevParams &P, DevArrays &A, int slot, long long step, long long i,
+                                               unsigned long long &tested)
+{
+    const int4 dp = A.dp[i];
+    if (dp.x < 0) return;
+    const int rp = A.rep[i];
+    const int a = A.rx_order[rp * kMaxRx + slot];
+    const RepDev &R = A.reps[rp];
+    const int me = A.tag[i];
+    const int drx = A.drx[i];
+    const int pv[4] = {dp.x, dp.y, dp.z, dp.w};
+#pragma unroll
+    for (int s = 0; s < kVmax; ++s) {
+        const int p = pv[s];
+        if (p < 0 || p < me) continue;           // the smaller tag owns the bond
+        if (((drx >> (8 * s)) & 0xFF) != a) continue;
+        ++tested;
+        const U4 w = pair_draw(R, a, kBreak, step, (uint32_t)(me - R.tag_off), (uint32_t)(p - R.tag_off));
+        // u53 < p_off  <=>  m < ceil(p_off 2^53) with m the 53-bit integer of u53
+        const unsigned long long m = ((unsigned long long)w.x << 21) | (unsigned long long)(w.y >> 11);
+        if (m < R.off_thresh[a]) {
+            atomicOr(&A.brk[i], 1u << s);
+            const int j = A.rtag[p];
+            const int4 q = A.dp[j];
+            const int qv[4] = {q.x, q.y, q.z, q.w};
+            int sj = 0;
+#pragma unroll
+            for (int t = 0; t < kVmax; ++t)
+                if (qv[t] == me) sj = t;
+            atomicOr(&A.brk[j], 1u << sj);
+        }
+    }
+}
+
 // The two proposal kernels of a reaction: each runs the scan (pull) or the
 // push version of its phase, as push_type decides for this reaction, so the
-// mode that is not used costs no launch.
+// mode that is not used costs no launch.  The first also draws the breaking
+// of the reaction's existing bonds (independent of the proposals), which
+// fills the issue slots that the latency-bound proposal work leaves idle.
 template <bool FORCED, bool SCREEN>
 __global__ void __launch_bounds__(256, 4) k_proposals(DevParams P, DevArrays A, int slot)
 {
@@ -573,6 +613,11 @@ __global__ void __launch_bounds__(256, 4) k_proposals(DevParams P, DevArrays A, 
     const int s = push_type(P, A, slot);
     if (s >= 0) push_pass1(P, A, slot, step, s);
     else pull_propose<SCREEN>(P, A, slot);
+    unsigned long long tested = 0;
+    for (long long i = gtid(); i < P.n; i += (long long)gridDim.x * blockDim.x) break_particle(P, A, slot, step, i, tested);
+    const int idx[1] = {cBreakTested};
+    const unsigned long long v[1] = {tested};
+    warp_counts<1>(A.counters, idx, v);
 }
 
 template <bool FORCED>
@@ -585,23 +630,22 @@ __global__ void __launch_bounds__(256) k_resolve(DevParams P, DevArrays A, int s
     else pull_exact(P, A, slot, step);
 }
 
-// Acceptance of the listed sites' edges (thread q < list length) and the
-// breaking draws of the bonds of particle i (thread i < n) in one launch: both
-// read the state as it was before this reaction and write disjoint outputs
-// (fpart; the brk bits).
+// Acceptance (Eq. 3) of the surviving edges: in scan mode one thread per
+// listed site, in push mode one per pushing site.
 template <bool FORCED>
-__global__ void k_accept_break(DevParams P, DevArrays A, int slot)
+__global__ void k_accept(DevParams P, DevArrays A, int slot)
 {
     long long step;
     if (!sweep_active<FORCED>(P, A, step)) return;
-    const long long g = gtid();
-    unsigned long long edge = 0, surv = 0, formed = 0, tested = 0;
+    unsigned long long edge = 0, surv = 0, formed = 0;
     const int ps = push_type(P, A, slot);
+    const long long stride = (long long)gridDim.x * blockDim.x;
     if (ps >= 0) {
         // push mode: every edge has a pushing end; the edge that can survive at
         // pushing site c is the one its best[] names (its low word is the
         // other end's tag)
-        if (g < A.avail_count[ps]) {
+        const int ns = A.avail_count[ps];
+        for (long long g = gtid(); g < ns; g += stride) {
             const int c = A.avail_list[(long long)ps * P.n + g];
             const unsigned long long bc = A.best[c];
             if (bc != 0ull) {
@@ -632,7 +676,7 @@ __global__ void k_accept_break(DevParams P, DevArrays A, int slot)
         }
     }
     const int nlist = ps >= 0 ? 0 : *A.list_count;
-    if (g < nlist) {
+    for (long long g = gtid(); g < nlist; g += stride) {
         const int i = A.site_list[g];
         const int j = A.prop[i];
         if (j >= 0) {
@@ -669,41 +713,9 @@ __global__ void k_accept_break(DevParams P, DevArrays A, int slot)
             }
         }
     }
-    const int4 dp = g < P.n ? A.dp[g] : make_int4(-1, -1, -1, -1);
-    if (dp.x >= 0) {
-        const long long i = g;
-        const int rp = A.rep[i];
-        const int a = A.rx_order[rp * kMaxRx + slot];
-        const RepDev &R = A.reps[rp];
-        const int me = A.tag[i];
-        const int drx = A.drx[i];
-        const int pv[4] = {dp.x, dp.y, dp.z, dp.w};
-#pragma unroll
-        for (int s = 0; s < kVmax; ++s) {
-            const int p = pv[s];
-            if (p < 0 || p < me) continue;           // the smaller tag owns the bond
-            if (((drx >> (8 * s)) & 0xFF) != a) continue;
-            ++tested;
-            const U4 w = pair_draw(R, a, kBreak, step, (uint32_t)(me - R.tag_off),
-                                   (uint32_t)(p - R.tag_off));
-            // u53 < p_off  <=>  m < ceil(p_off 2^53) with m the 53-bit integer of u53
-            const unsigned long long m = ((unsigned long long)w.x << 21) | (unsigned long long)(w.y >> 11);
-            if (m < R.off_thresh[a]) {
-                atomicOr(&A.brk[i], 1u << s);
-                const int j = A.rtag[p];
-                const int4 q = A.dp[j];
-                const int qv[4] = {q.x, q.y, q.z, q.w};
-                int sj = 0;
-#pragma unroll
-                for (int t = 0; t < kVmax; ++t)
-                    if (qv[t] == me) sj = t;
-                atomicOr(&A.brk[j], 1u << sj);
-            }
-        }
-    }
-    const int idx[5] = {cEdges, cSurvivors, cFormed, cFormedTotal, cBreakTested};
-    const unsigned long long v[5] = {edge, surv, formed, formed, tested};
-    warp_counts<5>(A.counters, idx, v);
+    const int idx[4] = {cEdges, cSurvivors, cFormed, cFormedTotal};
+    const unsigned long long v[4] = {edge, surv, formed, formed};
+    warp_counts<4>(A.counters, idx, v);
 }
 
 template <bool FORCED>
@@ -888,7 +900,7 @@ void sweep_reaction(const DevParams &P, const DevArrays &A, int slot, Launch L)
     else k_proposals<FORCED, false><<<gprop, L.block, 0, L.stream>>>(P, A, slot);
     k_resolve<FORCED><<<std::max<unsigned>(gl, (unsigned)std::min<long long>(grid_for(P.n, 256), 4LL * sm_count())),
                         256, 0, L.stream>>>(P, A, slot);
-    k_accept_break<FORCED><<<g, L.block, 0, L.stream>>>(P, A, slot);
+    k_accept<FORCED><<<gl, 256, 0, L.stream>>>(P, A, slot);
     if (P.log_events) launch_log_events(P, A, slot, FORCED, L);
     k_apply<FORCED><<<g, L.block, 0, L.stream>>>(P, A, slot);
 }
