@@ -54,7 +54,7 @@ __device__ __forceinline__ int4 apply_particle(const DevParams &P, DevArrays &A,
         ++m;
     }
     if (f >= 0) {
-        const int rp = A.rep[i];
+        const int rp = rep_of(P, A, i);
         const int a = A.rx_order[rp * kMaxRx + slot];
         const int pt = A.tag[f];
         int s = m;

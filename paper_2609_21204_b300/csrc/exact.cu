@@ -242,7 +242,7 @@ __device__ __forceinline__ void pull_propose(const DevParams &P, DevArrays &A, i
     if (i < P.n) {
         int best = -1, ncont = 0;
         double best_d = 0.0;
-        const int rp = A.rep[i];
+        const int rp = rep_of(P, A, i);
         const int a = A.rx_order[rp * kMaxRx + slot];
         const int ti = A.type[i];
         const int ta = P.rx_ta[a], tb = P.rx_tb[a];
@@ -340,7 +340,7 @@ __device__ __forceinline__ void pull_exact(const DevParams &P, DevArrays &A, int
     for (long long q = gtid(); q < nlist; q += (long long)gridDim.x * blockDim.x) {
         const int i = A.site_list[q];
         const int nc = A.ncont[i];
-        const int rp = A.rep[i];
+        const int rp = rep_of(P, A, i);
         const int a = A.rx_order[rp * kMaxRx + slot];
         const RepDev &R = A.reps[rp];
         if (nc == 0) {
@@ -571,7 +571,7 @@ __device__ __forceinline__ void break_particle(const DevParams &P, DevArrays &A,
 {
     const int4 dp = A.dp[i];
     if (dp.x < 0) return;
-    const int rp = A.rep[i];
+    const int rp = rep_of(P, A, i);
     const int a = A.rx_order[rp * kMaxRx + slot];
     const RepDev &R = A.reps[rp];
     const int me = A.tag[i];
@@ -680,7 +680,7 @@ __global__ void k_accept(DevParams P, DevArrays A, int slot)
         const int i = A.site_list[g];
         const int j = A.prop[i];
         if (j >= 0) {
-            const int rp = A.rep[i];
+            const int rp = rep_of(P, A, i);
             const int a = A.rx_order[rp * kMaxRx + slot];
             const RepDev &R = A.reps[rp];
             const uint32_t ti = (uint32_t)(A.tag[i] - R.tag_off), tj = (uint32_t)(A.tag[j] - R.tag_off);
@@ -756,7 +756,7 @@ __global__ void __launch_bounds__(256) k_integrate(DevParams P, DevArrays A)
     if (i >= P.n) return;
     if (!status_ok(A.status)) return;
     const long long step = *A.step;
-    const int rp = A.rep[i];
+    const int rp = rep_of(P, A, i);
     const RepDev &Rp = A.reps[rp];
     const uint32_t tl = (uint32_t)(A.tag[i] - Rp.tag_off);
     const U4 w = philox10(U4{(uint32_t)((unsigned long long)step & 0xFFFFFFFFull),
@@ -824,7 +824,7 @@ __global__ void __launch_bounds__(256) k_integrate_mixed(DevParams P, DevArrays 
     if (i >= P.n) return;
     if (!status_ok(A.status)) return;
     const long long step = *A.step;
-    const RepDev &Rp = A.reps[A.rep[i]];
+    const RepDev &Rp = A.reps[rep_of(P, A, i)];
     const uint32_t tl = (uint32_t)(A.tag[i] - Rp.tag_off);
     const U4 w = philox10(U4{(uint32_t)((unsigned long long)step & 0xFFFFFFFFull),
                              (uint32_t)((unsigned long long)step >> 32), tl, 0u},

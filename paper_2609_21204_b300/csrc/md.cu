@@ -62,7 +62,7 @@ __global__ void k_cell_key(DevParams P, DevArrays A)
     if (i == 0) counter_add1(A.counters, cRebuildLaunches, 1ull);   // launches, taken or not
     if (i >= P.n) return;
     if (!status_ok(A.status) || !*A.need_rebuild) return;
-    const RepDev &R = A.reps[A.rep[i]];
+    const RepDev &R = A.reps[rep_of(P, A, i)];
     double x = A.x[i], y = A.y[i], z = A.z[i];
     // inside [0, L) on every axis? (non-negative doubles order like their bits)
     const long long bx = __double_as_longlong(x), by = __double_as_longlong(y), bz = __double_as_longlong(z);
@@ -237,7 +237,7 @@ __global__ void k_gather(DevParams P, DevArrays A, DevArrays B)
     B.type[k] = t;
     const int tag = A.tag[i];
     B.tag[k] = tag;
-    const int rp = A.rep[i];
+    const int rp = rep_of(P, A, i);
     if (P.nrep > 1) B.rep[k] = rp;                  // one system: rep is all zeros and stays so
     if (P.has_static) {
         B.sp[k] = A.sp[i];
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A)
         const V p = pos[i];
         const uint32_t b = w_bits(p);
         const int ti = bits_type(b), cx = bits_cx(b), cy = bits_cy(b), cz = bits_cz(b);
-        const RepDev &Rp = A.reps[A.rep[i]];
+        const RepDev &Rp = A.reps[rep_of(P, A, i)];
         const int nx = Rp.nc[0], ny = Rp.nc[1], nz = Rp.nc[2];
         const float wx = Rp.wf[0], wy = Rp.wf[1], wz = Rp.wf[2];
         const float pxf = (float)p.x, pyf = (float)p.y, pzf = (float)p.z;
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_force(DevParams
     const V *pos = reinterpret_cast<const V *>(A.pos4);
     const V pi = pos[i];
     const int ti = bits_type(w_bits(pi));
-    const RepDev &Rp = A.reps[A.rep[i]];
+    const RepDev &Rp = A.reps[rep_of(P, A, i)];
     R fx = 0, fy = 0, fz = 0;
     double ep = 0.0, eb = 0.0, vir = 0.0;
     const int nn = A.nn[i];

@@ -467,7 +467,7 @@ __global__ void k_log_events(DevParams P, DevArrays A, int slot)
     for (long long i = gtid(); i < P.n; i += (long long)gridDim.x * blockDim.x) {
         const int j = A.prop[(int)i];
         if (j < 0 || A.fpart[i] != j) continue;
-        const int rp = A.rep[i];
+        const int rp = rep_of(P, A, i);
         const int a = A.rx_order[rp * kMaxRx + slot];
         const RepDev &R = A.reps[rp];
         int ci[kMhCand];

@@ -276,6 +276,12 @@ __device__ __forceinline__ void set_w_bits(double4_32a &p, uint32_t b)
 
 __device__ __forceinline__ bool status_ok(const uint32_t *st) { return *(volatile const uint32_t *)st == 0u; }
 
+// replica of particle i (no load for a single system)
+__device__ __forceinline__ int rep_of(const DevParams &P, const DevArrays &A, long long i)
+{
+    return P.nrep > 1 ? A.rep[i] : 0;
+}
+
 // warp-aggregated 64-bit counter increment (one atomic per full warp)
 __device__ __forceinline__ void warp_count(unsigned long long *ctr, unsigned long long v)
 {
