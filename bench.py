@@ -491,10 +491,13 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
         sim = make("mixed")
         sim.step(W)
     if not args.no_e2e:
-        # end to end through the C ABI with host buffers: upload the state, one
-        # step, read positions back — every step
-        pos = np.ascontiguousarray(sim.positions())
-        vel = np.ascontiguousarray(sim.velocities())
+        # end to end through the C ABI with host buffers in pinned memory: every
+        # step uploads positions + velocities, runs one step and reads the
+        # positions back
+        pin = lambda: torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+        pos, vel = pin(), pin()
+        sim.positions(out=pos)
+        sim.velocities(out=vel)
         E = args.e2e_steps
         barrier()
         torch.cuda.synchronize()
@@ -502,13 +505,14 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
         for _ in range(E):
             sim.set_positions(pos, vel)
             sim.step(1)
-            pos = sim.positions()
+            sim.positions(out=pos)
         torch.cuda.synchronize()
         te = max_all(time.perf_counter() - t0)
         out["e2e"] = {"value": n_all * E / te, "unit": UNIT, "h2d_bytes_per_step": 48 * n,
                       "d2h_bytes_per_step": 24 * n, "steps": E,
-                      "what": "per step: snap_set_positions (positions+velocities from host), "
-                              "snap_step(1), snap_get_positions (to host)"}
+                      "what": "per step from pinned host buffers: snap_set_positions (positions + "
+                              "velocities), snap_step(1) (the new positions force a list rebuild), "
+                              "snap_get_positions (to host)"}
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         o = oracle.OracleSystem(s)

@@ -243,13 +243,22 @@ class Snap:
         m = n_out.value
         return np.stack([pairs[0:2 * m:2], pairs[1:2 * m:2], rx[:m]], axis=1).astype(np.int64)
 
-    def positions(self):
-        p = np.zeros((self.n, 3))
+    @staticmethod
+    def _out3(n, out):
+        if out is None:
+            return np.empty((n, 3))
+        if out.dtype != np.float64 or out.shape != (n, 3) or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float64 array of shape (n, 3)")
+        return out
+
+    def positions(self, out=None):
+        """Wrapped positions in tag order; `out` (e.g. a pinned array) is filled in place."""
+        p = self._out3(self.n, out)
         self._check(self._lib.snap_get_positions(self._ctx, p.ctypes.data))
         return p
 
-    def velocities(self):
-        v = np.zeros((self.n, 3))
+    def velocities(self, out=None):
+        v = self._out3(self.n, out)
         self._check(self._lib.snap_get_velocities(self._ctx, v.ctypes.data))
         return v
 

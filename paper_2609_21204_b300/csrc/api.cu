@@ -67,6 +67,9 @@ struct snap_ctx {
     RepDev *d_reps = nullptr;
     int32_t *d_bsum = nullptr;
     double *d_red = nullptr;
+    double *io3 = nullptr;           // tag-ordered (x, y, z) staging for host I/O
+    int32_t *io_img = nullptr;
+    uint32_t *io_flag = nullptr;
     std::vector<void *> allocs;
     // Metropolis–Hastings mode and event log
     int mh_mode = 0;                 // 0: DyBond sweep, 1: MH uniform, 2: MH learned
@@ -1030,21 +1033,40 @@ extern "C" snap_status snap_set_particles(snap_ctx *c, const double *pos3, const
     return set_need_rebuild(c);
 }
 
+// device staging for the host I/O calls (allocated on first use)
+snap_status ensure_io(snap_ctx *c)
+{
+    if (c->io3) return SNAP_OK;
+    const size_t n = (size_t)std::max<int64_t>(c->n, 1);
+    if (!alloc_arr(c, c->io3, 3 * n) || !alloc_arr(c, c->io_img, 3 * n) || !alloc_arr(c, c->io_flag, 1))
+        return fail(c, SNAP_ERR_OOM, "I/O staging");
+    return SNAP_OK;
+}
+
+// One copy of the tag-ordered triples in each direction; the reordering,
+// wrapping and image bookkeeping run on the device (io.cu).
 extern "C" snap_status snap_set_positions(snap_ctx *c, const double *pos3, const double *vel3)
 {
     snap_status s = check_ready(c);
     if (s != SNAP_OK) return s;
     if (c->n > 0 && !pos3) return fail(c, SNAP_ERR_ARG, "positions are required");
-    std::vector<int32_t> img((size_t)c->n * 3, 0);
-    if ((s = positions_in(c, pos3, &img)) != SNAP_OK) return s;
-    if (vel3 && (s = velocities_in(c, vel3)) != SNAP_OK) return s;
-    std::vector<int32_t> ic(c->n);
-    int32_t *idst[3] = {c->A.ix, c->A.iy, c->A.iz};
-    int32_t *istg[3] = {c->B.ix, c->B.iy, c->B.iz};
-    for (int d = 0; d < 3; ++d) {
-        for (int64_t t = 0; t < c->n; ++t) ic[t] = img[3 * t + d];
-        if ((s = upload_in<int32_t>(c, idst[d], istg[d], ic.data(), c->n)) != SNAP_OK) return s;
+    if (c->n == 0) return SNAP_OK;
+    if ((s = ensure_io(c)) != SNAP_OK) return s;
+    const Launch L = launch(c);
+    const size_t bytes = sizeof(double) * 3 * (size_t)c->n;
+    CUDA_TRY(c, cudaMemcpyAsync(c->io3, pos3, bytes, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->io_flag, 0, sizeof(uint32_t), c->stream));
+    launch_nonfinite(c->io3, 3 * c->n, c->io_flag, L);
+    uint32_t bad = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&bad, c->io_flag, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (bad) return fail(c, SNAP_ERR_NONFINITE, "non-finite input position");
+    launch_pos_in(c->io3, c->P, c->A, L);
+    if (vel3) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->io3, vel3, bytes, cudaMemcpyHostToDevice, c->stream));
+        launch_vel_in(c->io3, c->A, c->fp64, c->n, L);
     }
+    CUDA_TRY(c, cudaGetLastError());
     return set_need_rebuild(c);
 }
 
@@ -1282,30 +1304,18 @@ snap_status raw_positions_images(snap_ctx *c, double *pos3, int32_t *img3)
     return SNAP_OK;
 }
 
-snap_status wrapped_positions_images(snap_ctx *c, double *pos3, int32_t *img3)
-{
-    snap_status s = raw_positions_images(c, pos3, img3);
-    if (s != SNAP_OK) return s;
-    for (int64_t t = 0; t < c->n; ++t) {
-        const RepHost &R = c->reps[rep_of_tag(c, t)];
-        for (int d = 0; d < 3; ++d) {
-            double &x = pos3[3 * t + d];
-            if (x >= 0.0 && x < R.L[d]) continue;
-            int32_t k = 0;
-            wrap_host(x, k, R.L[d]);
-            img3[3 * t + d] += k;
-        }
-    }
-    return SNAP_OK;
-}
-
 extern "C" snap_status snap_get_positions(snap_ctx *c, double *pos3)
 {
     snap_status s = check_ready(c);
     if (s != SNAP_OK) return s;
     if (c->n > 0 && !pos3) return fail(c, SNAP_ERR_ARG, "pos3 is NULL");
-    std::vector<int32_t> img((size_t)c->n * 3);
-    return wrapped_positions_images(c, pos3, img.data());
+    if (c->n == 0) return SNAP_OK;
+    if ((s = ensure_io(c)) != SNAP_OK) return s;
+    launch_pos_out(c->io3, nullptr, c->P, c->A, launch(c));
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(pos3, c->io3, sizeof(double) * 3 * (size_t)c->n, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNAP_OK;
 }
 
 extern "C" snap_status snap_get_velocities(snap_ctx *c, double *vel3)
@@ -1313,22 +1323,12 @@ extern "C" snap_status snap_get_velocities(snap_ctx *c, double *vel3)
     snap_status s = check_ready(c);
     if (s != SNAP_OK) return s;
     if (c->n > 0 && !vel3) return fail(c, SNAP_ERR_ARG, "vel3 is NULL");
-    std::vector<double> v(c->n);
-    const double *src[3] = {c->A.vx, c->A.vy, c->A.vz};
-    double *stg[3] = {c->B.vx, c->B.vy, c->B.vz};
-    if (!c->fp64) {
-        launch_v4_out(stg[0], stg[1], stg[2], c->A.v4, c->A.rtag, c->n, launch(c));
-        CUDA_TRY(c, cudaGetLastError());
-    }
-    for (int d = 0; d < 3; ++d) {
-        if (c->fp64) {
-            if ((s = download_out<double>(c, v.data(), src[d], stg[d], c->n)) != SNAP_OK) return s;
-        } else {
-            CUDA_TRY(c, cudaMemcpyAsync(v.data(), stg[d], sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream));
-            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-        }
-        for (int64_t t = 0; t < c->n; ++t) vel3[3 * t + d] = v[t];
-    }
+    if (c->n == 0) return SNAP_OK;
+    if ((s = ensure_io(c)) != SNAP_OK) return s;
+    launch_vel_out(c->io3, c->A, c->fp64, c->n, launch(c));
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(vel3, c->io3, sizeof(double) * 3 * (size_t)c->n, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return SNAP_OK;
 }
 
@@ -1337,8 +1337,14 @@ extern "C" snap_status snap_get_images(snap_ctx *c, int32_t *img3)
     snap_status s = check_ready(c);
     if (s != SNAP_OK) return s;
     if (c->n > 0 && !img3) return fail(c, SNAP_ERR_ARG, "img3 is NULL");
-    std::vector<double> pos((size_t)c->n * 3);
-    return wrapped_positions_images(c, pos.data(), img3);
+    if (c->n == 0) return SNAP_OK;
+    if ((s = ensure_io(c)) != SNAP_OK) return s;
+    launch_pos_out(nullptr, c->io_img, c->P, c->A, launch(c));
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(img3, c->io_img, sizeof(int32_t) * 3 * (size_t)c->n, cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNAP_OK;
 }
 
 extern "C" snap_status snap_get_neighbors(snap_ctx *c, int32_t *pairs, int64_t cap, int64_t *n_out)

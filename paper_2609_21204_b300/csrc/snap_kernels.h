@@ -54,6 +54,12 @@ template <typename T> void launch_in(T *dst_sorted, const T *src_tag, const int3
 template <typename T> void launch_out(T *dst_tag, const T *src_sorted, const int32_t *rtag, long long n, Launch L);
 void launch_force_out(double *dst3, const void *force, bool fp64, const int32_t *rtag, long long n, Launch L);
 void launch_iota(int32_t *dst, long long n, Launch L);
+// host I/O in tag-ordered (x, y, z) triples, converted on the device (io.cu)
+void launch_nonfinite(const double *v, long long m, uint32_t *flag, Launch L);
+void launch_pos_in(const double *src3, const DevParams &P, const DevArrays &A, Launch L);
+void launch_pos_out(double *dst3, int32_t *img3, const DevParams &P, const DevArrays &A, Launch L);
+void launch_vel_in(const double *src3, const DevArrays &A, bool fp64, long long n, Launch L);
+void launch_vel_out(double *dst3, const DevArrays &A, bool fp64, long long n, Launch L);
 // mixed-mode FP32 velocities <-> tag-ordered FP64 columns
 void launch_v4_in(float4 *v4, const double *vx, const double *vy, const double *vz, const int32_t *rtag,
                   long long n, Launch L);
