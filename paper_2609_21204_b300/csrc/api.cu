@@ -81,6 +81,7 @@ struct snap_ctx {
     // graphs
     cudaGraphExec_t graph = nullptr;
     bool graph_dirty = true;
+    void *graph_key = nullptr;       // A.pos4 when the graph was captured (the step swaps pos4/pos4n)
     int nbr_cap = 0;
     int rnbr_cap = 0;
 };
@@ -364,13 +365,20 @@ void seq_sweep(snap_ctx *c, bool forced)
     }
 }
 
+// force + integration in one kernel that writes the new coordinates to the
+// second buffer; the host swaps the two buffers after queueing it
+void seq_md(snap_ctx *c, Launch L)
+{
+    launch_step_md(c->P, c->A, c->fp64, L);
+    std::swap(c->A.pos4, c->A.pos4n);
+}
+
 void seq_step(snap_ctx *c)
 {
     const Launch L = launch(c);
     seq_rebuild(c);
     seq_sweep(c, false);
-    launch_force(c->P, c->A, c->fp64, false, L);
-    launch_integrate(c->P, c->A, c->fp64, L);
+    seq_md(c, L);
     launch_step_end(c->A, L);
 }
 
@@ -409,8 +417,7 @@ cudaError_t capture_step_conditional(snap_ctx *c)
     e = cudaStreamEndCapture(c->side, &out);
     if (e != cudaSuccess) return e;
     seq_sweep(c, false);
-    launch_force(c->P, c->A, c->fp64, false, L);
-    launch_integrate(c->P, c->A, c->fp64, L);
+    seq_md(c, L);
     launch_step_end(c->A, L);
     return cudaGetLastError();
 }
@@ -448,6 +455,9 @@ snap_status build_graph(snap_ctx *c)
     const int mode = graph_mode();
     if (!c->side) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
+    static_assert(kGraphSteps % 2 == 0, "a graph must swap pos4/pos4n an even number of times");
+    c->graph_key = c->A.pos4;
+    void *const pos4_0 = c->A.pos4, *const pos4_1 = c->A.pos4n;   // restored after the capture
     CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t ce = cudaSuccess;
     for (int s = 0; s < kGraphSteps && ce == cudaSuccess; ++s) {
@@ -458,6 +468,8 @@ snap_status build_graph(snap_ctx *c)
             ce = capture_step_conditional(c);
         }
     }
+    c->A.pos4 = pos4_0;   // an even number of swaps; also undoes a capture that stopped early
+    c->A.pos4n = pos4_1;
     if (ce != cudaSuccess) {
         end_dangling_capture(c->side);
         end_dangling_capture(c->stream);
@@ -825,7 +837,8 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
                   alloc_arr(c, D->sp, n) && alloc_arr(c, D->sbt, n) && alloc_arr(c, D->dp, n) &&
                   alloc_arr(c, D->drx, n) && alloc_arr(c, D->dbirth, n) && alloc_arr(c, D->occ, n);
         D->pos4 = dalloc(c, v4 * n);
-        if (!ok || !D->pos4) return bail(SNAP_ERR_OOM, "particles");
+        if (D == &c->A) D->pos4n = dalloc(c, v4 * n);
+        if (!ok || !D->pos4 || (D == &c->A && !D->pos4n)) return bail(SNAP_ERR_OOM, "particles");
         if (!c->fp64 && !alloc_arr(c, D->v4, n)) return bail(SNAP_ERR_OOM, "velocities");
     }
     DevArrays &A = c->A;
@@ -1110,7 +1123,7 @@ extern "C" snap_status snap_step(snap_ctx *c, int64_t nsteps)
     while (cur < target) {
         long long todo = std::min<long long>(target - cur, kPollSteps);
         long long ngraph = graph_mode() == 2 ? 0 : todo / kGraphSteps;
-        if (ngraph > 0 && c->graph_dirty) {
+        if (ngraph > 0 && (c->graph_dirty || c->graph_key != c->A.pos4)) {
             if ((s = build_graph(c)) != SNAP_OK) return s;
         }
         for (long long g = 0; g < ngraph; ++g) CUDA_TRY(c, cudaGraphLaunch(c->graph, c->stream));
@@ -1126,8 +1139,12 @@ extern "C" snap_status snap_step(snap_ctx *c, int64_t nsteps)
             continue;
         }
         if (st) {
+            // the step stopped part-way: regenerate the relative coordinates
+            // from the FP64 positions at the next step
             clear_status(c);
-            return status_to_code(c, st);
+            const snap_status code = status_to_code(c, st);
+            set_need_rebuild(c);
+            return code;
         }
     }
     return SNAP_OK;

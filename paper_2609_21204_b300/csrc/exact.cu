@@ -26,6 +26,7 @@
 
 #include "snap_kernels.h"
 #include "apply.cuh"
+#include "integrate.cuh"
 
 namespace snap {
 
@@ -731,93 +732,22 @@ __global__ void k_apply(DevParams P, DevArrays A, int slot)
 }
 
 // ------------------------------------------------------------ integrator
-// a = F_c(x_t) - gamma v_{t-1/2} + sqrt(2 gamma kT/dt) xi,  xi = sqrt(3)(2u - 1)
-// v_{t+1/2} = v_{t-1/2} + dt a;  x_{t+1} = x_t + dt v_{t+1/2};  wrap into [0, L)
-__device__ __forceinline__ void wrap(double &x, int &img, double L)
-{
-    if (x >= L) {
-        x = __dsub_rn(x, L);
-        img += 1;
-    } else if (x < 0.0) {
-        x = __dadd_rn(x, L);
-        img -= 1;
-        if (x >= L) {
-            x = __dsub_rn(x, L);
-            img += 1;
-        }
-    }
-}
-
+// Langevin integrators (integrate.cuh) reading the forces of k_force and
+// updating the cell-relative coordinates in place.
 template <typename R>
 __global__ void __launch_bounds__(256) k_integrate(DevParams P, DevArrays A)
 {
-    using V = typename Vec4<R>::T;
     const long long i = gtid();
     if (i >= P.n) return;
     if (!status_ok(A.status)) return;
     const long long step = *A.step;
-    const int rp = rep_of(P, A, i);
-    const RepDev &Rp = A.reps[rp];
-    const uint32_t tl = (uint32_t)(A.tag[i] - Rp.tag_off);
-    const U4 w = philox10(U4{(uint32_t)((unsigned long long)step & 0xFFFFFFFFull),
-                             (uint32_t)((unsigned long long)step >> 32), tl, 0u},
-                          Rp.key0, rx_key1(Rp, 0, kLangevin));
-    const V f = reinterpret_cast<const V *>(A.force)[i];
-    const double fv[3] = {(double)f.x, (double)f.y, (double)f.z};
-    const uint32_t wv[3] = {w.x, w.y, w.z};
-    double *xs[3] = {A.x, A.y, A.z};
-    double *vs[3] = {A.vx, A.vy, A.vz};
-    int *is[3] = {A.ix, A.iy, A.iz};
-    double xn[3];
-    bool finite = true;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const double u = __dadd_rn(__dmul_rn((double)wv[d], 0x1.0p-32), 0x1.0p-33);
-        const double xi = __dmul_rn(P.sqrt3, __dsub_rn(__dmul_rn(2.0, u), 1.0));
-        const double v0 = vs[d][i];
-        const double drag = __dmul_rn(P.gamma, v0);
-        const double acc = __dadd_rn(__dsub_rn(fv[d], drag), __dmul_rn(Rp.noise_c, xi));
-        const double v1 = __dadd_rn(v0, __dmul_rn(P.dt, acc));
-        double x1 = __dadd_rn(xs[d][i], __dmul_rn(P.dt, v1));
-        finite = finite && isfinite(x1);
-        int img = is[d][i];
-        wrap(x1, img, Rp.L[d]);
-        vs[d][i] = v1;
-        xs[d][i] = x1;
-        is[d][i] = img;
-        xn[d] = x1;
-    }
-    if (!finite) {
-        atomicOr(A.status, (uint32_t)kStNonfinite);
-        return;
-    }
-    // relative coordinates against the frozen cell origin, minimum image
-    V p = reinterpret_cast<V *>(A.pos4)[i];
-    const uint32_t bits = w_bits(p);
-    const int c[3] = {bits_cx(bits), bits_cy(bits), bits_cz(bits)};
-    double rel[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        double r = __dsub_rn(xn[d], __dmul_rn((double)c[d], Rp.w[d]));
-        if (r > Rp.halfL[d]) r = __dsub_rn(r, Rp.L[d]);
-        else if (r < -Rp.halfL[d]) r = __dadd_rn(r, Rp.L[d]);
-        rel[d] = r;
-    }
-    p.x = (R)rel[0]; p.y = (R)rel[1]; p.z = (R)rel[2];
-    reinterpret_cast<V *>(A.pos4)[i] = p;
-    const float4 ref = A.ref4[i];
-    const float ex = (float)rel[0] - ref.x, ey = (float)rel[1] - ref.y, ez = (float)rel[2] - ref.z;
-    if (ex * ex + ey * ey + ez * ez > P.disp2f) *A.need_rebuild = 1;
+    const RepDev &Rp = A.reps[rep_of(P, A, i)];
+    const double4_32a f = reinterpret_cast<const double4_32a *>(A.force)[i];
+    const double fv[3] = {f.x, f.y, f.z};
+    double4_32a *pos = reinterpret_cast<double4_32a *>(A.pos4);
+    integrate_fp64(P, A, i, step, Rp, fv, pos[i], pos);
 }
 
-// Mixed-precision Langevin step: the kick and the velocity in FP32, the
-// position accumulated in FP64 (x += dt v, one FP64 fma and one conversion per
-// axis).  The cell-relative FP32 coordinate used by the force loop advances
-// by the same FP32 displacement (one FP32 fma), and every kMixedResync steps
-// (and at every rebuild) it is reset to (float)(x - origin) from the FP64
-// position, so it never drifts by more than kMixedResync roundings of a
-// coordinate below 4 (8 x 2.4e-7 < 2e-6).  Positions stay unwrapped between
-// neighbour-list rebuilds (the rebuild wraps them).
 __global__ void __launch_bounds__(256) k_integrate_mixed(DevParams P, DevArrays A)
 {
     const long long i = gtid();
@@ -825,51 +755,9 @@ __global__ void __launch_bounds__(256) k_integrate_mixed(DevParams P, DevArrays 
     if (!status_ok(A.status)) return;
     const long long step = *A.step;
     const RepDev &Rp = A.reps[rep_of(P, A, i)];
-    const uint32_t tl = (uint32_t)(A.tag[i] - Rp.tag_off);
-    const U4 w = philox10(U4{(uint32_t)((unsigned long long)step & 0xFFFFFFFFull),
-                             (uint32_t)((unsigned long long)step >> 32), tl, 0u},
-                          Rp.key0, rx_key1(Rp, 0, kLangevin));
     const float4 f = reinterpret_cast<const float4 *>(A.force)[i];
-    float4 v = A.v4[i];
-    float4 p = reinterpret_cast<float4 *>(A.pos4)[i];
-    const float cn = (float)Rp.noise_c, g = (float)P.gamma, s3 = (float)P.sqrt3, dt = (float)P.dt;
-    // xi = sqrt(3) (2u - 1) with u = (w >> 8 + 1/2) 2^-24 in (0, 1)
-    const float ux = fmaf((float)(w.x >> 8), 0x1.0p-24f, 0x1.0p-25f);
-    const float uy = fmaf((float)(w.y >> 8), 0x1.0p-24f, 0x1.0p-25f);
-    const float uz = fmaf((float)(w.z >> 8), 0x1.0p-24f, 0x1.0p-25f);
-    v.x = fmaf(dt, fmaf(cn, s3 * fmaf(2.0f, ux, -1.0f), fmaf(-g, v.x, f.x)), v.x);
-    v.y = fmaf(dt, fmaf(cn, s3 * fmaf(2.0f, uy, -1.0f), fmaf(-g, v.y, f.y)), v.y);
-    v.z = fmaf(dt, fmaf(cn, s3 * fmaf(2.0f, uz, -1.0f), fmaf(-g, v.z, f.z)), v.z);
-    const double x1 = fma(P.dt, (double)v.x, A.x[i]);
-    const double y1 = fma(P.dt, (double)v.y, A.y[i]);
-    const double z1 = fma(P.dt, (double)v.z, A.z[i]);
-    if ((step & (kMixedResync - 1)) == 0) {          // uniform over the grid
-        // origin of the frozen cell, as the rebuild computed it
-        const uint32_t b = w_bits(p);
-        p.x = (float)(x1 - (double)bits_cx(b) * Rp.w[0]);
-        p.y = (float)(y1 - (double)bits_cy(b) * Rp.w[1]);
-        p.z = (float)(z1 - (double)bits_cz(b) * Rp.w[2]);
-    } else {
-        p.x = fmaf(dt, v.x, p.x);
-        p.y = fmaf(dt, v.y, p.y);
-        p.z = fmaf(dt, v.z, p.z);
-    }
-    // finiteness from the exponent bits (no FP64 compare)
-    const unsigned long long bad = 0x7FF0000000000000ull;
-    if (((unsigned long long)__double_as_longlong(x1) & bad) == bad ||
-        ((unsigned long long)__double_as_longlong(y1) & bad) == bad ||
-        ((unsigned long long)__double_as_longlong(z1) & bad) == bad) {
-        atomicOr(A.status, (uint32_t)kStNonfinite);
-        return;
-    }
-    A.x[i] = x1;
-    A.y[i] = y1;
-    A.z[i] = z1;
-    A.v4[i] = v;
-    reinterpret_cast<float4 *>(A.pos4)[i] = p;
-    const float4 ref = A.ref4[i];
-    const float ex = p.x - ref.x, ey = p.y - ref.y, ez = p.z - ref.z;
-    if (ex * ex + ey * ey + ez * ez > P.disp2f) *A.need_rebuild = 1;
+    float4 *pos = reinterpret_cast<float4 *>(A.pos4);
+    integrate_mixed(P, A, i, step, Rp, f.x, f.y, f.z, pos[i], pos);
 }
 
 __global__ void k_step_end(DevArrays A)

@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "snap_kernels.h"
+#include "integrate.cuh"
 
 namespace snap {
 
@@ -450,19 +451,17 @@ __device__ __forceinline__ bool bond_factor(const DevParams &P, int bt, R r2, R 
     return true;
 }
 
+// Force on particle i: WCA/LJ pairs over the force list, static and dynamic
+// bonds; the energy terms when E.  Returns false (and latches the status) on
+// a FENE overstretch.
 template <typename R, bool E>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_force(DevParams P, DevArrays A)
+__device__ __forceinline__ bool force_particle(const DevParams &P, const DevArrays &A, long long i,
+                                               const typename Vec4<R>::T &pi, const RepDev &Rp, R &fx, R &fy, R &fz,
+                                               double &ep, double &eb, double &vir)
 {
     using V = typename Vec4<R>::T;
-    const long long i = gtid();
-    if (i >= P.n) return;
-    if (!status_ok(A.status)) return;
     const V *pos = reinterpret_cast<const V *>(A.pos4);
-    const V pi = pos[i];
     const int ti = bits_type(w_bits(pi));
-    const RepDev &Rp = A.reps[rep_of(P, A, i)];
-    R fx = 0, fy = 0, fz = 0;
-    double ep = 0.0, eb = 0.0, vir = 0.0;
     const int nn = A.nn[i];
     const long long stride = P.nbr_stride;
     const int *nb = A.nbr + i;
@@ -548,6 +547,21 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_force(DevParams
         if (E) { eb += 0.5 * u; vir -= 0.5 * (double)fb * (double)r2; }
     }
     if (bad) atomicOr(A.status, (uint32_t)kStFene);
+    return !bad;
+}
+
+template <typename R, bool E>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_force(DevParams P, DevArrays A)
+{
+    using V = typename Vec4<R>::T;
+    const long long i = gtid();
+    if (i >= P.n) return;
+    if (!status_ok(A.status)) return;
+    const V pi = reinterpret_cast<const V *>(A.pos4)[i];
+    const RepDev &Rp = A.reps[rep_of(P, A, i)];
+    R fx = 0, fy = 0, fz = 0;
+    double ep = 0.0, eb = 0.0, vir = 0.0;
+    force_particle<R, E>(P, A, i, pi, Rp, fx, fy, fz, ep, eb, vir);
     V f;
     f.x = fx; f.y = fy; f.z = fz; f.w = 0;
     reinterpret_cast<V *>(A.force)[i] = f;
@@ -563,6 +577,31 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_force(DevParams
         A.e_part[4 * i + 1] = eb;
         A.e_part[4 * i + 2] = vir;
         A.e_part[4 * i + 3] = 0.5 * (vx * vx + vy * vy + vz * vz);
+    }
+}
+
+// One MD step of a particle after the sweep: its force and its Langevin
+// update in one pass (the force never goes to memory).  Neighbours' positions
+// are read from pos4 while the new relative coordinate goes to pos4n, the
+// other of two buffers, which the host swaps after the step.
+template <typename R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_step_md(DevParams P, DevArrays A)
+{
+    using V = typename Vec4<R>::T;
+    const long long i = gtid();
+    if (i >= P.n) return;
+    if (!status_ok(A.status)) return;
+    const V pi = reinterpret_cast<const V *>(A.pos4)[i];
+    const RepDev &Rp = A.reps[rep_of(P, A, i)];
+    R fx = 0, fy = 0, fz = 0;
+    double ep = 0.0, eb = 0.0, vir = 0.0;
+    if (!force_particle<R, false>(P, A, i, pi, Rp, fx, fy, fz, ep, eb, vir)) return;
+    const long long step = *A.step;
+    if constexpr (sizeof(R) == 8) {
+        const double fv[3] = {fx, fy, fz};
+        integrate_fp64(P, A, i, step, Rp, fv, pi, reinterpret_cast<double4_32a *>(A.pos4n));
+    } else {
+        integrate_mixed(P, A, i, step, Rp, fx, fy, fz, pi, reinterpret_cast<float4 *>(A.pos4n));
     }
 }
 
@@ -671,6 +710,14 @@ void launch_rebuild_done(const DevArrays &A, Launch L) { k_rebuild_done<<<1, 1, 
 void launch_set_rebuild_cond(const DevArrays &A, cudaGraphConditionalHandle h, Launch L)
 {
     k_set_rebuild_cond<<<1, 1, 0, L.stream>>>(A, h);
+}
+
+void launch_step_md(const DevParams &P, const DevArrays &A, bool fp64, Launch L)
+{
+    if (P.n == 0) return;
+    const unsigned g = grid_for(P.n, L.block);
+    if (fp64) k_step_md<double><<<g, L.block, 0, L.stream>>>(P, A);
+    else k_step_md<float><<<g, L.block, 0, L.stream>>>(P, A);
 }
 
 void launch_force(const DevParams &P, const DevArrays &A, bool fp64, bool energy, Launch L)

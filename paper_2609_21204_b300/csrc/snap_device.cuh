@@ -88,6 +88,7 @@ struct DevArrays {
     int32_t *ix, *iy, *iz;          // image counters
     int32_t *type, *tag, *rtag, *rep;
     void *pos4;                     // float4 or double4_32a: coords relative to frozen cell origin, w = bits
+    void *pos4n;                    // the second pos4 buffer: the fused step writes the new coordinates here
     float4 *ref4;                   // rel coords at the last rebuild (displacement test)
     void *force;                    // float4 or double4_32a (w unused)
     int4 *sp;                       // static partner tags (-1 empty), kSmax per particle

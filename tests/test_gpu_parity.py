@@ -338,3 +338,30 @@ def test_batched_bonded_fraction_matches_oracle_statistics(snapmod):
         o = np.array(orc_series[r][8:])
         se = math.sqrt(g.var() / g.size + o.var() / o.size) + 0.02
         assert abs(g.mean() - o.mean()) < 4 * se, (r, specs[r], g.mean(), o.mean(), se)
+
+
+def test_host_io_wraps_and_counts_images(snapmod):
+    """Positions set outside the box come back wrapped into [0, L) with the
+    crossings in the image counters; velocities round-trip (FP32 in mixed
+    mode); non-finite input is rejected without touching the state."""
+    s = random_frozen(seed=61, n=3000, box=14.0, overlap_factor=0.6)
+    L = float(s.box[0])
+    for precision, vtol in (("fp64", 0.0), ("mixed", 1e-7)):
+        sim = snapmod.from_system(s, precision=precision)
+        shift = np.array([[2, -1, 0], [-3, 0, 5], [0, 1, -1]])[np.arange(s.n) % 3]
+        raw = s.pos + shift * L
+        vel = np.random.default_rng(1).normal(size=(s.n, 3))
+        sim.set_positions(raw, vel)
+        got = sim.positions()
+        assert np.all(got >= 0.0) and np.all(got < L)
+        np.testing.assert_allclose(got, s.pos, rtol=0, atol=1e-12)
+        assert np.array_equal(sim.images(), shift)
+        np.testing.assert_allclose(sim.velocities(), vel, rtol=vtol, atol=0)
+        out = np.empty((s.n, 3))
+        assert sim.positions(out=out) is out and np.array_equal(out, got)
+        bad = raw.copy()
+        bad[7, 1] = np.nan
+        with pytest.raises(snapmod.SnapError):
+            sim.set_positions(bad)
+        np.testing.assert_array_equal(sim.positions(), got)
+        sim.close()
