@@ -171,21 +171,23 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def force_traffic_from_profile(n, nbar):
-    """DRAM bytes per launch of the force kernel from the committed ncu summary,
-    if it was taken on the current kernel source; scaled to this launch."""
-    prof = ROOT / "profiles" / "force_kernel_colloid_linker.txt"
+def md_traffic_from_profile(n):
+    """DRAM bytes per launch of the fused force + Langevin kernel from the
+    committed ncu summary, if it was taken on the current kernel sources;
+    scaled to this launch by the particle count."""
+    prof = ROOT / "profiles" / "step_md_kernel_colloid_linker.txt"
     if not prof.exists():
         return None
-    src = (ROOT / "paper_2609_21204_b300" / "csrc" / "md.cu").read_bytes()
-    sha = hashlib.sha256(src).hexdigest()[:16]
+    csrc = ROOT / "paper_2609_21204_b300" / "csrc"
     kv = {}
     for line in prof.read_text().splitlines():
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("md_cu_sha256_16") != sha:
-        return None
+    for f in ("md.cu", "integrate.cuh"):
+        sha = hashlib.sha256((csrc / f).read_bytes()).hexdigest()[:16]
+        if kv.get(f.replace(".", "_") + "_sha256_16") != sha:
+            return None
     try:
         per_particle = float(kv["dram_bytes_per_particle"])
     except (KeyError, ValueError):
@@ -420,24 +422,28 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
     rebuild_ms = {k: round(float(np.mean([r[k] for r in reb])), 5) for k in reb[0]}
     st2 = sim.stats()
     nbar = st2["nlist_entries"] / n
-    force_ms = ph["force"]
-    # algorithmic bytes of the force kernel per particle: own pos4 16, replica id 4,
-    # count 4, 4 per neighbour index, dynamic slots 16 + 4 (static slots 16 + 4
-    # when there are static bonds), force 16
-    bytes_pp = 16 + 4 + 4 + 4 * nbar + 20 + (20 if len(s.static_bonds) else 0) + 16
+    md_ms = ph["md"]
+    # algorithmic bytes per particle of the fused force + Langevin kernel (mixed
+    # precision, one system: no replica ids).  Force part: own pos4 16, count 4,
+    # 4 per neighbour index, dynamic slots 16 + 4 (static slots 16 + 4 when there
+    # are static bonds).  Langevin part: tag 4, velocity 16, FP64 position 24 and
+    # reference position 16 read; FP64 position 24, velocity 16 and the new
+    # relative coordinate 16 written.  Neighbours' coordinates are the same pos4
+    # array and count once.
+    bytes_pp = (16 + 4 + 4 * nbar + 20 + (20 if len(s.static_bonds) else 0)) + (4 + 16 + 24 + 16) + (24 + 16 + 16)
     alg_bytes = bytes_pp * n
     peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / (force_ms / 1e3) / 1e9
-    traffic = force_traffic_from_profile(n, nbar)
+    achieved = alg_bytes / (md_ms / 1e3) / 1e9
+    traffic = md_traffic_from_profile(n)
     sweep_pairs = st2["scanned"] + st2["break_tested"]
     bond_pairs_per_s = sweep_pairs / (ph["sweep"] / 1e3) if ph["sweep"] > 0 else None
 
     # kernels launched: per step the rebuild condition, the sweep (begin + 4 per
-    # reaction: proposals, resolution, accept/break, apply), force, integrate
-    # and step end; per rebuild 10 more (cell keys, 3 scan kernels, scatter,
-    # cell sort, gather, copy back, lists, done)
+    # reaction: proposals and break draws, resolution, acceptance, apply), the
+    # fused force + Langevin kernel and step end; per rebuild 10 more (cell keys,
+    # 3 scan kernels, scatter, cell sort, gather, copy back, lists, done)
     builds = st1["nlist_builds"] - st0["nlist_builds"]
-    launches = K * (1 + (1 + 4 * len(s.reactions)) + 3) + 10 * builds
+    launches = K * (1 + (1 + 4 * len(s.reactions)) + 2) + 10 * builds
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -454,11 +460,11 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
                   "proposals": st2["proposals"], "formed": st2["formed"], "broken": st2["broken"],
                   "n_bonds": st2["n_bonds"], "mean_neighbours": nbar,
                   "nlist_builds_in_timed_region": st1["nlist_builds"] - st0["nlist_builds"]},
-        "roofline": {"kernel": "k_force<float> (pair + bond forces)", "bound": "hbm",
+        "roofline": {"kernel": "k_step_md<float> (pair + bond forces, Langevin update)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_kind, "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg_bytes,
-                     "launch_ms": force_ms},
+                     "launch_ms": md_ms},
     }
     if not args.no_fp64:
         sim.close()

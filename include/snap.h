@@ -193,8 +193,9 @@ snap_status snap_step(snap_ctx *, int64_t nsteps);
 /* Advance nsteps MD steps launched one kernel at a time with CUDA events
  * between the phases, and write the average milliseconds per step of each
  * phase to ms[SNAP_NPHASES]: [0] neighbour-list maintenance (all rebuild
- * kernels, mostly early exits), [1] bond sweep, [2] force kernel, [3]
- * integrator + step end.  Same results as snap_step; slower (no graphs). */
+ * kernels, mostly early exits), [1] bond sweep, [2] the force + Langevin
+ * kernel of the production step, [3] step end.  Same kernels and results as
+ * snap_step; slower (no graphs). */
 #define SNAP_NPHASES 4
 snap_status snap_step_profiled(snap_ctx *, int64_t nsteps, double *ms);
 /* One neighbour-list rebuild at the current positions (forced), each kernel

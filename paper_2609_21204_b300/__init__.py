@@ -211,10 +211,11 @@ class Snap:
 
     def step_profiled(self, nsteps):
         """Run nsteps without graphs, timing each phase with CUDA events; returns
-        average ms per step of (rebuild, sweep, force, integrate)."""
+        average ms per step of (rebuild, sweep, md = the fused force + Langevin
+        kernel, step_end)."""
         ms = np.zeros(4)
         self._check(self._lib.snap_step_profiled(self._ctx, int(nsteps), ms.ctypes.data))
-        return dict(rebuild=ms[0], sweep=ms[1], force=ms[2], integrate=ms[3])
+        return dict(rebuild=ms[0], sweep=ms[1], md=ms[2], step_end=ms[3])
 
     REBUILD_PHASES = ("cell_key", "scan", "scatter", "cell_sort", "gather", "copyback", "nlist", "done")
 

@@ -1173,9 +1173,8 @@ extern "C" snap_status snap_step_profiled(snap_ctx *c, int64_t nsteps, double *m
         cudaEventRecord(e[1], c->stream);
         seq_sweep(c, false);
         cudaEventRecord(e[2], c->stream);
-        launch_force(c->P, c->A, c->fp64, false, L);
+        seq_md(c, L);
         cudaEventRecord(e[3], c->stream);
-        launch_integrate(c->P, c->A, c->fp64, L);
         launch_step_end(c->A, L);
         cudaEventRecord(e[4], c->stream);
     }
