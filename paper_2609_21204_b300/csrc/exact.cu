@@ -26,7 +26,6 @@
 
 #include "snap_kernels.h"
 #include "apply.cuh"
-#include "integrate.cuh"
 
 namespace snap {
 
@@ -731,35 +730,6 @@ __global__ void k_apply(DevParams P, DevArrays A, int slot)
     warp_counts<2>(A.counters, idx, v);
 }
 
-// ------------------------------------------------------------ integrator
-// Langevin integrators (integrate.cuh) reading the forces of k_force and
-// updating the cell-relative coordinates in place.
-template <typename R>
-__global__ void __launch_bounds__(256) k_integrate(DevParams P, DevArrays A)
-{
-    const long long i = gtid();
-    if (i >= P.n) return;
-    if (!status_ok(A.status)) return;
-    const long long step = *A.step;
-    const RepDev &Rp = A.reps[rep_of(P, A, i)];
-    const double4_32a f = reinterpret_cast<const double4_32a *>(A.force)[i];
-    const double fv[3] = {f.x, f.y, f.z};
-    double4_32a *pos = reinterpret_cast<double4_32a *>(A.pos4);
-    integrate_fp64(P, A, i, step, Rp, fv, pos[i], pos);
-}
-
-__global__ void __launch_bounds__(256) k_integrate_mixed(DevParams P, DevArrays A)
-{
-    const long long i = gtid();
-    if (i >= P.n) return;
-    if (!status_ok(A.status)) return;
-    const long long step = *A.step;
-    const RepDev &Rp = A.reps[rep_of(P, A, i)];
-    const float4 f = reinterpret_cast<const float4 *>(A.force)[i];
-    float4 *pos = reinterpret_cast<float4 *>(A.pos4);
-    integrate_mixed(P, A, i, step, Rp, f.x, f.y, f.z, pos[i], pos);
-}
-
 __global__ void k_step_end(DevArrays A)
 {
     if (!status_ok(A.status)) return;
@@ -807,13 +777,6 @@ void launch_sweep_reaction(const DevParams &P, const DevArrays &A, int slot, Lau
 void launch_sweep_reaction_forced(const DevParams &P, const DevArrays &A, int slot, Launch L)
 {
     sweep_reaction<true>(P, A, slot, L);
-}
-
-void launch_integrate(const DevParams &P, const DevArrays &A, bool fp64, Launch L)
-{
-    if (P.n == 0) return;
-    if (fp64) k_integrate<double><<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A);
-    else k_integrate_mixed<<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A);
 }
 
 void launch_step_end(const DevArrays &A, Launch L) { k_step_end<<<1, 1, 0, L.stream>>>(A); }

@@ -3,9 +3,9 @@
 //   v_{t+1/2} = v_{t-1/2} + dt a;  x_{t+1} = x_t + dt v_{t+1/2}
 // with u from Philox(LANGEVIN; step, tag).  Every floating-point operation is
 // an explicit intrinsic (one rounding each, no contraction), so the result
-// does not depend on the compilation unit.  Used by the integrator kernels
-// and by the fused force + integrate kernel; pos_out receives the new
-// cell-relative coordinate (in place, or the other of two buffers).
+// does not depend on the compilation unit.  Used by the fused force +
+// integrate kernel; pos_out receives the new cell-relative coordinate (the
+// other of two buffers).
 #pragma once
 #include "snap_device.cuh"
 

@@ -48,7 +48,6 @@ void launch_force(const DevParams &P, const DevArrays &A, bool fp64, bool energy
 // force + Langevin update in one kernel; writes the new coordinates to A.pos4n
 // (the caller swaps pos4 and pos4n afterwards)
 void launch_step_md(const DevParams &P, const DevArrays &A, bool fp64, Launch L);
-void launch_integrate(const DevParams &P, const DevArrays &A, bool fp64, Launch L);
 void launch_step_end(const DevArrays &A, Launch L);
 void launch_reduce_cols(const double *src, int ncol, long long n, double *out, Launch L);
 
