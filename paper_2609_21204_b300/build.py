@@ -30,8 +30,8 @@ def nvcc() -> str:
 def _stale(obj: Path, src: Path) -> bool:
     if not obj.exists():
         return True
-    deps = [src, CSRC / "snap_device.cuh", CSRC / "snap_kernels.h", CSRC / "snap_mlp.h",
-            ROOT / "include" / "snap.h"]
+    # every header of the package and of the C ABI (the kernels share device code in .cuh files)
+    deps = [src, *CSRC.glob("*.cuh"), *CSRC.glob("*.h"), *(ROOT / "include").glob("*.h")]
     return obj.stat().st_mtime < max(d.stat().st_mtime for d in deps if d.exists())
 
 

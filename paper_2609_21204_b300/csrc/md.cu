@@ -299,6 +299,32 @@ __global__ void k_copyback(DevParams P, DevArrays A, DevArrays B)
 // per-particle culling it tests ~4x more pairs; a single loop whose passes
 // either open the next range or test one candidate, to keep the lanes in
 // step, ran 1.6x slower.)
+// Candidates s0..e-1 of one (cell, type) against particle i (offset o of the
+// cell): appended to the force list (F) and/or the reactive list (X).
+template <typename V, bool F, bool X>
+__device__ __forceinline__ int2 scan_range(const V *pos, int s0, int e, long long i, float ox, float oy, float oz,
+                                           float fcut2, float xcut2, int *nbr, int *rnbr, long long stride, int cap,
+                                           int rcap, int cnt, int rcnt)
+{
+    for (int j = s0; j < e; ++j) {
+        if (j == i) continue;
+        const V q = pos[j];
+        const float ddx = (float)q.x + ox;
+        const float ddy = (float)q.y + oy;
+        const float ddz = (float)q.z + oz;
+        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+        if (F && r2 < fcut2) {
+            if (cnt < cap) nbr[(long long)cnt * stride + i] = j;
+            ++cnt;
+        }
+        if (X && r2 < xcut2) {
+            if (rcnt < rcap) rnbr[(long long)rcnt * stride + i] = j;
+            ++rcnt;
+        }
+    }
+    return make_int2(cnt, rcnt);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A)
 {
@@ -344,22 +370,20 @@ __global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A)
                         if (d2 >= fmaxf(fcut2, xcut2)) continue;
                         const int key = t * P.ncell + c;
                         const int s0 = A.cell_start[key], e = A.cell_start[key + 1];
-                        for (int j = s0; j < e; ++j) {
-                            if (j == i) continue;
-                            const V q = pos[j];
-                            const float ddx = (float)q.x + ox;
-                            const float ddy = (float)q.y + oy;
-                            const float ddz = (float)q.z + oz;
-                            const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            if (r2 < fcut2) {
-                                if (cnt < cap) A.nbr[(long long)cnt * stride + i] = j;
-                                ++cnt;
-                            }
-                            if (r2 < xcut2) {
-                                if (rcnt < rcap) A.rnbr[(long long)rcnt * stride + i] = j;
-                                ++rcnt;
-                            }
-                        }
+                        // a zero cut-off takes no pair (r^2 < 0 never holds): such a
+                        // list is skipped, the same for every lane of a type-pure warp
+                        int2 cc;
+                        if (xcut2 <= 0.f)
+                            cc = scan_range<V, true, false>(pos, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr,
+                                                            stride, cap, rcap, cnt, rcnt);
+                        else if (fcut2 <= 0.f)
+                            cc = scan_range<V, false, true>(pos, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr,
+                                                            stride, cap, rcap, cnt, rcnt);
+                        else
+                            cc = scan_range<V, true, true>(pos, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr,
+                                                           stride, cap, rcap, cnt, rcnt);
+                        cnt = cc.x;
+                        rcnt = cc.y;
                     }
                 }
             }
@@ -465,9 +489,16 @@ __device__ __forceinline__ bool force_particle(const DevParams &P, const DevArra
     const int nn = A.nn[i];
     const long long stride = P.nbr_stride;
     const int *nb = A.nbr + i;
-    // bond partners first: their slot words are independent of the pair loop
+    // bond partners first: their slot words and sorted indices are independent
+    // of the pair loop, so the tag -> index loads overlap it
     const int4 dp = A.dp[i];
     const int drx = A.drx[i];
+    int dj[kVmax];
+    {
+        const int dpv[4] = {dp.x, dp.y, dp.z, dp.w};
+#pragma unroll
+        for (int s = 0; s < kVmax; ++s) dj[s] = dpv[s] >= 0 ? A.rtag[dpv[s]] : -1;
+    }
     // pairs in batches of four: four independent index loads, then four
     // independent position loads, then the arithmetic in list order
     for (int k0 = 0; k0 < nn; k0 += 4) {
@@ -527,12 +558,10 @@ __device__ __forceinline__ bool force_particle(const DevParams &P, const DevArra
         }
     }
     // dynamic bonds
-    const int dpv[4] = {dp.x, dp.y, dp.z, dp.w};
 #pragma unroll
     for (int s = 0; s < kVmax; ++s) {
-        const int ptag = dpv[s];
-        if (ptag < 0) continue;
-        const int j = A.rtag[ptag];
+        const int j = dj[s];
+        if (j < 0) continue;
         const V pj = pos[j];
         R dx, dy, dz;
         separation<R>(pi, pj, Rp, dx, dy, dz);
