@@ -62,6 +62,9 @@ def parse():
                     help="formation events logged for training the proposal network (0: skip the leg)")
     ap.add_argument("--learned-epochs", type=int, default=10)
     ap.add_argument("--mh-steps", type=int, default=500)
+    ap.add_argument("--competing-n", type=int, default=262144,
+                    help="particles of the four-reaction soup leg (0: skip the leg)")
+    ap.add_argument("--competing-steps", type=int, default=1000)
     ap.add_argument("--input-cache", default="",
                     help="directory to keep the generated coordinates between invocations")
     return ap.parse_args()
@@ -263,6 +266,43 @@ def _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream):
             "ms_per_step": t * 1e3 / args.batch_steps, "steps": args.batch_steps,
             "particles": nb, "replicas": len(batch), "n_bonds": st["n_bonds"],
             "autotune": {k: tune[k] for k in ("block_size", "skin", "cached", "key")}}
+
+
+def _run_competing(args, torch, snap, barrier, max_all, sum_all, stream):
+    """Four reactions competing for shared sites (App. A, the mobile version of
+    the Eq. Z test): A-B, A-C, D-B, D-C, valence 1, in a WCA soup; four sweep
+    passes per step in an order redrawn every sweep.  Reports throughput and
+    the mass-action cross ratio n_AB n_DC / (n_AC n_DB) against
+    K_AB K_DC / (K_AC K_DB)."""
+    from synth import four_reaction_soup
+    eps = (0.5, 1.5, 1.0, 2.5)
+    s = four_reaction_soup(seed=20260921, n=args.competing_n, rho=0.3, eps=eps)
+    sim = snap.from_system(s, precision="mixed", block_size=128, skin=0.4)
+    sim.step(max(args.warmup, 200))
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.competing_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = max_all(e0.elapsed_time(e1) / 1e3)
+    per_rx = np.zeros(4)
+    for _ in range(50):   # bond counts per reaction, sampled after the timed region
+        sim.step(20)
+        per_rx += np.bincount(sim.bonds()[:, 2], minlength=4)
+    per_rx /= 50
+    sim.close()
+    ab, ac, db, dc = per_rx
+    return {"workload": f"four-reaction soup: {s.n} particles, A, B, C, D in equal numbers (valence 1, "
+                        f"sigma 1) at number density 0.3, reactions A-B, A-C, D-B, D-C with eps {list(eps)} kT, "
+                        "harmonic k=100 r0=1.1 r_max=1.3, WCA, Langevin gamma=1 dt=0.005 kT=1",
+            "value": sum_all(float(s.n)) * args.competing_steps / t, "unit": UNIT,
+            "ms_per_step": t * 1e3 / args.competing_steps, "steps": args.competing_steps,
+            "mean_bonds_per_reaction": per_rx.tolist(),
+            "cross_ratio": float(ab * dc / (ac * db)) if min(ac, db) > 0 else None,
+            "cross_ratio_mass_action": math.exp(eps[0] + eps[3] - eps[1] - eps[2])}
 
 
 def _segment_metrics(y, off, lab):
@@ -489,6 +529,11 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
     if batch is not None:
         sim.close()
         out["batched"] = _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream)
+        sim = make("mixed")
+        sim.step(W)
+    if args.competing_n > 0:
+        sim.close()
+        out["competing"] = _run_competing(args, torch, snap, barrier, max_all, sum_all, stream)
         sim = make("mixed")
         sim.step(W)
     if args.learned_events > 0:

@@ -254,6 +254,59 @@ def random_frozen(seed: int, n: int, box: float, type_fracs=(0.5, 0.5), sigma=(1
         kT=kT, seed=seed)
 
 
+def frozen_squares(seed: int = 1, n_squares: int = 216, eps=(0.5, 1.5, 1.0, 2.0), spacing: float = 5.0,
+                   k: float = 100.0, r0: float = 1.1, r_max: float = 1.3, kT: float = 1.0) -> System:
+    """Four reactions competing for shared binders (App. A, Eq. Z): isolated
+    squares with corners A, B, D, C in that order (types 0, 1, 3, 2; valence 1
+    each), side r0, randomly rotated, on a cubic lattice of the given spacing.
+    The four reactions A-B, A-C, D-B and D-C, one bond type each, join the
+    four edges, all held at the rest length (U_b = 0); the diagonals A-D and
+    B-C do not react.  eps: the four bond free energies in that order."""
+    rng = np.random.default_rng(seed)
+    m = int(math.ceil(n_squares ** (1.0 / 3.0)))
+    L = m * spacing
+    g = np.stack(np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij"),
+                 axis=-1).reshape(-1, 3)[:n_squares] * spacing + 0.5 * spacing
+    corners = np.array([[0.0, 0.0, 0.0], [r0, 0.0, 0.0], [r0, r0, 0.0], [0.0, r0, 0.0]])
+    corners -= corners.mean(axis=0)
+    pos = np.empty((4 * n_squares, 3))
+    for q in range(n_squares):
+        rot, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        pos[4 * q:4 * q + 4] = g[q] + corners @ rot.T
+    pos %= L
+    types = np.tile(np.array([0, 1, 3, 2], np.int32), n_squares)
+    ea, eb, ec, ed = (float(e) for e in eps)
+    return System(
+        name="frozen_squares", box=np.array([L, L, L]), type_names=["A", "B", "C", "D"],
+        sigma=np.ones(4), valence=np.ones(4, np.int32),
+        eps_pair=np.ones((4, 4)), rcut=None,
+        bond_types=[BondType(HARMONIC, k, r0) for _ in range(4)],
+        reactions=[Reaction(0, 1, 0, 0.0, r_max, ea), Reaction(0, 2, 1, 0.0, r_max, eb),
+                   Reaction(3, 1, 2, 0.0, r_max, ec), Reaction(3, 2, 3, 0.0, r_max, ed)],
+        pos=pos, vel=np.zeros_like(pos), types=types,
+        static_bonds=np.zeros((0, 2), np.int32), static_bond_types=np.zeros(0, np.int32),
+        kT=kT, seed=seed)
+
+
+def four_reaction_soup(seed: int = 1, n: int = 2000, rho: float = 0.3, eps=(0.5, 1.5, 1.0, 2.0),
+                       k: float = 100.0, r0: float = 1.1, r_max: float = 1.3, overlap_factor: float = 1.0,
+                       kT: float = 1.0) -> System:
+    """The four reactions of `frozen_squares` (A-B, A-C, D-B, D-C, valence 1,
+    one bond type each) in a mobile WCA soup of equal numbers of A, B, C and D
+    at number density rho (App. A, the dynamic version of the Eq. Z test).
+    overlap_factor < 1 packs contested frozen configurations for sweep parity."""
+    box = (n / rho) ** (1.0 / 3.0)
+    s = random_frozen(seed=seed, n=n, box=box, type_fracs=(0.25, 0.25, 0.25, 0.25), sigma=(1.0,) * 4,
+                      valence=(1, 1, 1, 1), k=k, r0=r0, r_max=r_max, overlap_factor=overlap_factor, kT=kT)
+    ea, eb, ec, ed = (float(e) for e in eps)
+    s.name = "four_reaction_soup"
+    s.type_names = ["A", "B", "C", "D"]
+    s.bond_types = [BondType(HARMONIC, k, r0) for _ in range(4)]
+    s.reactions = [Reaction(0, 1, 0, 0.0, r_max, ea), Reaction(0, 2, 1, 0.0, r_max, eb),
+                   Reaction(3, 1, 2, 0.0, r_max, ec), Reaction(3, 2, 3, 0.0, r_max, ed)]
+    return s
+
+
 def frozen_stars(seed: int = 1, n_stars: int = 125, arms: int = 4, r_lo: float = 1.0, r_hi: float = 1.25,
                  spacing: float = 5.0, eps: float = 1.0, k: float = 20.0, r0: float = 1.1,
                  r_max: float = 1.3, kT: float = 1.0, min_sep: float = 0.8) -> System:
