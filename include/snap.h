@@ -157,9 +157,13 @@ snap_status snap_add_static_bonds(snap_ctx *, int64_t nb, const int32_t *tag_pai
 
 /* Register a reaction between particle types type_a and type_b forming bonds
  * of harmonic bond type bt when r_min <= r <= r_max, with per-sweep
- * probabilities p_on0 and p_off (Eqs. 1-3; K = p_on0/p_off).  self_avoid must
- * be 0 (intramolecular exclusion is not built).  Writes the reaction index to
- * *index_out when non-NULL. */
+ * probabilities p_on0 and p_off (Eqs. 1-3; K = p_on0/p_off).  self_avoid = 1
+ * excludes intramolecular bonds (Sec. II.D): two sites of one molecule — a
+ * connected component of the static bonds, traced by the library when the
+ * first step runs and again whenever static bonds are added — are never
+ * partners of this reaction; 0 admits them; other values return SNAP_ERR_ARG.
+ * The Metropolis–Hastings move set (snap_set_mh) refuses such a reaction.
+ * Writes the reaction index to *index_out when non-NULL. */
 snap_status snap_add_reaction(snap_ctx *, int32_t type_a, int32_t type_b, int32_t bt,
                               double r_min, double r_max, double p_on0, double p_off,
                               int32_t self_avoid, int32_t *index_out);

@@ -67,7 +67,7 @@ class State(C.Structure):
                 ("dbirth", C.c_void_p), ("occ", C.c_void_p),
                 ("fx", C.c_void_p), ("fy", C.c_void_p), ("fz", C.c_void_p),
                 ("pe", C.c_void_p), ("life_hist", C.c_void_p), ("nhist", C.c_int32),
-                ("step", C.c_int64)]
+                ("step", C.c_int64), ("mol", C.c_void_p)]
 
 
 class SweepStats(C.Structure):
@@ -146,6 +146,19 @@ def rates_from_eps(eps: float, p_on0: float = 1.0):
     return p_on0, p_on0 * math.exp(-eps)
 
 
+def molecules(n, static_bonds):
+    """Molecule id of every particle (Sec. II.D): the connected components of
+    the graph whose edges are the static bonds, labelled by scipy's
+    connected-components routine; a particle without static bonds is a
+    molecule of its own."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    b = np.asarray(static_bonds, dtype=np.int64).reshape(-1, 2)
+    g = coo_matrix((np.ones(b.shape[0]), (b[:, 0], b[:, 1])), shape=(n, n))
+    _, labels = connected_components(g, directed=False)
+    return labels.astype(np.int32)
+
+
 class OracleSystem:
     """One system held in tag order with numpy arrays the C code reads and writes."""
 
@@ -203,6 +216,7 @@ class OracleSystem:
         self.fz = np.zeros(n)
         self.pe = np.zeros(n)
         self.life_hist = np.zeros(nhist, dtype=np.int64)
+        self.mol = molecules(n, s.static_bonds)
         self.step = 0
         self._state = State()
         self._sync_ptrs()
@@ -210,7 +224,7 @@ class OracleSystem:
     def _sync_ptrs(self):
         S = self._state
         for f in ("x", "y", "z", "vx", "vy", "vz", "img", "type", "sp", "sbt", "dp", "drx",
-                  "dbirth", "occ", "fx", "fy", "fz", "pe", "life_hist"):
+                  "dbirth", "occ", "fx", "fy", "fz", "pe", "life_hist", "mol"):
             setattr(S, f, _ptr(getattr(self, f)))
         S.nhist = self.life_hist.size
         S.step = self.step

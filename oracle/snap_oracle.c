@@ -28,7 +28,11 @@
  *     CUDA path, which implements the same published recipe, decides alike;
  *   - Langevin: leapfrog form of velocity Verlet with drag -gamma v_{t-1/2}
  *     and a uniform random force sqrt(2 gamma kT / dt) * sqrt(3) (2u - 1);
- *   - no pair exclusions: WCA acts on bonded pairs too.
+ *   - no pair exclusions: WCA acts on bonded pairs too;
+ *   - a molecule is a connected component of the static-bond graph (a
+ *     particle without static bonds is a molecule of its own); the
+ *     self-avoid flag of a reaction removes same-molecule partners from its
+ *     candidates, in the proposal phase and in the MH move set alike.
  *
  * Parity unpinned: none of the functions below is left without a test that
  * ties it to the paper or to mathematics (closed forms, brute force,
@@ -284,6 +288,14 @@ static int orc_is_bonded(const orc_state *S, int64_t i, int64_t j)
     return 0;
 }
 
+/* Intramolecular exclusion (Sec. II.D): with the reaction's self-avoid flag
+ * set, two sites of the same molecule (traced through the static bonds) are
+ * not partners of each other. */
+static int orc_same_molecule(const orc_reaction *R, const orc_state *S, int64_t i, int64_t j)
+{
+    return R->self_avoid && S->mol[i] == S->mol[j];
+}
+
 typedef struct {
     const orc_params *P;
     const orc_state *S;
@@ -309,6 +321,7 @@ static void orc_prop_visit(int64_t j, void *vctx)
     if (!orc_partner_type_ok(c->R, ti, tj)) return;
     if (S->occ[j] >= P->valence[tj]) return;
     if (orc_is_bonded(S, c->i, j)) return;
+    if (orc_same_molecule(c->R, S, c->i, j)) return;
     c->scanned++;
     double dx, dy, dz;
     double r2 = orc_dist2(P, S, c->i, j, &dx, &dy, &dz);
@@ -632,6 +645,7 @@ static int orc_mh_candidates(const orc_params *P, const orc_state *S, const orc_
             if (S->occ[j] >= P->valence[tj]) continue;
             if (orc_is_bonded(S, i, j)) continue;
         }
+        if (orc_same_molecule(R, S, i, j)) continue;
         if (!orc_owner_is(P, i, j)) continue;
         double dx, dy, dz;
         double r2 = orc_dist2(P, S, i, j, &dx, &dy, &dz);

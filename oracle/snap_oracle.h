@@ -34,7 +34,7 @@ typedef struct {
     int32_t type_a, type_b, bond_type;
     double r_min, r_max;
     double p_on0, p_off;       /* per-sweep probabilities, Eq. (2) */
-    int32_t self_avoid;        /* must be 0 */
+    int32_t self_avoid;        /* 1: sites of one molecule (orc_state.mol) do not react with each other */
 } orc_reaction;
 
 typedef struct {
@@ -71,6 +71,8 @@ typedef struct {
     int64_t *life_hist;         /* lifetime histogram in sweeps (nullable) */
     int32_t nhist;
     int64_t step;
+    const int32_t *mol;         /* molecule id per particle: the connected components of the
+                                 * static bonds; read by reactions with self_avoid */
 } orc_state;
 
 typedef struct {

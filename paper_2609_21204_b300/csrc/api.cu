@@ -22,6 +22,7 @@ constexpr int kPollSteps = 2000;    // status poll interval inside snap_step
 struct RxHost {
     int ta, tb, bt;
     double rmin, rmax, pon, poff;
+    int self_avoid;
 };
 
 struct RepHost {
@@ -56,6 +57,7 @@ struct snap_ctx {
     std::vector<std::vector<double>> rep_pon, rep_poff;  // [reaction][replica]
     std::vector<RepHost> reps;
     std::vector<int32_t> sp_host, sbt_host;  // tag-indexed static slots
+    std::vector<int32_t> mol_host;          // molecule id by tag, when a reaction excludes them
     int64_t n_static = 0;                     // static bonds added
     int64_t bonds_base = 0;                  // dynamic bonds set explicitly
     // device
@@ -238,6 +240,7 @@ void fill_params(snap_ctx *c)
         P.rx_ta[a] = c->rx[a].ta;
         P.rx_tb[a] = c->rx[a].tb;
         P.rx_bt[a] = c->rx[a].bt;
+        P.rx_self[a] = c->rx[a].self_avoid;
         P.rx_rmin2[a] = c->rx[a].rmin * c->rx[a].rmin;
         P.rx_rmax2[a] = c->rx[a].rmax * c->rx[a].rmax;
     }
@@ -263,6 +266,41 @@ void fill_params(snap_ctx *c)
 }
 
 // everything that depends on the model (cut-offs -> cell grids -> capacities)
+// Molecule ids (Sec. II.D): connected components of the static bonds by
+// union-find over tags, each labelled by its smallest tag; uploaded by tag
+// when some reaction excludes intramolecular partners, else nothing.
+snap_status upload_molecules(snap_ctx *c)
+{
+    bool any = false;
+    for (const auto &r : c->rx) any = any || r.self_avoid;
+    if (!any) return SNAP_OK;
+    const int64_t n = c->n;
+    std::vector<int32_t> up((size_t)n);
+    for (int64_t t = 0; t < n; ++t) up[t] = (int32_t)t;
+    auto root = [&](int32_t x) {
+        while (up[x] != x) {
+            up[x] = up[up[x]];
+            x = up[x];
+        }
+        return x;
+    };
+    for (int64_t t = 0; t < n; ++t)
+        for (int s = 0; s < kSmax; ++s) {
+            const int32_t u = c->sp_host[4 * (size_t)t + s];
+            if (u < 0) continue;
+            const int32_t ra = root((int32_t)t), rb = root(u);
+            if (ra != rb) up[std::max(ra, rb)] = std::min(ra, rb);   // the smaller tag stays the root
+        }
+    c->mol_host.resize((size_t)n);
+    for (int64_t t = 0; t < n; ++t) c->mol_host[t] = root((int32_t)t);
+    if (!c->A.mol && !alloc_arr(c, c->A.mol, (size_t)std::max<int64_t>(n, 1)))
+        return fail(c, SNAP_ERR_OOM, "molecule ids");
+    CUDA_TRY(c, cudaMemcpyAsync(c->A.mol, c->mol_host.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SNAP_OK;
+}
+
 snap_status ensure_ready(snap_ctx *c)
 {
     if (c->ready) return SNAP_OK;
@@ -330,6 +368,7 @@ snap_status ensure_ready(snap_ctx *c)
     fill_params(c);
     snap_status s = upload_reps(c);
     if (s != SNAP_OK) return s;
+    if ((s = upload_molecules(c)) != SNAP_OK) return s;
     c->ready = true;
     c->graph_dirty = true;
     return SNAP_OK;
@@ -969,6 +1008,10 @@ extern "C" snap_status snap_add_static_bonds(snap_ctx *c, int64_t nb, const int3
     c->n_static += nb;
     c->P.has_static = c->n_static > 0 ? 1 : 0;
     c->graph_dirty = true;
+    if (c->ready) {
+        snap_status s = upload_molecules(c);
+        if (s != SNAP_OK) return s;
+    }
     if (c->particles_set) return upload_static(c);
     return SNAP_OK;
 }
@@ -986,8 +1029,8 @@ extern "C" snap_status snap_add_reaction(snap_ctx *c, int32_t ta, int32_t tb, in
     if (!(rmin >= 0.0) || !(rmax > rmin) || !std::isfinite(rmax)) return fail(c, SNAP_ERR_ARG, "bad formation window");
     if (!(pon >= 0.0 && pon <= 1.0) || !(poff >= 0.0 && poff <= 1.0))
         return fail(c, SNAP_ERR_ARG, "per-sweep probabilities must lie in [0, 1] (Eq. 2)");
-    if (self_avoid != 0) return fail(c, SNAP_ERR_ARG, "intramolecular exclusion is not supported");
-    c->rx.push_back(RxHost{ta, tb, bt, rmin, rmax, pon, poff});
+    if (self_avoid != 0 && self_avoid != 1) return fail(c, SNAP_ERR_ARG, "self_avoid must be 0 or 1");
+    c->rx.push_back(RxHost{ta, tb, bt, rmin, rmax, pon, poff, self_avoid});
     c->rep_pon.push_back(std::vector<double>(c->reps.size(), pon));
     c->rep_poff.push_back(std::vector<double>(c->reps.size(), poff));
     if (index_out) *index_out = (int32_t)c->rx.size() - 1;
@@ -1577,6 +1620,8 @@ extern "C" snap_status snap_set_mh(snap_ctx *c, int32_t mode, const snap_mlp *ml
     if (mode != 0) {
         if (c->rx.size() != 1 || c->reps.size() != 1)
             return fail(c, SNAP_ERR_ARG, "Metropolis-Hastings mode supports one reaction in one system");
+        if (c->rx[0].self_avoid)
+            return fail(c, SNAP_ERR_ARG, "Metropolis-Hastings mode does not support intramolecular exclusion");
         const double side = 2.0 * c->rx[0].rmax + 0.05;
         int nc[3];
         for (int d = 0; d < 3; ++d) {

@@ -193,21 +193,26 @@ __device__ __forceinline__ int push_type(const DevParams &P, const DevArrays &A,
 }
 
 // Partners of site i that may be proposed: available with the partner type
-// (one byte load) and not already bonded to i (sorted indices of i's partners).
+// (one byte load), not already bonded to i (sorted indices of i's partners)
+// and, when the reaction excludes intramolecular bonds (Sec. II.D), not of
+// i's molecule (mol >= 0 only then).
 struct SiteFilter {
     uint8_t pt;
     int b0, b1, b2, b3;
+    int mol;
     __device__ __forceinline__ bool ok(const DevArrays &A, int j) const
     {
-        return A.avail[j] == pt && j != b0 && j != b1 && j != b2 && j != b3;
+        return A.avail[j] == pt && j != b0 && j != b1 && j != b2 && j != b3 && (mol < 0 || A.mol[A.tag[j]] != mol);
     }
 };
 
-__device__ __forceinline__ SiteFilter site_filter(const DevArrays &A, int ti, int ta, int tb, int i)
+__device__ __forceinline__ SiteFilter site_filter(const DevParams &P, const DevArrays &A, int a, int ti, int ta,
+                                                  int tb, int i)
 {
     const int4 dp = A.dp[i];
     SiteFilter f;
     f.pt = (uint8_t)(ti == ta ? tb : ta);
+    f.mol = P.rx_self[a] ? A.mol[A.tag[i]] : -1;
     f.b0 = dp.x >= 0 ? A.rtag[dp.x] : -1;
     f.b1 = dp.y >= 0 ? A.rtag[dp.y] : -1;
     f.b2 = dp.z >= 0 ? A.rtag[dp.z] : -1;
@@ -248,7 +253,7 @@ __device__ __forceinline__ void pull_propose(const DevParams &P, DevArrays &A, i
         const int ta = P.rx_ta[a], tb = P.rx_tb[a];
         if ((ti == ta || ti == tb) && A.occ[i] < P.valence[ti]) {
             const RepDev &R = A.reps[rp];
-            const SiteFilter flt = site_filter(A, ti, ta, tb, (int)i);
+            const SiteFilter flt = site_filter(P, A, a, ti, ta, tb, (int)i);
             const int nn = A.rnn[i];
             const int *nb = A.rnbr + i;
             const long long stride = P.nbr_stride;
@@ -364,7 +369,7 @@ __device__ __forceinline__ void pull_exact(const DevParams &P, DevArrays &A, int
             }
         } else {
             // screen overflow: the plain exact scan
-            const SiteFilter flt = site_filter(A, A.type[i], P.rx_ta[a], P.rx_tb[a], i);
+            const SiteFilter flt = site_filter(P, A, a, A.type[i], P.rx_ta[a], P.rx_tb[a], i);
             const int nn = A.rnn[i];
             for (int k = 0; k < nn; ++k) {
                 const int j = A.rnbr[(long long)k * P.nbr_stride + i];
@@ -462,7 +467,7 @@ __device__ __forceinline__ void push_pass1(const DevParams &P, DevArrays &A, int
     const float4 *pos4 = reinterpret_cast<const float4 *>(A.pos4);
     for (long long q = gtid() >> 5; q < ns; q += warps) {
         const int i = list[q];
-        const SiteFilter flt = site_filter(A, s, ta, tb, i);
+        const SiteFilter flt = site_filter(P, A, a, s, ta, tb, i);
         const int nn = A.rnn[i];
         if (lane == 0) nscan += (unsigned long long)nn;
         const uint32_t bi = cell_bits(P, A, i);
@@ -532,7 +537,7 @@ __device__ __forceinline__ void push_pass2(const DevParams &P, DevArrays &A, int
     for (long long q = gtid() >> 5; q < ns; q += warps) {
         const int i = list[q];
         if (A.prop[i] < 0) continue;                     // warp-uniform: no candidate in window
-        const SiteFilter flt = site_filter(A, s, ta, tb, i);
+        const SiteFilter flt = site_filter(P, A, a, s, ta, tb, i);
         const int nn = A.rnn[i];
         const unsigned long long me = (unsigned long long)(uint32_t)A.tag[i];
         const int pi = A.prop[i];

@@ -47,6 +47,7 @@ struct DevParams {
     float bkf[kMaxBondTypes], br0f[kMaxBondTypes];
     // reactions
     int32_t rx_ta[kMaxRx], rx_tb[kMaxRx], rx_bt[kMaxRx];
+    int32_t rx_self[kMaxRx];   // 1: sites of one molecule do not react with each other (Sec. II.D)
     double rx_rmin2[kMaxRx], rx_rmax2[kMaxRx];
     // integrator
     double dt, half_dt, gamma, sqrt3;
@@ -87,6 +88,8 @@ struct DevArrays {
     float4 *v4;                     // mixed mode velocities (w unused)
     int32_t *ix, *iy, *iz;          // image counters
     int32_t *type, *tag, *rtag, *rep;
+    int32_t *mol;   // molecule id by tag (connected components of the static bonds); null unless a
+                    // reaction excludes intramolecular partners
     void *pos4;                     // float4 or double4_32a: coords relative to frozen cell origin, w = bits
     void *pos4n;                    // the second pos4 buffer: the fused step writes the new coordinates here
     float4 *ref4;                   // rel coords at the last rebuild (displacement test)

@@ -307,6 +307,56 @@ def four_reaction_soup(seed: int = 1, n: int = 2000, rho: float = 0.3, eps=(0.5,
     return s
 
 
+def frozen_loops(seed: int = 1, n_units: int = 125, self_avoid: int = 1, eps: float = 1.0, d: float = 1.1,
+                 spacing: float = 5.0, k: float = 100.0, r0: float = 1.1, r_max: float = 1.3,
+                 kT: float = 1.0) -> System:
+    """Intramolecular exclusion, both ways (Sec. II.D, App. A): every unit holds
+    one molecule P-M-Q (P type 0 and Q type 1, valence 1, joined through a
+    non-reactive bead M of type 2 by two static FENE bonds) whose two sites sit
+    at distance d, and a control pair: a lone P and a lone Q, also at distance
+    d, that belong to different molecules.  Units are randomly rotated on a
+    cubic lattice of the given spacing; the reaction P-Q carries self_avoid."""
+    rng = np.random.default_rng(seed)
+    m = int(math.ceil(n_units ** (1.0 / 3.0)))
+    L = m * spacing
+    g = np.stack(np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij"),
+                 axis=-1).reshape(-1, 3)[:n_units] * spacing + 0.5 * spacing
+    # molecule P, M, Q; control P', Q' two units of length away along z
+    local = np.array([[0.0, 0.0, 0.0], [0.5 * d, 0.9, 0.0], [d, 0.0, 0.0],
+                      [0.0, 0.0, 2.0], [d, 0.0, 2.0]])
+    local -= local.mean(axis=0)
+    pos = np.empty((5 * n_units, 3))
+    for q in range(n_units):
+        rot, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        pos[5 * q:5 * q + 5] = g[q] + local @ rot.T
+    pos %= L
+    types = np.tile(np.array([0, 2, 1, 0, 1], np.int32), n_units)
+    base = 5 * np.arange(n_units, dtype=np.int32)
+    sb = np.concatenate([np.stack([base, base + 1], axis=1), np.stack([base + 1, base + 2], axis=1)])
+    return System(
+        name="frozen_loops", box=np.array([L, L, L]), type_names=["P", "Q", "M"],
+        sigma=np.ones(3), valence=np.array([1, 1, 0], np.int32),
+        eps_pair=np.ones((3, 3)), rcut=None,
+        bond_types=[BondType(FENE, 30.0, 1.5), BondType(HARMONIC, k, r0)],
+        reactions=[Reaction(0, 1, 1, 0.0, r_max, eps, self_avoid)],
+        pos=pos, vel=np.zeros_like(pos), types=types,
+        static_bonds=sb.astype(np.int32), static_bond_types=np.zeros(sb.shape[0], np.int32),
+        kT=kT, seed=seed)
+
+
+def telechelic_rings(seed: int = 1, n_chains: int = 300, beads: int = 3, rho: float = 0.3,
+                     self_avoid: int = 1, eps: float = 3.0, r_max: float = 1.25, kT: float = 1.0) -> System:
+    """Short telechelic chains whose end beads (type S, valence 1) react with
+    each other, S-S, with no crosslinkers: with self_avoid = 0 the two ends of
+    one chain may close it into a ring (a self-loop of the molecule), with
+    self_avoid = 1 they may not (Sec. II.D)."""
+    s = telechelic(seed=seed, n_chains=n_chains, beads=beads, n_x=0, rho=rho, eps=eps, r_max=r_max, kT=kT)
+    s.name = "telechelic_rings"
+    s.valence = np.array([0, 1, 0], np.int32)
+    s.reactions = [Reaction(1, 1, 1, 0.0, r_max, eps, self_avoid)]
+    return s
+
+
 def frozen_stars(seed: int = 1, n_stars: int = 125, arms: int = 4, r_lo: float = 1.0, r_hi: float = 1.25,
                  spacing: float = 5.0, eps: float = 1.0, k: float = 20.0, r0: float = 1.1,
                  r_max: float = 1.3, kT: float = 1.0, min_sep: float = 0.8) -> System:
