@@ -168,6 +168,25 @@ snap_status snap_add_reaction(snap_ctx *, int32_t type_a, int32_t type_b, int32_
                               double r_min, double r_max, double p_on0, double p_off,
                               int32_t self_avoid, int32_t *index_out);
 
+/* Slip bond (Sec. II.D, Eq. slip): bonds of reaction `reaction` break with
+ * P_off(r) = p_off exp(a sqrt(U_b(r)/kT)), capped at 1, evaluated in FP64 at
+ * the bond's separation in every sweep.  At kT = 0 the factor takes its
+ * limits (1 for U_b = 0; P_off = 1 for U_b > 0).  a = 0 (the default) keeps
+ * P_off constant.  a must be finite and >= 0; the modifier excludes the melting
+ * switch on the same reaction and the Metropolis–Hastings move set
+ * (SNAP_ERR_ARG / SNAP_ERR_STATE). */
+snap_status snap_set_slip(snap_ctx *, int32_t reaction, double a);
+
+/* Melting switch (Sec. II.D, Eqs. gT and kT): the rate constants of reaction
+ * `reaction` become k(T) = k_init (1 - g) + k_melt g with
+ * g = (tanh(lambda (T - t_melt)) + 1) / 2 at each replica's set-point kT, and
+ * the per-sweep probabilities P = k n dt (Eq. 2, n = bond_period), replacing
+ * the reaction's p_on0 and p_off in every replica.  Rates must be finite and
+ * >= 0 with P <= 1 (else SNAP_ERR_ARG and nothing changes); excludes the slip
+ * bond on the same reaction. */
+snap_status snap_set_melting(snap_ctx *, int32_t reaction, double lambda, double t_melt,
+                             double kon_init, double koff_init, double kon_melt, double koff_melt);
+
 /* Per-replica rates of one reaction (batched sweeps over the bond energy). */
 snap_status snap_set_reaction_rates(snap_ctx *, int32_t reaction, int32_t replica,
                                     double p_on0, double p_off);

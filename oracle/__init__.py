@@ -44,7 +44,8 @@ def build(force: bool = False) -> Path:
 class Reaction(C.Structure):
     _fields_ = [("type_a", C.c_int32), ("type_b", C.c_int32), ("bond_type", C.c_int32),
                 ("r_min", C.c_double), ("r_max", C.c_double),
-                ("p_on0", C.c_double), ("p_off", C.c_double), ("self_avoid", C.c_int32)]
+                ("p_on0", C.c_double), ("p_off", C.c_double), ("self_avoid", C.c_int32),
+                ("slip_a", C.c_double)]
 
 
 class Params(C.Structure):
@@ -146,6 +147,16 @@ def rates_from_eps(eps: float, p_on0: float = 1.0):
     return p_on0, p_on0 * math.exp(-eps)
 
 
+def melting_rates(T, lam, t_melt, kon_init, koff_init, kon_melt, koff_melt, n, dt):
+    """Melting switch, Eqs. (gT)-(kT), and per-sweep probabilities, Eq. (2):
+    g = (tanh(lam (T - T_melt)) + 1) / 2, k(T) = k_init (1 - g) + k_melt g,
+    P = k n dt.  Returns (P_on^0, P_off)."""
+    g = 0.5 * (math.tanh(lam * (T - t_melt)) + 1.0)
+    kon = kon_init * (1.0 - g) + kon_melt * g
+    koff = koff_init * (1.0 - g) + koff_melt * g
+    return kon * n * dt, koff * n * dt
+
+
 def molecules(n, static_bonds):
     """Molecule id of every particle (Sec. II.D): the connected components of
     the graph whose edges are the static bonds, labelled by scipy's
@@ -183,9 +194,12 @@ class OracleSystem:
             P.bkind[i], P.bk[i], P.br0[i] = int(bt.kind), float(bt.k), float(bt.r0)
         P.nrx = len(s.reactions)
         for i, r in enumerate(s.reactions):
-            pon, poff = rates_from_eps(r.eps, p_on0)
+            if getattr(r, "melt", None) is not None:
+                pon, poff = melting_rates(float(s.kT), *r.melt, int(s.bond_period), float(s.dt))
+            else:
+                pon, poff = rates_from_eps(r.eps, p_on0)
             P.rx[i] = Reaction(r.type_a, r.type_b, r.bond_type, r.r_min, r.r_max, pon, poff,
-                               r.self_avoid)
+                               r.self_avoid, float(getattr(r, "slip_a", 0.0)))
         P.bond_period = int(s.bond_period)
         self.params = P
         self.n = n

@@ -176,6 +176,24 @@ static double orc_p_on(const orc_params *P, const orc_reaction *R, double r)
     return (U <= 0.0) ? R->p_on0 : 0.0;
 }
 
+/* Slip bond, Eq. (slip): a bond at separation r breaks with
+ * P_off(r) = P_off^0 exp(a sqrt(U_b(r)/kT)), capped at 1.  As kT -> 0 the
+ * factor tends to 1 for U_b = 0 and to infinity (P_off -> 1) for U_b > 0; at
+ * kT = 0 it takes those limits.  An exponent of 700 or more caps at once. */
+static double orc_p_off(const orc_params *P, const orc_reaction *R, double r)
+{
+    if (R->slip_a == 0.0 || R->p_off == 0.0) return R->p_off;
+    double dr = r - P->br0[R->bond_type];
+    double U = 0.5 * P->bk[R->bond_type] * dr * dr;
+    double x;
+    if (P->kT > 0.0) x = U / P->kT;
+    else x = (U > 0.0) ? INFINITY : 0.0;
+    double e = R->slip_a * sqrt(x);
+    if (!(e < 700.0)) return 1.0;
+    double p = R->p_off * orc_exp(e);
+    return p < 1.0 ? p : 1.0;
+}
+
 /* ------------------------------------------------------------ geometry */
 
 static double orc_min_image(double d, double L, double invL)
@@ -512,7 +530,12 @@ int orc_sweep(const orc_params *P, orc_state *S, int64_t step, orc_sweep_stats *
                 local.break_tested++;
                 uint32_t w[4];
                 orc_pair_draw(P, a, ORC_BREAK, step, i, j, w);
-                if (orc_u53(w[0], w[1]) < R->p_off) brk[i * ORC_VMAX + s] = 1;
+                double p_off = R->p_off;
+                if (R->slip_a != 0.0) {
+                    double dx, dy, dz;
+                    p_off = orc_p_off(P, R, sqrt(orc_dist2(P, S, i, j, &dx, &dy, &dz)));
+                }
+                if (orc_u53(w[0], w[1]) < p_off) brk[i * ORC_VMAX + s] = 1;
             }
         }
         /* apply: breaks first, then the formed bonds (occupancy updated for the

@@ -35,6 +35,7 @@ typedef struct {
     double r_min, r_max;
     double p_on0, p_off;       /* per-sweep probabilities, Eq. (2) */
     int32_t self_avoid;        /* 1: sites of one molecule (orc_state.mol) do not react with each other */
+    double slip_a;             /* slip bond, Eq. (slip): P_off(r) = p_off exp(a sqrt(U_b(r)/kT)); 0: off */
 } orc_reaction;
 
 typedef struct {

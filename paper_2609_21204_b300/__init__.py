@@ -185,6 +185,16 @@ class Snap:
         self._check(self._lib.snap_set_reaction_rates(self._ctx, int(reaction), int(replica),
                                                       float(p_on0), float(p_off)))
 
+    def set_slip(self, reaction, a):
+        """Slip-bond modifier of one reaction (Eq. slip); a = 0 switches it off."""
+        self._check(self._lib.snap_set_slip(self._ctx, int(reaction), float(a)))
+
+    def set_melting(self, reaction, lam, t_melt, kon_init, koff_init, kon_melt, koff_melt):
+        """Melting switch of one reaction (Eqs. gT-kT) at every replica's kT."""
+        self._check(self._lib.snap_set_melting(self._ctx, int(reaction), float(lam), float(t_melt),
+                                               float(kon_init), float(koff_init), float(kon_melt),
+                                               float(koff_melt)))
+
     # -- state ---------------------------------------------------------------
     def set_particles(self, pos, vel, types):
         p = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
@@ -470,6 +480,11 @@ def from_system(sysdef, precision="mixed", p_on0=1.0, skin=None, **kw) -> Snap:
             for a, r in enumerate(s.reactions):
                 pon, poff = rates_from_eps(r.eps, p_on0, s.dt, s.bond_period)
                 sim.set_reaction_rates(a, ri, pon, poff)
+    for a, r in enumerate(s0.reactions):
+        if getattr(r, "slip_a", 0.0):
+            sim.set_slip(a, r.slip_a)
+        if getattr(r, "melt", None) is not None:
+            sim.set_melting(a, *r.melt)
     pos = np.concatenate([s.pos for s in systems])
     vel = np.concatenate([s.vel for s in systems])
     types = np.concatenate([s.types for s in systems])

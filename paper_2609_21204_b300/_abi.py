@@ -56,6 +56,8 @@ SIGNATURES = {
     "snap_add_reaction": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
                                     C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_int32)]),
     "snap_set_reaction_rates": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_double, C.c_double]),
+    "snap_set_slip": (C.c_int, [_P, C.c_int32, C.c_double]),
+    "snap_set_melting": (C.c_int, [_P, C.c_int32] + [C.c_double] * 6),
     "snap_set_particles": (C.c_int, [_P, _P, _P, _P]),
     "snap_set_positions": (C.c_int, [_P, _P, _P]),
     "snap_set_bonds": (C.c_int, [_P, C.c_int64, _P, _P]),

@@ -23,6 +23,8 @@ struct RxHost {
     int ta, tb, bt;
     double rmin, rmax, pon, poff;
     int self_avoid;
+    double slip_a = 0.0;    // slip-bond modifier, Eq. (slip)
+    bool melting = false;   // rates from the melting switch, Eqs. (gT)-(kT)
 };
 
 struct RepHost {
@@ -241,6 +243,8 @@ void fill_params(snap_ctx *c)
         P.rx_tb[a] = c->rx[a].tb;
         P.rx_bt[a] = c->rx[a].bt;
         P.rx_self[a] = c->rx[a].self_avoid;
+        P.rx_slip[a] = c->rx[a].slip_a;
+        if (c->rx[a].slip_a != 0.0) P.slip_mask |= 1 << a;
         P.rx_rmin2[a] = c->rx[a].rmin * c->rx[a].rmin;
         P.rx_rmax2[a] = c->rx[a].rmax * c->rx[a].rmax;
     }
@@ -1037,6 +1041,58 @@ extern "C" snap_status snap_add_reaction(snap_ctx *c, int32_t ta, int32_t tb, in
     return SNAP_OK;
 }
 
+extern "C" snap_status snap_set_slip(snap_ctx *c, int32_t a, double slip_a)
+{
+    if (!c) return SNAP_ERR_ARG;
+    if (a < 0 || a >= (int)c->rx.size()) return fail(c, SNAP_ERR_ARG, "reaction out of range");
+    if (!(slip_a >= 0.0) || !std::isfinite(slip_a)) return fail(c, SNAP_ERR_ARG, "slip parameter must be finite and >= 0");
+    if (slip_a != 0.0 && c->rx[a].melting)
+        return fail(c, SNAP_ERR_ARG, "the slip bond and the melting switch are mutually exclusive");
+    if (slip_a != 0.0 && c->mh_mode != 0)
+        return fail(c, SNAP_ERR_STATE, "Metropolis-Hastings mode does not support the slip bond");
+    c->rx[a].slip_a = slip_a;
+    c->P.rx_slip[a] = slip_a;
+    if (slip_a != 0.0) c->P.slip_mask |= 1 << a;
+    else c->P.slip_mask &= ~(1 << a);
+    c->graph_dirty = true;
+    return SNAP_OK;
+}
+
+// Eqs. (gT)-(kT) at each replica's set-point temperature, then Eq. (2).
+extern "C" snap_status snap_set_melting(snap_ctx *c, int32_t a, double lambda, double t_melt, double kon_init,
+                                        double koff_init, double kon_melt, double koff_melt)
+{
+    if (!c) return SNAP_ERR_ARG;
+    if (a < 0 || a >= (int)c->rx.size()) return fail(c, SNAP_ERR_ARG, "reaction out of range");
+    if (c->rx[a].slip_a != 0.0)
+        return fail(c, SNAP_ERR_ARG, "the slip bond and the melting switch are mutually exclusive");
+    const double v[6] = {lambda, t_melt, kon_init, koff_init, kon_melt, koff_melt};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(c, SNAP_ERR_ARG, "melting parameters must be finite");
+    if (kon_init < 0.0 || koff_init < 0.0 || kon_melt < 0.0 || koff_melt < 0.0)
+        return fail(c, SNAP_ERR_ARG, "rate constants must be >= 0");
+    const double ndt = (double)c->cfg.bond_period;
+    std::vector<double> pon(c->reps.size()), poff(c->reps.size());
+    for (size_t r = 0; r < c->reps.size(); ++r) {
+        const double g = 0.5 * (std::tanh(lambda * (c->reps[r].kT - t_melt)) + 1.0);
+        const double kon = kon_init * (1.0 - g) + kon_melt * g;
+        const double koff = koff_init * (1.0 - g) + koff_melt * g;
+        pon[r] = kon * ndt * c->cfg.dt;
+        poff[r] = koff * ndt * c->cfg.dt;
+        if (!(pon[r] <= 1.0 && poff[r] <= 1.0))
+            return fail(c, SNAP_ERR_ARG, "a rate times n dt exceeds 1 (Eq. 2): lower the rates or the bond period");
+    }
+    for (size_t r = 0; r < c->reps.size(); ++r) {
+        c->rep_pon[a][r] = pon[r];
+        c->rep_poff[a][r] = poff[r];
+    }
+    c->rx[a].pon = pon[0];
+    c->rx[a].poff = poff[0];
+    c->rx[a].melting = true;
+    if (c->ready) return upload_reps(c);
+    return SNAP_OK;
+}
+
 extern "C" snap_status snap_set_reaction_rates(snap_ctx *c, int32_t a, int32_t r, double pon, double poff)
 {
     if (!c) return SNAP_ERR_ARG;
@@ -1622,6 +1678,8 @@ extern "C" snap_status snap_set_mh(snap_ctx *c, int32_t mode, const snap_mlp *ml
             return fail(c, SNAP_ERR_ARG, "Metropolis-Hastings mode supports one reaction in one system");
         if (c->rx[0].self_avoid)
             return fail(c, SNAP_ERR_ARG, "Metropolis-Hastings mode does not support intramolecular exclusion");
+        if (c->rx[0].slip_a != 0.0)
+            return fail(c, SNAP_ERR_ARG, "Metropolis-Hastings mode does not support the slip bond");
         const double side = 2.0 * c->rx[0].rmax + 0.05;
         int nc[3];
         for (int d = 0; d < 3; ++d) {

@@ -567,10 +567,32 @@ __device__ __forceinline__ void push_pass2(const DevParams &P, DevArrays &A, int
     warp_counts<2>(A.counters, idx, v);
 }
 
+// Slip bond, Eq. (slip): P_off(r) = P_off^0 exp(a sqrt(U_b(r)/kT)), capped at 1.
+// At kT = 0 the factor takes its limits (1 for U_b = 0, infinite for U_b > 0);
+// an exponent of 700 or more caps at once.  Every operation is one IEEE
+// rounding; exp is this library's own (the acceptance factor's).
+__device__ __forceinline__ double slip_p_off(double p0, double k, double r0, double kT, double a, double r)
+{
+    if (p0 == 0.0) return p0;
+    const double dr = __dsub_rn(r, r0);
+    const double U = __dmul_rn(__dmul_rn(__dmul_rn(0.5, k), dr), dr);
+    double x;
+    if (kT > 0.0) x = __ddiv_rn(U, kT);
+    else x = U > 0.0 ? __longlong_as_double(0x7FF0000000000000ll) : 0.0;
+    const double e = __dmul_rn(a, __dsqrt_rn(x));
+    if (!(e < 700.0)) return 1.0;
+    const double p = __dmul_rn(p0, exp_cw(e));
+    return p < 1.0 ? p : 1.0;
+}
+
 // Breaking (Fig. 1d) of particle i's bonds of the reaction in slot `slot`:
 // each bond present when the reaction began, owned by its smaller tag,
 // breaks iff Philox(BREAK; tags) gives u53 < P_off.  Reads the slots as they
 // were before the reaction; writes only the break bits, which k_apply reads.
+// SLIP: the draws of slip reactions (Eq. slip), which run in a kernel of
+// their own (k_break_slip) so that the proposal kernel, which hosts the
+// constant-P_off draws, keeps its registers; each kind skips the other's.
+template <bool SLIP>
 __device__ __forceinline__ void break_particle(const DevParams &P, DevArrays &A, int slot, long long step, long long i,
                                                unsigned long long &tested)
 {
@@ -578,6 +600,7 @@ __device__ __forceinline__ void break_particle(const DevParams &P, DevArrays &A,
     if (dp.x < 0) return;
     const int rp = rep_of(P, A, i);
     const int a = A.rx_order[rp * kMaxRx + slot];
+    if ((((P.slip_mask >> a) & 1) != 0) != SLIP) return;
     const RepDev &R = A.reps[rp];
     const int me = A.tag[i];
     const int drx = A.drx[i];
@@ -589,11 +612,22 @@ __device__ __forceinline__ void break_particle(const DevParams &P, DevArrays &A,
         if (((drx >> (8 * s)) & 0xFF) != a) continue;
         ++tested;
         const U4 w = pair_draw(R, a, kBreak, step, (uint32_t)(me - R.tag_off), (uint32_t)(p - R.tag_off));
-        // u53 < p_off  <=>  m < ceil(p_off 2^53) with m the 53-bit integer of u53
+        // u53 < p_off  <=>  m < ceil(p_off 2^53) with m the 53-bit integer of u53;
+        // with the slip modifier P_off depends on r and m < p_off 2^53 is tested in
+        // FP64 (both sides exact)
         const unsigned long long m = ((unsigned long long)w.x << 21) | (unsigned long long)(w.y >> 11);
-        if (m < R.off_thresh[a]) {
+        const int j = A.rtag[p];
+        bool brk;
+        if (SLIP) {
+            const int bt = P.rx_bt[a];
+            const double pr = slip_p_off(R.p_off[a], P.bk[bt], P.br0[bt], R.kT, P.rx_slip[a],
+                                         __dsqrt_rn(exact_r2(A, R, (int)i, j)));
+            brk = (double)m < __dmul_rn(pr, 0x1p53);
+        } else {
+            brk = m < R.off_thresh[a];
+        }
+        if (brk) {
             atomicOr(&A.brk[i], 1u << s);
-            const int j = A.rtag[p];
             const int4 q = A.dp[j];
             const int qv[4] = {q.x, q.y, q.z, q.w};
             int sj = 0;
@@ -619,7 +653,24 @@ __global__ void __launch_bounds__(256, 4) k_proposals(DevParams P, DevArrays A, 
     if (s >= 0) push_pass1(P, A, slot, step, s);
     else pull_propose<SCREEN>(P, A, slot);
     unsigned long long tested = 0;
-    for (long long i = gtid(); i < P.n; i += (long long)gridDim.x * blockDim.x) break_particle(P, A, slot, step, i, tested);
+    for (long long i = gtid(); i < P.n; i += (long long)gridDim.x * blockDim.x)
+        break_particle<false>(P, A, slot, step, i, tested);
+    const int idx[1] = {cBreakTested};
+    const unsigned long long v[1] = {tested};
+    warp_counts<1>(A.counters, idx, v);
+}
+
+// Breaking draws of slip reactions (launched only when some reaction has the
+// slip modifier), between the proposal kernel and the apply phase that reads
+// the break bits.
+template <bool FORCED>
+__global__ void __launch_bounds__(256) k_break_slip(DevParams P, DevArrays A, int slot)
+{
+    long long step;
+    if (!sweep_active<FORCED>(P, A, step)) return;
+    unsigned long long tested = 0;
+    for (long long i = gtid(); i < P.n; i += (long long)gridDim.x * blockDim.x)
+        break_particle<true>(P, A, slot, step, i, tested);
     const int idx[1] = {cBreakTested};
     const unsigned long long v[1] = {tested};
     warp_counts<1>(A.counters, idx, v);
@@ -761,6 +812,7 @@ void sweep_reaction(const DevParams &P, const DevArrays &A, int slot, Launch L)
     const unsigned gprop = (unsigned)std::min<long long>(g, 8LL * sm_count() * (256 / L.block));
     if (P.screen) k_proposals<FORCED, true><<<gprop, L.block, 0, L.stream>>>(P, A, slot);
     else k_proposals<FORCED, false><<<gprop, L.block, 0, L.stream>>>(P, A, slot);
+    if (P.slip_mask) k_break_slip<FORCED><<<gprop, L.block, 0, L.stream>>>(P, A, slot);
     k_resolve<FORCED><<<std::max<unsigned>(gl, (unsigned)std::min<long long>(grid_for(P.n, 256), 4LL * sm_count())),
                         256, 0, L.stream>>>(P, A, slot);
     k_accept<FORCED><<<gl, 256, 0, L.stream>>>(P, A, slot);

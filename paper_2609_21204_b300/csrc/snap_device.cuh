@@ -48,6 +48,8 @@ struct DevParams {
     // reactions
     int32_t rx_ta[kMaxRx], rx_tb[kMaxRx], rx_bt[kMaxRx];
     int32_t rx_self[kMaxRx];   // 1: sites of one molecule do not react with each other (Sec. II.D)
+    double rx_slip[kMaxRx];    // slip-bond parameter a of Eq. (slip); 0: constant P_off
+    int32_t slip_mask;         // bit a set: reaction a has the slip modifier
     double rx_rmin2[kMaxRx], rx_rmax2[kMaxRx];
     // integrator
     double dt, half_dt, gamma, sqrt3;

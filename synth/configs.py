@@ -30,6 +30,9 @@ class Reaction:
     r_max: float
     eps: float            # bond free energy in kT (the paper's ε = ln K)
     self_avoid: int = 0
+    slip_a: float = 0.0   # slip-bond parameter a of Eq. (slip); 0: constant P_off
+    melt: tuple | None = None   # melting switch, Eqs. (gT)-(kT): (lambda, T_melt, k_on^init,
+                                # k_off^init, k_on^melt, k_off^melt); rates replace eps
 
 
 @dataclass
