@@ -167,7 +167,7 @@ def test_modifier_misuse_is_refused(snapmod):
             sim.set_slip(0, -1.0)
         sim.set_slip(0, 0.0)
         with pytest.raises(snapmod.SnapError):
-            sim.set_melting(0, 8.0, 1.0, 400.0, 4.0, 0.0, 16.0)   # k_on n dt = 2 > 1
+            sim.set_melting(0, 8.0, 1.0, 1000.0, 4.0, 0.0, 16.0)  # at T = T_melt: k_on n dt = 2.5 > 1
         sim.set_melting(0, 8.0, 1.0, 20.0, 4.0, 0.0, 16.0)
         with pytest.raises(snapmod.SnapError):
             sim.set_slip(0, 1.0)
