@@ -173,3 +173,22 @@ def test_modifier_misuse_is_refused(snapmod):
             sim.set_slip(0, 1.0)
     finally:
         sim.close()
+
+
+def test_bond_period_trajectory_follows_oracle(snapmod):
+    # a sweep every n = 5 steps (Eq. 2: P = k n dt per sweep); FP64 step for step
+    s = assoc_ab(seed=16)
+    s.bond_period = 5
+    sim = snapmod.from_system(s, precision="fp64")
+    orc = oracle.OracleSystem(s)
+    try:
+        for _ in range(6):
+            sim.step(17)
+            orc.run(17)
+            d = sim.positions() - orc.pos
+            d -= s.box * np.rint(d / s.box)
+            assert np.abs(d).max() < 1e-9
+            assert np.array_equal(sim.bonds(), orc.bonds())
+        assert sim.stats()["sweeps"] == len(range(0, 6 * 17, 5))
+    finally:
+        sim.close()

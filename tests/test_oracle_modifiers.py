@@ -134,3 +134,20 @@ def test_melting_switch_bonded_fraction(oracle_mod, dT):
         assert expect < 2e-3                         # melted: binding switched off
     se = _two_state_se(expect, pon, poff, n_pairs, T) + 1e-4
     assert abs(frac - expect) < 4.5 * se, (frac, expect, se)
+
+
+def test_bond_period_sweeps_only_every_n_steps(oracle_mod):
+    # Eq. 2 with n > 1: the updater acts on steps that are multiples of n only
+    from synth import assoc_ab
+    s = assoc_ab(seed=16)
+    s.bond_period = 5
+    o = oracle_mod.OracleSystem(s)
+    prev = o.bonds()
+    changed_at = []
+    for t in range(60):
+        o.run(1)
+        b = o.bonds()
+        if not np.array_equal(b, prev):
+            changed_at.append(t)
+        prev = b
+    assert changed_at and all(t % 5 == 0 for t in changed_at), changed_at
