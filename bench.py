@@ -198,6 +198,45 @@ def md_traffic_from_profile(n):
     return per_particle * n
 
 
+# ----------------------------------------------------------------- ranks
+class RankGroup:
+    """What the ranks of one bench run share: a barrier and the max / sum of a
+    number over ranks (NCCL tensors on the GPU, gloo on the host).  With one
+    rank every call is the identity.  The snap arm shards whole replicas: each
+    rank runs its own system (rank_seed) and no data crosses ranks."""
+
+    def __init__(self, dist, world, device):
+        self.dist, self.world, self.device = dist, world, device
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def _reduce(self, x, op):
+        if self.world == 1:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max_all(self, x):
+        return self._reduce(x, self.dist.ReduceOp.MAX)
+
+    def sum_all(self, x):
+        return self._reduce(x, self.dist.ReduceOp.SUM)
+
+    def throughput(self, n_local, steps, seconds_local):
+        """Whole-job particle-steps per second: every rank's particles over the
+        slowest rank's time."""
+        return self.sum_all(float(n_local)) * steps / self.max_all(seconds_local)
+
+
+def rank_seed(base, rank):
+    """Seed of the system a rank runs (replica r uses seed + r)."""
+    return base + rank
+
+
 # ----------------------------------------------------------------- snap arm
 def run_snap(args):
     # the batched leg's inputs are generated first, in a spawned pool, before any GPU call
@@ -214,23 +253,8 @@ def run_snap(args):
     torch.cuda.set_device(local)
     dev_index = torch.cuda.current_device()
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_all(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_all(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    group = RankGroup(dist, world, "cuda")
+    barrier, max_all, sum_all = group.barrier, group.max_all, group.sum_all
 
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -325,7 +349,7 @@ def _run_learned(args, torch, snap, rank, stream):
     plain method's formation events, train the BF16 network on the device,
     then run Langevin dynamics with Metropolis-Hastings bond moves under the
     uniform and the learned proposal from the same state."""
-    s = build_system(args, 20260921 + 7 + rank, rho=0.8)
+    s = build_system(args, rank_seed(20260921 + 7, rank), rho=0.8)
     sim = snap.from_system(s, precision="mixed", block_size=args.block)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -420,7 +444,7 @@ def _run_learned(args, torch, snap, rank, stream):
 
 def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier, max_all, sum_all,
                         stream, batch=None):
-    s = build_system(args, 20260921 + rank)
+    s = build_system(args, rank_seed(20260921, rank))
     n = s.n
     K, W = args.steps, args.warmup
     if args.block or args.skin:
