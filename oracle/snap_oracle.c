@@ -583,8 +583,8 @@ int orc_sweep(const orc_params *P, orc_state *S, int64_t step, orc_sweep_stats *
 
 /* ------------------------------------------------------- MH sweep */
 /*
- * Metropolis–Hastings bond moves (an extension beyond the paper, used to
- * judge a learned proposal).  Move set: an initiator i, drawn uniformly among
+ * Metropolis–Hastings bond moves (an extension beyond the paper, the baseline
+ * a learned proposal is measured against).  Move set: an initiator i, drawn uniformly among
  * the reactive particles of an active checkerboard cell, either forms a bond
  * with one of its owned candidates j (free, compatible, unbonded, inside
  * [r_min, r_max]) chosen with probability q(j | i) — here uniform — or breaks

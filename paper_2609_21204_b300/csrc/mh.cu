@@ -1,5 +1,5 @@
 // Metropolis–Hastings bond moves and bond-event logging (an extension beyond
-// the paper: the learned proposal and the uniform proposal that judges it).
+// the paper: the learned proposal and the uniform proposal it is measured against).
 //
 // Move set (one reaction, one system): checkerboard cells of side
 // >= 2 r_max + 0.05, an even number per axis, colour = parities of the cell
