@@ -232,6 +232,19 @@ class RankGroup:
         return self.sum_all(float(n_local)) * steps / self.max_all(seconds_local)
 
 
+def run_leg(out, key, world, fn):
+    """Run one secondary leg of the benchmark into out[key].  With one rank a
+    leg that raises is recorded as {"error": ...} so that the headline line
+    still prints; with several ranks the error propagates (a rank that skipped
+    the rest of a leg would leave the others waiting in a collective)."""
+    try:
+        out[key] = fn()
+    except Exception as e:   # noqa: BLE001 - recorded in the JSON line, not hidden
+        if world > 1:
+            raise
+        out[key] = {"error": f"{type(e).__name__}: {e}"}
+
+
 def rank_seed(base, rank):
     """Seed of the system a rank runs (replica r uses seed + r)."""
     return base + rank
@@ -532,37 +545,45 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
     }
     if not args.no_fp64:
         sim.close()
-        sim64 = make("fp64")
-        sim64.step(W)
-        barrier()
-        torch.cuda.synchronize()
-        K64 = args.fp64_steps
-        e0.record(stream)
-        sim64.step(K64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t64 = max_all(e0.elapsed_time(e1) / 1e3)
-        v64 = n_all * K64 / t64
-        ph64 = sim64.step_profiled(max(5, args.profile_steps // 5))
-        out["fp64_plain"] = {"value": v64, "ms_per_step": t64 * 1e3 / K64, "steps": K64,
-                             "phases_ms_per_step": {k: round(v, 5) for k, v in ph64.items()}}
-        out["speedup_mixed_vs_fp64_plain"] = value / v64
-        sim64.close()
+
+        def fp64_leg():
+            sim64 = make("fp64")
+            try:
+                sim64.step(W)
+                barrier()
+                torch.cuda.synchronize()
+                K64 = args.fp64_steps
+                e0.record(stream)
+                sim64.step(K64)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t64 = max_all(e0.elapsed_time(e1) / 1e3)
+                v64 = n_all * K64 / t64
+                ph64 = sim64.step_profiled(max(5, args.profile_steps // 5))
+            finally:
+                sim64.close()
+            out["speedup_mixed_vs_fp64_plain"] = value / v64
+            return {"value": v64, "ms_per_step": t64 * 1e3 / K64, "steps": K64,
+                    "phases_ms_per_step": {k: round(v, 5) for k, v in ph64.items()}}
+
+        run_leg(out, "fp64_plain", world, fp64_leg)
         sim = make("mixed")
         sim.step(W)
     if batch is not None:
         sim.close()
-        out["batched"] = _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream)
+        run_leg(out, "batched", world,
+                lambda: _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream))
         sim = make("mixed")
         sim.step(W)
     if args.competing_n > 0:
         sim.close()
-        out["competing"] = _run_competing(args, torch, snap, barrier, max_all, sum_all, stream)
+        run_leg(out, "competing", world,
+                lambda: _run_competing(args, torch, snap, barrier, max_all, sum_all, stream))
         sim = make("mixed")
         sim.step(W)
     if args.learned_events > 0:
         sim.close()
-        out["learned"] = _run_learned(args, torch, snap, rank, stream)
+        run_leg(out, "learned", world, lambda: _run_learned(args, torch, snap, rank, stream))
         sim = make("mixed")
         sim.step(W)
     if not args.no_e2e:

@@ -82,3 +82,18 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
     # a non-zero rank returns before touching its arguments or the oracle
     assert bench.run_reference(None) is None
+
+
+def test_secondary_leg_failure_is_recorded_at_one_rank_and_raised_at_several():
+    import bench
+
+    def boom():
+        raise RuntimeError("leg failed")
+
+    out = {}
+    bench.run_leg(out, "leg", 1, boom)
+    assert out == {"leg": {"error": "RuntimeError: leg failed"}}
+    bench.run_leg(out, "ok", 1, lambda: {"value": 1.0})
+    assert out["ok"] == {"value": 1.0}
+    with pytest.raises(RuntimeError):
+        bench.run_leg({}, "leg", 2, boom)
