@@ -111,3 +111,18 @@ def test_rings_form_only_without_exclusion(oracle_mod):
         counts[sa] = (rings, joins)
     assert counts[0][0] > 100 and counts[0][1] > 100, counts
     assert counts[1][0] == 0 and counts[1][1] > 100, counts
+
+
+@pytest.mark.parametrize("self_avoid", [1, 0])
+def test_mh_moves_respect_the_exclusion(oracle_mod, self_avoid):
+    # the oracle's Metropolis-Hastings move set filters candidates the same way
+    s = frozen_loops(seed=7, n_units=64, self_avoid=self_avoid, eps=1.0)
+    o = oracle_mod.OracleSystem(s, p_on0=1.0)
+    intra = ctrl = 0
+    for t in range(3000):
+        o.mh_sweep(step=t)
+        b = o.bonds()
+        intra += int(((b[:, 0] % 5 == 0) & (b[:, 1] == b[:, 0] + 2)).sum())
+        ctrl += int(((b[:, 0] % 5 == 3) & (b[:, 1] == b[:, 0] + 1)).sum())
+    assert ctrl > 0
+    assert (intra == 0) == bool(self_avoid), (intra, ctrl)
