@@ -104,6 +104,8 @@ def lib():
         _lib.orc_u53.restype = C.c_double
         _lib.orc_exp.argtypes = [C.c_double]
         _lib.orc_exp.restype = C.c_double
+        _lib.orc_log.argtypes = [C.c_double]
+        _lib.orc_log.restype = C.c_double
         _lib.orc_bond_energy.argtypes = [C.POINTER(Params), C.c_int32, C.c_double]
         _lib.orc_bond_energy.restype = C.c_double
         _lib.orc_sweep.argtypes = [C.POINTER(Params), C.POINTER(State), C.c_int64,
@@ -139,6 +141,10 @@ def u53(w0, w1):
 
 def exp(x: float) -> float:
     return lib().orc_exp(float(x))
+
+
+def log(x: float) -> float:
+    return lib().orc_log(float(x))
 
 
 def rates_from_eps(eps: float, p_on0: float = 1.0):

@@ -149,6 +149,54 @@ double orc_exp(double x)
     return (p * orc_pow2i(k1)) * orc_pow2i(k2);
 }
 
+/* Natural logarithm for the FENE bond energy of Eq. (3), this file's own so
+ * that the CUDA path, which follows the same published recipe, decides alike:
+ * x = m 2^e with m in [sqrt(1/2), sqrt(2)), s = (m - 1)/(m + 1) and
+ * ln m = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + ...), the series kept to s^27
+ * (|s| <= 0.172, so the next term is below 1e-21 of the result);
+ * ln x = e ln2 + ln m with ln2 split in two words.  Positive normal and
+ * subnormal x; 0 -> -inf, negative or NaN -> NaN, +inf -> +inf. */
+double orc_log(double x)
+{
+    if (x != x || x < 0.0) return NAN;
+    if (x == 0.0) return -INFINITY;
+    if (x == INFINITY) return INFINITY;
+    int e = 0;
+    if (x < 0x1.0p-1022) {                    /* subnormal: scale into the normal range */
+        x *= 0x1.0p54;
+        e = -54;
+    }
+    uint64_t b;
+    memcpy(&b, &x, sizeof b);
+    e += (int)((b >> 52) & 0x7FF) - 1023;
+    b = (b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;   /* m in [1, 2) */
+    double m;
+    memcpy(&m, &b, sizeof m);
+    if (m > 0x1.6a09e667f3bcdp+0) {           /* sqrt(2): halve m, exactly */
+        m *= 0.5;
+        e += 1;
+    }
+    double s = (m - 1.0) / (m + 1.0);
+    double z = s * s;
+    double q = 1.0 / 27.0;
+    q = fma(q, z, 1.0 / 25.0);
+    q = fma(q, z, 1.0 / 23.0);
+    q = fma(q, z, 1.0 / 21.0);
+    q = fma(q, z, 1.0 / 19.0);
+    q = fma(q, z, 1.0 / 17.0);
+    q = fma(q, z, 1.0 / 15.0);
+    q = fma(q, z, 1.0 / 13.0);
+    q = fma(q, z, 1.0 / 11.0);
+    q = fma(q, z, 1.0 / 9.0);
+    q = fma(q, z, 1.0 / 7.0);
+    q = fma(q, z, 1.0 / 5.0);
+    q = fma(q, z, 1.0 / 3.0);
+    double t = 2.0 * s;
+    double lm = fma(t, z * q, t);
+    double de = (double)e;
+    return fma(de, ORC_LN2_HI, fma(de, ORC_LN2_LO, lm));
+}
+
 /* ------------------------------------------------------- bond energies */
 
 double orc_bond_energy(const orc_params *P, int32_t bt, double r)
@@ -164,11 +212,31 @@ double orc_bond_energy(const orc_params *P, int32_t bt, double r)
     return -0.5 * k * r0 * r0 * log(1.0 - q);
 }
 
+/* U_b of a dynamic bond for Eq. (3): harmonic 1/2 k (r - r0)^2, or FENE
+ * -1/2 k R0^2 ln(1 - (r/R0)^2) with this file's logarithm (+inf at r >= R0). */
+static double orc_dyn_energy(const orc_params *P, int32_t bt, double r)
+{
+    double k = P->bk[bt], r0 = P->br0[bt];
+    if (P->bkind[bt] == ORC_HARMONIC) {
+        double dr = r - r0;
+        return 0.5 * k * dr * dr;
+    }
+    double q = (r * r) / (r0 * r0);
+    if (!(q < 1.0)) return INFINITY;
+    return -0.5 * k * r0 * r0 * orc_log(1.0 - q);
+}
+
+/* The separation a proposal aims at (Sec. II.C: |r - r0| is minimised): the
+ * rest length of a harmonic bond; 0, the minimum of the FENE term, for FENE. */
+static double orc_rest_length(const orc_params *P, int32_t bt)
+{
+    return P->bkind[bt] == ORC_HARMONIC ? P->br0[bt] : 0.0;
+}
+
 /* Eq. (3): P_on(r) = P_on^0 exp(-U_b(r)/kT); at kT = 0 the factor is [U_b <= 0]. */
 static double orc_p_on(const orc_params *P, const orc_reaction *R, double r)
 {
-    double dr = r - P->br0[R->bond_type];
-    double U = 0.5 * P->bk[R->bond_type] * dr * dr;
+    double U = orc_dyn_energy(P, R->bond_type, r);
     if (P->kT > 0.0) {
         double a = U / P->kT;
         return R->p_on0 * orc_exp(-a);
@@ -183,8 +251,7 @@ static double orc_p_on(const orc_params *P, const orc_reaction *R, double r)
 static double orc_p_off(const orc_params *P, const orc_reaction *R, double r)
 {
     if (R->slip_a == 0.0 || R->p_off == 0.0) return R->p_off;
-    double dr = r - P->br0[R->bond_type];
-    double U = 0.5 * P->bk[R->bond_type] * dr * dr;
+    double U = orc_dyn_energy(P, R->bond_type, r);
     double x;
     if (P->kT > 0.0) x = U / P->kT;
     else x = (U > 0.0) ? INFINITY : 0.0;
@@ -406,7 +473,7 @@ int32_t orc_candidates(const orc_params *P, const orc_state *S, int32_t a, int64
     c.P = P; c.S = S; c.R = R; c.i = i;
     c.rmin2 = R->r_min * R->r_min;
     c.rmax2 = R->r_max * R->r_max;
-    c.r0 = P->br0[R->bond_type];
+    c.r0 = orc_rest_length(P, R->bond_type);
     c.best = -1;
     c.list = out; c.cap = cap;
     int32_t ti = S->type[i];
@@ -453,7 +520,7 @@ int orc_sweep(const orc_params *P, orc_state *S, int64_t step, orc_sweep_stats *
         int32_t a = order[slot];
         const orc_reaction *R = &P->rx[a];
         double rmin2 = R->r_min * R->r_min, rmax2 = R->r_max * R->r_max;
-        double r0 = P->br0[R->bond_type];
+        double r0 = orc_rest_length(P, R->bond_type);
 
         /* (a) proposal — occupancies as they stand when the reaction begins */
         for (int64_t i = 0; i < n; ++i) {
@@ -609,8 +676,7 @@ static int orc_owner_is(const orc_params *P, int64_t i, int64_t j)
 
 static double orc_factor(const orc_params *P, const orc_reaction *R, double r)
 {
-    double dr = r - P->br0[R->bond_type];
-    double U = 0.5 * P->bk[R->bond_type] * dr * dr;
+    double U = orc_dyn_energy(P, R->bond_type, r);
     if (P->kT > 0.0) {
         double a = U / P->kT;
         return orc_exp(-a);

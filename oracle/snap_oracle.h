@@ -102,6 +102,7 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 double orc_u53(uint32_t w0, uint32_t w1);
 /* exp(x) by Cody–Waite ln2 reduction and a degree-13 Taylor polynomial. */
 double orc_exp(double x);
+double orc_log(double x);
 /* Bond energy U_b(r) of bond type bt. */
 double orc_bond_energy(const orc_params *P, int32_t bt, double r);
 

@@ -83,3 +83,25 @@ def test_exp_subnormal_range(oracle_mod):
         got = oracle_mod.exp(x)
         # subnormal results carry fewer bits: allow 2 units of the smallest subnormal
         assert abs(got - ref) <= max(2 * math.ulp(ref), 2 * 5e-324)
+
+
+def test_log_against_libm(oracle_mod):
+    # the oracle's own logarithm (used for the FENE bond energy of Eq. 3)
+    rng = np.random.default_rng(11)
+    xs = np.concatenate([np.geomspace(1e-320, 1e308, 4000), rng.uniform(0.5, 2.0, 20000),
+                         1.0 - np.geomspace(1e-16, 0.999, 4000), [0.5, 2.0, math.sqrt(2.0), 1.0]])
+    worst = 0.0
+    for x in xs:
+        ref = math.log(x)
+        got = oracle_mod.log(x)
+        if ref == 0.0:
+            assert got == 0.0
+            continue
+        worst = max(worst, abs(got - ref) / math.ulp(ref))
+    assert worst <= 2.0, worst
+    assert oracle_mod.log(1.0) == 0.0
+    assert oracle_mod.log(0.0) == -math.inf and oracle_mod.log(math.inf) == math.inf
+    assert math.isnan(oracle_mod.log(-1.0)) and math.isnan(oracle_mod.log(float("nan")))
+    # exp and log of this library invert each other to a few ulp
+    for x in rng.uniform(-30, 30, 2000):
+        assert abs(oracle_mod.log(oracle_mod.exp(x)) - x) <= 4 * math.ulp(max(abs(x), 1e-300)) + 1e-15
