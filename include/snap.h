@@ -156,8 +156,13 @@ snap_status snap_add_static_bonds(snap_ctx *, int64_t nb, const int32_t *tag_pai
                                   int32_t bt);
 
 /* Register a reaction between particle types type_a and type_b forming bonds
- * of harmonic bond type bt when r_min <= r <= r_max, with per-sweep
- * probabilities p_on0 and p_off (Eqs. 1-3; K = p_on0/p_off).  self_avoid = 1
+ * of bond type bt (set before; any kind) when r_min <= r <= r_max, with
+ * per-sweep probabilities p_on0 and p_off (Eqs. 1-3; K = p_on0/p_off).  The
+ * Metropolis factor of Eq. 3 uses that bond type's energy (FENE: evaluated
+ * with the library's own logarithm, +inf at r >= R0), and a proposal keeps
+ * the partner closest to the bond term's minimum: r0 for a harmonic bond, 0
+ * for FENE (Sec. II.B-C).  The slip bond and the Metropolis–Hastings move set
+ * need a harmonic bond type.  self_avoid = 1
  * excludes intramolecular bonds (Sec. II.D): two sites of one molecule — a
  * connected component of the static bonds, traced by the library when the
  * first step runs and again whenever static bonds are added — are never

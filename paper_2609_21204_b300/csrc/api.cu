@@ -244,6 +244,8 @@ void fill_params(snap_ctx *c)
         P.rx_bt[a] = c->rx[a].bt;
         P.rx_self[a] = c->rx[a].self_avoid;
         P.rx_slip[a] = c->rx[a].slip_a;
+        // proposals aim at the minimum of the bond term: r0 (harmonic), 0 (FENE)
+        P.rx_r0[a] = c->bkind[c->rx[a].bt] == SNAP_HARMONIC ? c->br0[c->rx[a].bt] : 0.0;
         if (c->rx[a].slip_a != 0.0) P.slip_mask |= 1 << a;
         P.rx_rmin2[a] = c->rx[a].rmin * c->rx[a].rmin;
         P.rx_rmax2[a] = c->rx[a].rmax * c->rx[a].rmax;
@@ -976,7 +978,8 @@ extern "C" snap_status snap_set_bond_params(snap_ctx *c, int32_t bt, int32_t kin
     if (!(k >= 0.0) || !(r0 > 0.0) || !std::isfinite(k) || !std::isfinite(r0))
         return fail(c, SNAP_ERR_ARG, "bond parameters must be finite, k >= 0, r0 > 0");
     for (const auto &r : c->rx)
-        if (r.bt == bt && kind != SNAP_HARMONIC) return fail(c, SNAP_ERR_ARG, "reaction bond types must be harmonic");
+        if (r.bt == bt && kind != SNAP_HARMONIC && (r.slip_a != 0.0 || c->mh_mode != 0))
+            return fail(c, SNAP_ERR_ARG, "the slip bond and Metropolis-Hastings moves need a harmonic bond type");
     c->bkind[bt] = kind;
     c->bk[bt] = k;
     c->br0[bt] = r0;
@@ -1028,8 +1031,8 @@ extern "C" snap_status snap_add_reaction(snap_ctx *c, int32_t ta, int32_t tb, in
     if (c->ready) return fail(c, SNAP_ERR_STATE, "reactions must be registered before the first step");
     if ((int)c->rx.size() >= kMaxRx) return fail(c, SNAP_ERR_ARG, "too many reactions");
     if (ta < 0 || tb < 0 || ta >= c->ntypes || tb >= c->ntypes) return fail(c, SNAP_ERR_ARG, "reaction type out of range");
-    if (bt < 0 || bt >= kMaxBondTypes || !c->bset[bt] || c->bkind[bt] != SNAP_HARMONIC)
-        return fail(c, SNAP_ERR_ARG, "reaction bond type must be a harmonic bond type that has been set");
+    if (bt < 0 || bt >= kMaxBondTypes || !c->bset[bt])
+        return fail(c, SNAP_ERR_ARG, "reaction bond type must be a bond type that has been set");
     if (!(rmin >= 0.0) || !(rmax > rmin) || !std::isfinite(rmax)) return fail(c, SNAP_ERR_ARG, "bad formation window");
     if (!(pon >= 0.0 && pon <= 1.0) || !(poff >= 0.0 && poff <= 1.0))
         return fail(c, SNAP_ERR_ARG, "per-sweep probabilities must lie in [0, 1] (Eq. 2)");
@@ -1048,6 +1051,8 @@ extern "C" snap_status snap_set_slip(snap_ctx *c, int32_t a, double slip_a)
     if (!(slip_a >= 0.0) || !std::isfinite(slip_a)) return fail(c, SNAP_ERR_ARG, "slip parameter must be finite and >= 0");
     if (slip_a != 0.0 && c->rx[a].melting)
         return fail(c, SNAP_ERR_ARG, "the slip bond and the melting switch are mutually exclusive");
+    if (slip_a != 0.0 && c->bkind[c->rx[a].bt] != SNAP_HARMONIC)
+        return fail(c, SNAP_ERR_ARG, "the slip bond needs a harmonic bond type");
     if (slip_a != 0.0 && c->mh_mode != 0)
         return fail(c, SNAP_ERR_STATE, "Metropolis-Hastings mode does not support the slip bond");
     c->rx[a].slip_a = slip_a;
@@ -1680,6 +1685,8 @@ extern "C" snap_status snap_set_mh(snap_ctx *c, int32_t mode, const snap_mlp *ml
             return fail(c, SNAP_ERR_ARG, "Metropolis-Hastings mode does not support intramolecular exclusion");
         if (c->rx[0].slip_a != 0.0)
             return fail(c, SNAP_ERR_ARG, "Metropolis-Hastings mode does not support the slip bond");
+        if (c->bkind[c->rx[0].bt] != SNAP_HARMONIC)
+            return fail(c, SNAP_ERR_ARG, "Metropolis-Hastings mode needs a harmonic bond type");
         const double side = 2.0 * c->rx[0].rmax + 0.05;
         int nc[3];
         for (int d = 0; d < 3; ++d) {

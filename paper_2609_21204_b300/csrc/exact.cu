@@ -262,7 +262,7 @@ __device__ __forceinline__ void pull_propose(const DevParams &P, DevArrays &A, i
                 const float4 *pos4 = reinterpret_cast<const float4 *>(A.pos4);
                 const float4 pi4 = pos4[i];
                 const float rmin2f = (float)P.rx_rmin2[a], rmax2f = (float)P.rx_rmax2[a];
-                const float r0f = (float)P.br0[P.rx_bt[a]];
+                const float r0f = (float)P.rx_r0[a];
                 float min_upper = 3.0e38f;
                 unsigned long long sure_in = 0;
                 for (int k = 0; k < nn; ++k) {
@@ -293,7 +293,7 @@ __device__ __forceinline__ void pull_propose(const DevParams &P, DevArrays &A, i
                 want = ncont > 0;
             } else {
                 const double rmin2 = P.rx_rmin2[a], rmax2 = P.rx_rmax2[a];
-                const double r0 = P.br0[P.rx_bt[a]];
+                const double r0 = P.rx_r0[a];
                 int best_tag = 0;
                 double best_r = 0.0;
                 for (int k = 0; k < nn; ++k) {
@@ -354,7 +354,7 @@ __device__ __forceinline__ void pull_exact(const DevParams &P, DevArrays &A, int
             continue;
         }
         const double rmin2 = P.rx_rmin2[a], rmax2 = P.rx_rmax2[a];
-        const double r0 = P.br0[P.rx_bt[a]];
+        const double r0 = P.rx_r0[a];
         int best = -1, best_tag = 0;
         double best_d = 0.0, best_r = 0.0;
         if (nc <= kContenders) {
@@ -456,7 +456,7 @@ __device__ __forceinline__ void push_pass1(const DevParams &P, DevArrays &A, int
     const int ta = P.rx_ta[a], tb = P.rx_tb[a];
     const RepDev &R = A.reps[0];
     const double rmin2 = P.rx_rmin2[a], rmax2 = P.rx_rmax2[a];
-    const double r0 = P.br0[P.rx_bt[a]];
+    const double r0 = P.rx_r0[a];
     const long long stride = P.nbr_stride;
     const int lane = threadIdx.x & 31;
     unsigned long long scanned = 0, inwin = 0, nscan = 0, nprop = 0;
@@ -527,7 +527,7 @@ __device__ __forceinline__ void push_pass2(const DevParams &P, DevArrays &A, int
     const int ta = P.rx_ta[a], tb = P.rx_tb[a];
     const RepDev &R = A.reps[0];
     const double rmin2 = P.rx_rmin2[a], rmax2 = P.rx_rmax2[a];
-    const double r0 = P.br0[P.rx_bt[a]];
+    const double r0 = P.rx_r0[a];
     const long long stride = P.nbr_stride;
     const int lane = threadIdx.x & 31;
     const int ns = A.avail_count[s];
@@ -686,6 +686,19 @@ __global__ void __launch_bounds__(256) k_resolve(DevParams P, DevArrays A, int s
     else pull_exact(P, A, slot, step);
 }
 
+// U_b of a proposed dynamic bond from d = |r - r0| (Eq. 3): harmonic
+// k d^2 / 2 (the sign of r - r0 cancels exactly); FENE, whose proposals aim
+// at r0 = 0 so that d = r, -k R0^2 ln(1 - (r/R0)^2) / 2 with this library's
+// logarithm, +inf at r >= R0.
+__device__ __forceinline__ double dyn_bond_u(const DevParams &P, int bt, double d)
+{
+    if (P.bkind[bt] == 0) return __dmul_rn(__dmul_rn(__dmul_rn(0.5, P.bk[bt]), d), d);
+    const double R0 = P.br0[bt];
+    const double q = __ddiv_rn(__dmul_rn(d, d), __dmul_rn(R0, R0));
+    if (!(q < 1.0)) return __longlong_as_double(0x7FF0000000000000ll);
+    return __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(-0.5, P.bk[bt]), R0), R0), log_cw(__dsub_rn(1.0, q)));
+}
+
 // Acceptance (Eq. 3) of the surviving edges: in scan mode one thread per
 // listed site, in push mode one per pushing site.
 template <bool FORCED>
@@ -715,10 +728,9 @@ __global__ void k_accept(DevParams P, DevArrays A, int slot)
                     const uint32_t lo = tc < tj ? tc : tj, hi = tc < tj ? tj : tc;
                     const U4 w = pair_draw(R, a, kForm, step, lo, hi);
                     const double u = u53(w.x, w.y);
-                    const int bt = P.rx_bt[a];
-                    // U = k (r - r0)^2 / 2 from d = |r - r0| of whichever end proposed the edge
+                    // U_b from d = |r - r0| of whichever end proposed the edge
                     const double d = A.prop[c] == j ? A.prop_d[c] : A.prop_d[j];
-                    const double U = __dmul_rn(__dmul_rn(__dmul_rn(0.5, P.bk[bt]), d), d);
+                    const double U = dyn_bond_u(P, P.rx_bt[a], d);
                     double pon;
                     if (R.kT > 0.0) pon = __dmul_rn(R.p_on0[a], exp_cw(-__ddiv_rn(U, R.kT)));
                     else pon = (U <= 0.0) ? R.p_on0[a] : 0.0;
@@ -749,10 +761,7 @@ __global__ void k_accept(DevParams P, DevArrays A, int slot)
                     const uint32_t lo = ti < tj ? ti : tj, hi = ti < tj ? tj : ti;
                     const U4 w = pair_draw(R, a, kForm, step, lo, hi);
                     const double u = u53(w.x, w.y);
-                    const int bt = P.rx_bt[a];
-                    // U = k (r - r0)^2 / 2 from d = |r - r0| (the sign of r - r0 cancels exactly)
-                    const double d = A.prop_d[i];
-                    const double U = __dmul_rn(__dmul_rn(__dmul_rn(0.5, P.bk[bt]), d), d);
+                    const double U = dyn_bond_u(P, P.rx_bt[a], A.prop_d[i]);
                     double pon;
                     if (R.kT > 0.0) {
                         const double e = __ddiv_rn(U, R.kT);

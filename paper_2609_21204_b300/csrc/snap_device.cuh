@@ -42,13 +42,14 @@ struct DevParams {
     double rc2d[kMaxTypes * kMaxTypes];
     double sig2d[kMaxTypes * kMaxTypes], eps24d[kMaxTypes * kMaxTypes], shiftd[kMaxTypes * kMaxTypes];
     // bond types
-    int32_t bkind[kMaxBondTypes];
+    int32_t bkind[kMaxBondTypes];   // 0: harmonic, 1: FENE (the C ABI's bond kinds)
     double bk[kMaxBondTypes], br0[kMaxBondTypes];
     float bkf[kMaxBondTypes], br0f[kMaxBondTypes];
     // reactions
     int32_t rx_ta[kMaxRx], rx_tb[kMaxRx], rx_bt[kMaxRx];
     int32_t rx_self[kMaxRx];   // 1: sites of one molecule do not react with each other (Sec. II.D)
     double rx_slip[kMaxRx];    // slip-bond parameter a of Eq. (slip); 0: constant P_off
+    double rx_r0[kMaxRx];      // separation a proposal aims at: harmonic r0; 0 for FENE
     int32_t slip_mask;         // bit a set: reaction a has the slip modifier
     double rx_rmin2[kMaxRx], rx_rmax2[kMaxRx];
     // integrator
@@ -235,6 +236,47 @@ __device__ __forceinline__ double exp_cw(double x)
     const int ki = (int)k;
     const int h = ki / 2;
     return __dmul_rn(__dmul_rn(s, pow2_exact(h)), pow2_exact(ki - h));
+}
+
+// ------------------------------------------------------------ log
+// ln(x) for the FENE bond energy of Eq. (3): x = m 2^e with m in
+// [sqrt(1/2), sqrt(2)), s = (m - 1)/(m + 1) and ln m = 2 atanh(s) summed as
+// 2 (s + s^3/3 + ... + s^27/27) in Horner form with fused multiply-adds
+// (|s| <= 0.172: the first dropped term is below 1e-21 of the result);
+// ln x = e ln2 + ln m with ln2 split as for exp_cw.  Written from the
+// mathematics with correctly rounded IEEE operations, so it is reproducible
+// on any IEEE platform.  Domain: positive normal x (the caller passes
+// 1 - (r/R0)^2 >= 2^-53).
+__device__ __forceinline__ double log_cw(double x)
+{
+    const long long b = __double_as_longlong(x);
+    int e = (int)((b >> 52) & 0x7FF) - 1023;
+    double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);   // [1, 2)
+    if (m > 0x1.6a09e667f3bcdp+0) {          // sqrt(2): halve m, exactly
+        m = __dmul_rn(m, 0.5);
+        e += 1;
+    }
+    const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    const double z = __dmul_rn(s, s);
+    double q = 1.0 / 27.0;
+    q = fma(q, z, 1.0 / 25.0);
+    q = fma(q, z, 1.0 / 23.0);
+    q = fma(q, z, 1.0 / 21.0);
+    q = fma(q, z, 1.0 / 19.0);
+    q = fma(q, z, 1.0 / 17.0);
+    q = fma(q, z, 1.0 / 15.0);
+    q = fma(q, z, 1.0 / 13.0);
+    q = fma(q, z, 1.0 / 11.0);
+    q = fma(q, z, 1.0 / 9.0);
+    q = fma(q, z, 1.0 / 7.0);
+    q = fma(q, z, 1.0 / 5.0);
+    q = fma(q, z, 1.0 / 3.0);
+    const double t = __dmul_rn(2.0, s);
+    const double lm = fma(t, __dmul_rn(z, q), t);
+    const double de = (double)e;
+    const double ln2_a = 0x1.62e42fefa39efp-1;
+    const double ln2_b = 0x1.abc9e3b39803fp-56;
+    return fma(de, ln2_a, fma(de, ln2_b, lm));
 }
 
 // ------------------------------------------------------------ geometry

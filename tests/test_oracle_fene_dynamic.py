@@ -19,7 +19,7 @@ import pytest
 from synth import frozen_pairs, random_frozen, BondType, FENE
 
 
-def _fene(s, k=30.0, R0=1.5):
+def _fene(s, k=3.0, R0=1.5):
     s.bond_types = [BondType(FENE, k, R0)]
     return s
 
@@ -31,7 +31,7 @@ def _two_state_se(p, a, b, m, T):
 
 @pytest.mark.parametrize("r,kT", [(0.97, 1.0), (1.2, 1.0), (1.2, 2.0)])
 def test_fene_two_state_fraction(oracle_mod, r, kT):
-    k, R0, eps, n_pairs, T = 30.0, 1.5, 3.0, 200, 3000
+    k, R0, eps, n_pairs, T = 3.0, 1.5, 3.0, 200, 3000
     s = _fene(frozen_pairs(seed=5, n_pairs=n_pairs, r=r, eps=eps, r_max=1.4, kT=kT), k, R0)
     o = oracle_mod.OracleSystem(s, p_on0=1.0)
     p_on = (1.0 - (r / R0) ** 2) ** (k * R0 * R0 / (2.0 * kT))
@@ -44,11 +44,12 @@ def test_fene_two_state_fraction(oracle_mod, r, kT):
             counts.append(o.occ.sum() / 2)
     frac = np.mean(counts) / n_pairs
     se = _two_state_se(expect, p_on, p_off, n_pairs, T)
+    assert 0.1 < expect < 0.95                  # a regime where the factor matters
     assert abs(frac - expect) < 4.5 * se, (frac, expect, se)
 
 
 def test_fene_beyond_r0_never_bonds(oracle_mod):
-    s = _fene(frozen_pairs(seed=6, n_pairs=64, r=1.55, eps=5.0, r_max=1.6), 30.0, 1.5)
+    s = _fene(frozen_pairs(seed=6, n_pairs=64, r=1.55, eps=5.0, r_max=1.6))
     o = oracle_mod.OracleSystem(s, p_on0=1.0)
     for t in range(200):
         st = o.sweep(step=t)
