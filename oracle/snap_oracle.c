@@ -24,8 +24,11 @@
  *   - the proposal keeps the partner minimising |r - r0|, ties to the smaller
  *     tag; the window test is r_min^2 <= r^2 <= r_max^2 in FP64;
  *   - T in Eq. (3) is the set-point kT; at kT = 0 the factor is [U_b <= 0];
- *   - exp() in Eq. (3) is this file's own (Cody–Waite + Taylor), so that the
- *     CUDA path, which implements the same published recipe, decides alike;
+ *   - exp() in Eq. (3) is this file's own (Cody–Waite + Taylor), and so is
+ *     the log() of a FENE dynamic bond's energy (atanh series), so that the
+ *     CUDA path, which implements the same published recipes, decides alike;
+ *   - a proposal aims at the minimum of the reaction's bond term: r0 for a
+ *     harmonic bond, 0 for FENE;
  *   - Langevin: leapfrog form of velocity Verlet with drag -gamma v_{t-1/2}
  *     and a uniform random force sqrt(2 gamma kT / dt) * sqrt(3) (2u - 1);
  *   - no pair exclusions: WCA acts on bonded pairs too;
