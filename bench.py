@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", default="snap", choices=["snap", "reference"])
     ap.add_argument("--n-c", type=int, default=200_000)
     ap.add_argument("--n-l", type=int, default=800_000)
+    ap.add_argument("--equil-steps", type=int, default=2000,
+                    help="untimed steps from the bond-free start before the warm-up, so that every "
+                         "timed window sees the gel in its saturated (push-mode) state")
     ap.add_argument("--profile-steps", type=int, default=50)
     ap.add_argument("--fp64-steps", type=int, default=200)
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -286,6 +289,7 @@ def _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream):
                            skin=tune["skin"])
     nb = sum(s.n for s in batch)
     sim.step(args.warmup)
+    sim.prepare()
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -316,6 +320,7 @@ def _run_competing(args, torch, snap, barrier, max_all, sum_all, stream):
     s = four_reaction_soup(seed=20260921, n=args.competing_n, rho=0.3, eps=eps)
     sim = snap.from_system(s, precision="mixed", block_size=128, skin=0.4)
     sim.step(max(args.warmup, 200))
+    sim.prepare()
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -376,6 +381,7 @@ def _run_learned(args, torch, snap, rank, stream):
         return e0.elapsed_time(e1) / 1e3
 
     sim.step(args.warmup)
+    sim.prepare()
     K = args.mh_steps
     t_plain = timed(lambda: sim.step(K))
     # log formation events of plain sweeps
@@ -415,6 +421,7 @@ def _run_learned(args, torch, snap, rank, stream):
         sim.set_state(state)
         sim.set_mh(mode, mlp if mode == 2 else None, eps_u=0.05)
         sim.step(50)
+        sim.prepare()
         st0 = sim.stats()
         h0 = sim.lifetime_hist()
         t_mh = timed(lambda: sim.step(K))
@@ -473,7 +480,13 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
 
     sim = make("mixed")
 
+    # a fixed untimed equilibration (bonds form from the bond-free start), the
+    # warm-up, then the step graphs of both buffer parities are captured and
+    # uploaded so that no capture falls inside the timed region
+    E = args.equil_steps
+    sim.step(E)
     sim.step(W)
+    sim.prepare()
     st0 = sim.stats()
     barrier()
     torch.cuda.synchronize()
@@ -533,6 +546,9 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
         "phases_ms_per_step": {k: round(v, 5) for k, v in ph.items()},
         "rebuild_ms_per_kernel": rebuild_ms,
         "bond_update_pairs_per_s": bond_pairs_per_s,
+        "state_at_timing": {"equilibration_steps": E, "warmup_steps": W, "n_bonds": st0["n_bonds"],
+                            "colloid_slot_occupancy": st0["n_bonds"] / (4.0 * args.n_c),
+                            "graphs": "captured and uploaded for both buffer parities before the timed region"},
         "sweep": {"scanned_nlist_entries": st2["scanned"], "break_tested": st2["break_tested"],
                   "proposals": st2["proposals"], "formed": st2["formed"], "broken": st2["broken"],
                   "n_bonds": st2["n_bonds"], "mean_neighbours": nbar,
@@ -549,7 +565,9 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
         def fp64_leg():
             sim64 = make("fp64")
             try:
+                sim64.step(E)
                 sim64.step(W)
+                sim64.prepare()
                 barrier()
                 torch.cuda.synchronize()
                 K64 = args.fp64_steps

@@ -145,8 +145,8 @@ snap_status snap_set_types(snap_ctx *, int32_t ntypes, const double *sigma,
 snap_status snap_set_valence(snap_ctx *, const int32_t *valence);
 
 /* Bond type bt: SNAP_HARMONIC U = k/2 (r - r0)^2, or SNAP_FENE
- * U = -k R0^2/2 ln(1 - (r/R0)^2) with r0_or_R0 = R0.  Dynamic bonds must be
- * harmonic (Eq. 4); FENE is for static bonds. */
+ * U = -k R0^2/2 ln(1 - (r/R0)^2) with r0_or_R0 = R0.  Either kind may be a
+ * static bond or the bond type of a reaction (snap_add_reaction). */
 snap_status snap_set_bond_params(snap_ctx *, int32_t bt, int32_t kind, double k,
                                  double r0_or_R0);
 
@@ -217,6 +217,26 @@ snap_status snap_set_bonds(snap_ctx *, int64_t nb, const int32_t *tag_pairs,
  * environment variable SNAP_GRAPH_MODE=plain captures every kernel instead
  * (for per-kernel profilers), SNAP_GRAPH_MODE=none disables graphs. */
 snap_status snap_step(snap_ctx *, int64_t nsteps);
+
+/* Retry limit of the lock-free 16-byte compare-and-swap minimum that the
+ * proposal phase uses when one side of a reaction is scarce (default 65536).
+ * A pusher retries only when another pusher lowered the same key in between,
+ * so the limit is never reached in correct operation; reaching it latches
+ * SNAP_ERR_TIMEOUT, which the step or sweep call returns.  The failing step is
+ * not taken: its sweep's scratch is cleared, bonds and positions keep their
+ * values from before it, and the step counter does not advance.  Lowering the
+ * limit (0 makes every such exchange give up) exercises that path; limit < 0
+ * returns SNAP_ERR_ARG. */
+snap_status snap_set_retry_limit(snap_ctx *, int32_t limit);
+
+/* Capture, instantiate and upload the step graphs for both buffer parities
+ * now, so that no later snap_step pays for a capture (a step swaps two
+ * coordinate buffers; a call with an odd step count leaves the next call on
+ * the other one, and each parity has a graph of its own).  Runs no step and
+ * changes no state; waits for the stream.  With SNAP_GRAPH_MODE=none it does
+ * nothing.  Parameters or buffers that change later (a new reaction, a grown
+ * neighbour list) make the graphs stale; the next snap_step recaptures. */
+snap_status snap_prepare(snap_ctx *);
 
 /* Advance nsteps MD steps launched one kernel at a time with CUDA events
  * between the phases, and write the average milliseconds per step of each
@@ -339,8 +359,9 @@ snap_status snap_get_events(snap_ctx *, float *feat, int32_t *offsets, int32_t *
  * Computes the total Lennard-Jones/WCA pair energy (d_out[0]) and pair virial
  * sum_pairs (-dU/dr) r (d_out[1]) of n particles by direct summation over all
  * pairs, with the same pair potential and parameters as snap_set_types.
- * d_pos3: device, n*3 doubles (x,y,z per particle); d_type: device, n int32;
- * d_out: device, 2 doubles; box, sigma[ntypes], eps_pair[ntypes^2] and
+ * d_pos3: device, n*3 doubles (x,y,z per particle); d_type: device, n int32,
+ * each in [0, ntypes) (a particle whose type lies outside that range takes
+ * part in no pair); d_out: device, 2 doubles; box, sigma[ntypes], eps_pair[ntypes^2] and
  * rcut[ntypes^2] (nullable: WCA cut) are host arrays read before the call
  * returns.  Work is queued on `stream` (a cudaStream_t, NULL: default stream);
  * d_out is valid once the stream reaches that point.

@@ -219,6 +219,16 @@ class Snap:
     def step(self, nsteps=1):
         self._check(self._lib.snap_step(self._ctx, int(nsteps)))
 
+    def set_retry_limit(self, limit):
+        """Retry limit of the push-mode compare-and-swap loop (default 65536);
+        reaching it makes the step return SNAP_ERR_TIMEOUT without taking it."""
+        self._check(self._lib.snap_set_retry_limit(self._ctx, int(limit)))
+
+    def prepare(self):
+        """Capture and upload the step graphs of both buffer parities now (no
+        step runs), so that no later step() pays for a capture."""
+        self._check(self._lib.snap_prepare(self._ctx))
+
     def step_profiled(self, nsteps):
         """Run nsteps without graphs, timing each phase with CUDA events; returns
         average ms per step of (rebuild, sweep, md = the fused force + Langevin

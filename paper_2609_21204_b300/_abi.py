@@ -62,6 +62,8 @@ SIGNATURES = {
     "snap_set_positions": (C.c_int, [_P, _P, _P]),
     "snap_set_bonds": (C.c_int, [_P, C.c_int64, _P, _P]),
     "snap_step": (C.c_int, [_P, C.c_int64]),
+    "snap_prepare": (C.c_int, [_P]),
+    "snap_set_retry_limit": (C.c_int, [_P, C.c_int32]),
     "snap_step_profiled": (C.c_int, [_P, C.c_int64, _P]),
     "snap_bond_update": (C.c_int, [_P]),
     "snap_get_forces": (C.c_int, [_P, _P]),

@@ -83,11 +83,15 @@ struct snap_ctx {
     bool mh_alloc = false;
     long long ev_cap = 0;
     // graphs
-    cudaGraphExec_t graph = nullptr;
-    bool graph_dirty = true;
-    void *graph_key = nullptr;       // A.pos4 when the graph was captured (the step swaps pos4/pos4n)
+    // One instantiated graph per buffer parity: a step swaps pos4/pos4n, so a
+    // call whose step count leaves a remainder starts the next call on the
+    // other buffer; its graph is kept rather than recaptured.
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    void *graph_key[2] = {nullptr, nullptr};   // A.pos4 when each graph was captured
+    bool graph_dirty = true;                    // both graphs stale (parameters or buffers changed)
     int nbr_cap = 0;
     int rnbr_cap = 0;
+    int cas_cap = 1 << 16;           // push-mode compare-and-swap retries (snap_set_retry_limit)
 };
 
 namespace {
@@ -269,6 +273,7 @@ void fill_params(snap_ctx *c)
     P.log_events = c->ev_cap > 0 ? 1 : 0;
     P.pdist_rows = std::max<int64_t>(c->n, 1) / 5 + 1;
     P.has_static = c->n_static > 0 ? 1 : 0;   // push mode needs a side 4x scarcer: <= n / 5 sites
+    P.cas_cap = c->cas_cap;
 }
 
 // everything that depends on the model (cut-offs -> cell grids -> capacities)
@@ -491,17 +496,29 @@ void end_dangling_capture(cudaStream_t s)
     cudaGetLastError();
 }
 
-snap_status build_graph(snap_ctx *c)
+void drop_graphs(snap_ctx *c)
 {
-    if (c->graph) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+        c->graph_key[k] = nullptr;
+    }
+}
+
+// Capture kGraphSteps steps starting from the current buffer parity into
+// graph slot k.  Capturing queues nothing: the stream runs no work until the
+// graph is launched.
+snap_status build_graph(snap_ctx *c, int k)
+{
+    if (c->graph[k]) {
+        cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+        c->graph_key[k] = nullptr;
     }
     const int mode = graph_mode();
     if (!c->side) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     static_assert(kGraphSteps % 2 == 0, "a graph must swap pos4/pos4n an even number of times");
-    c->graph_key = c->A.pos4;
     void *const pos4_0 = c->A.pos4, *const pos4_1 = c->A.pos4n;   // restored after the capture
     CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t ce = cudaSuccess;
@@ -518,7 +535,6 @@ snap_status build_graph(snap_ctx *c)
     if (ce != cudaSuccess) {
         end_dangling_capture(c->side);
         end_dangling_capture(c->stream);
-        c->graph_dirty = true;
         return fail(c, SNAP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
     }
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
@@ -530,8 +546,31 @@ snap_status build_graph(snap_ctx *c)
         cudaGetLastError();
         return fail(c, SNAP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
-    c->graph = ex;
-    c->graph_dirty = false;
+    c->graph[k] = ex;
+    c->graph_key[k] = pos4_0;
+    return SNAP_OK;
+}
+
+// The graph for the current buffer parity, captured on first use (*out is
+// its slot).  Stale graphs are dropped first.
+snap_status graph_for_parity(snap_ctx *c, int &out)
+{
+    if (c->graph_dirty) {
+        drop_graphs(c);
+        c->graph_dirty = false;
+    }
+    for (int k = 0; k < 2; ++k)
+        if (c->graph[k] && c->graph_key[k] == c->A.pos4) {
+            out = k;
+            return SNAP_OK;
+        }
+    const int k = c->graph[0] ? 1 : 0;
+    snap_status s = build_graph(c, k);
+    if (s != SNAP_OK) {
+        c->graph_dirty = true;
+        return s;
+    }
+    out = k;
     return SNAP_OK;
 }
 
@@ -545,6 +584,18 @@ snap_status read_status(snap_ctx *c, uint32_t &st)
 snap_status clear_status(snap_ctx *c)
 {
     CUDA_TRY(c, cudaMemsetAsync(c->A.status, 0, sizeof(uint32_t), c->stream));
+    return SNAP_OK;
+}
+
+// After a latched status: clear it and the sweep scratch a stopped sweep may
+// have left behind.  The step that latched it did not complete (the step
+// counter did not advance).
+snap_status recover_status(snap_ctx *c)
+{
+    snap_status s = clear_status(c);
+    if (s != SNAP_OK) return s;
+    if (c->ready && c->particles_set) launch_sweep_reset(c->P, c->A, launch(c));
+    CUDA_TRY(c, cudaGetLastError());
     return SNAP_OK;
 }
 
@@ -610,7 +661,7 @@ template <typename F> snap_status run_with_retry(snap_ctx *c, F f)
             continue;
         }
         if (st) {
-            clear_status(c);
+            recover_status(c);
             return status_to_code(c, st);
         }
         return SNAP_OK;
@@ -1227,10 +1278,9 @@ extern "C" snap_status snap_step(snap_ctx *c, int64_t nsteps)
     while (cur < target) {
         long long todo = std::min<long long>(target - cur, kPollSteps);
         long long ngraph = graph_mode() == 2 ? 0 : todo / kGraphSteps;
-        if (ngraph > 0 && (c->graph_dirty || c->graph_key != c->A.pos4)) {
-            if ((s = build_graph(c)) != SNAP_OK) return s;
-        }
-        for (long long g = 0; g < ngraph; ++g) CUDA_TRY(c, cudaGraphLaunch(c->graph, c->stream));
+        int gk = 0;
+        if (ngraph > 0 && (s = graph_for_parity(c, gk)) != SNAP_OK) return s;
+        for (long long g = 0; g < ngraph; ++g) CUDA_TRY(c, cudaGraphLaunch(c->graph[gk], c->stream));
         for (long long r = ngraph * kGraphSteps; r < todo; ++r) seq_step(c);
         CUDA_TRY(c, cudaGetLastError());
         uint32_t st = 0;
@@ -1245,12 +1295,44 @@ extern "C" snap_status snap_step(snap_ctx *c, int64_t nsteps)
         if (st) {
             // the step stopped part-way: regenerate the relative coordinates
             // from the FP64 positions at the next step
-            clear_status(c);
+            recover_status(c);
             const snap_status code = status_to_code(c, st);
             set_need_rebuild(c);
             return code;
         }
     }
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_set_retry_limit(snap_ctx *c, int32_t limit)
+{
+    if (!c) return SNAP_ERR_ARG;
+    if (limit < 0) return fail(c, SNAP_ERR_ARG, "retry limit < 0");
+    c->cas_cap = limit;
+    c->P.cas_cap = limit;     // kernel parameters are captured by value: recapture the graphs
+    c->graph_dirty = true;
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_prepare(snap_ctx *c)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (graph_mode() == 2) return SNAP_OK;
+    for (int parity = 0; parity < 2; ++parity) {
+        int k = 0;
+        s = graph_for_parity(c, k);
+        if (s == SNAP_OK && cudaGraphUpload(c->graph[k], c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            s = fail(c, SNAP_ERR_CUDA, "cudaGraphUpload failed");
+        }
+        std::swap(c->A.pos4, c->A.pos4n);   // the other parity; two swaps restore the buffers
+        if (s != SNAP_OK) {
+            if (parity == 0) std::swap(c->A.pos4, c->A.pos4n);
+            return s;
+        }
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return SNAP_OK;
 }
 
@@ -1839,7 +1921,7 @@ extern "C" void snap_destroy(snap_ctx *c)
 {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->graph) cudaGraphExecDestroy(c->graph);
+    drop_graphs(c);
     std::vector<void *> all = c->allocs;
     for (void *p : all) dfree(c, p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -123,7 +123,10 @@ __device__ __forceinline__ double exact_r2(const DevArrays &A, const RepDev &R, 
 // The same value with the minimum image skipped on axes where it is the
 // identity: when the two frozen cells (bits of pos4.w) are neighbours without
 // wrapping and there are at least 6 cells, |d| < 2 w + skin < L / 2, so
-// rint(d / L) = 0 and d - L * 0 = d exactly.
+// rint(d / L) = 0 and d - L * 0 = d exactly.  Valid only while positions stay
+// unwrapped between rebuilds (mixed mode); FP64 mode wraps them every step,
+// so a particle that crossed a face since the rebuild sits a box edge away
+// from its frozen cell and needs the full minimum image.
 __device__ __forceinline__ double exact_r2_cells(const DevArrays &A, const RepDev &R, int i, int j, uint32_t bi,
                                                  uint32_t bj)
 {
@@ -431,12 +434,13 @@ __device__ __forceinline__ ulonglong2 cas128(ulonglong2 *p, ulonglong2 cmp, ulon
 
 // Lowers *p to (d, t) if smaller.  Lock-free: a failed exchange means another
 // pusher lowered the key; the retries are bounded by the pushers of one site
-// (the cap only guards against a defect, and latches a status bit).
+// (the cap, 2^16 unless snap_set_retry_limit lowers it, only guards against a
+// defect, and latches a status bit).
 __device__ __forceinline__ void atomic_min_key(ulonglong2 *p, unsigned long long d, unsigned long long t,
-                                               uint32_t *status)
+                                               uint32_t *status, int cap)
 {
     ulonglong2 cur = *p;
-    for (int it = 0; it < (1 << 16); ++it) {
+    for (int it = 0; it < cap; ++it) {
         if (!key_less(d, t, cur.x, cur.y)) return;
         const ulonglong2 old = cas128(p, cur, make_ulonglong2(d, t));
         if (old.x == cur.x && old.y == cur.y) return;
@@ -487,13 +491,14 @@ __device__ __forceinline__ void push_pass1(const DevParams &P, DevArrays &A, int
                     const float r2f = screen_r2(pi4, pj4, R);
                     maybe = !(r2f < rmin2f - kScreenR2 || r2f > rmax2f + kScreenR2);
                 } else {
-                    bj = cell_bits(P, A, j);
+                    bj = 0u;                             // FP64 mode: full minimum image, cells unused
                 }
-                const double r2 = maybe ? exact_r2_cells(A, R, i, j, bi, bj) : -1.0;
+                const double r2 = !maybe ? -1.0
+                                  : P.screen ? exact_r2_cells(A, R, i, j, bi, bj) : exact_r2(A, R, i, j);
                 if (maybe && r2 >= rmin2 && r2 <= rmax2) {
                     inwin += 2;
                     d = (unsigned long long)__double_as_longlong(fabs(__dsub_rn(__dsqrt_rn(r2), r0)));
-                    atomic_min_key(&A.pkey[j], d, me, A.status);
+                    atomic_min_key(&A.pkey[j], d, me, A.status, P.cas_cap);
                     const unsigned long long tj = (unsigned long long)(uint32_t)A.tag[j];
                     if (key_less(d, tj, bd, bt)) {
                         bd = d;
@@ -795,6 +800,23 @@ __global__ void k_apply(DevParams P, DevArrays A, int slot)
     warp_counts<2>(A.counters, idx, v);
 }
 
+// After a latched status the sweep may have stopped part-way (its later
+// kernels return early, k_apply among them): clear the per-reaction scratch
+// that k_apply would have cleared, so that the next sweep starts clean.  The
+// bond slots, occupancies and positions are untouched.
+__global__ void k_sweep_reset(DevParams P, DevArrays A)
+{
+    const long long i = gtid();
+    if (i == 0) *A.list_count = 0;
+    if (i < kMaxTypes) A.avail_count[i] = 0;
+    if (i >= P.n) return;
+    A.brk[i] = 0u;
+    A.fpart[i] = -1;
+    A.best[i] = 0ull;
+    A.prop[i] = -1;
+    A.pkey[i] = make_ulonglong2(~0ull, ~0ull);
+}
+
 __global__ void k_step_end(DevArrays A)
 {
     if (!status_ok(A.status)) return;
@@ -846,5 +868,10 @@ void launch_sweep_reaction_forced(const DevParams &P, const DevArrays &A, int sl
 }
 
 void launch_step_end(const DevArrays &A, Launch L) { k_step_end<<<1, 1, 0, L.stream>>>(A); }
+
+void launch_sweep_reset(const DevParams &P, const DevArrays &A, Launch L)
+{
+    k_sweep_reset<<<grid_for(std::max<long long>(P.n, kMaxTypes), 256), 256, 0, L.stream>>>(P, A);
+}
 
 }  // namespace snap

@@ -67,6 +67,7 @@ struct DevParams {
     int32_t log_events;     // record bond-formation events in the plain sweep
     int64_t pdist_rows;     // pushing sites whose pair distances fit the pdist scratch
     int32_t has_static;     // any static bonds (else their slots are neither gathered nor read)
+    int32_t cas_cap;        // retries of the push-mode 16-byte compare-and-swap before SNAP_ERR_TIMEOUT
 };
 
 struct RepDev {

@@ -42,6 +42,8 @@ void launch_sweep_reaction(const DevParams &P, const DevArrays &A, int slot, Lau
 // forced: run even when step % period != 0 (snap_bond_update)
 void launch_sweep_begin_forced(const DevParams &P, const DevArrays &A, Launch L);
 void launch_sweep_reaction_forced(const DevParams &P, const DevArrays &A, int slot, Launch L);
+// clears the per-reaction sweep scratch after a latched status stopped a sweep part-way
+void launch_sweep_reset(const DevParams &P, const DevArrays &A, Launch L);
 
 // ---- forces and integration ----
 void launch_force(const DevParams &P, const DevArrays &A, bool fp64, bool energy, Launch L);
