@@ -68,7 +68,8 @@ class State(C.Structure):
                 ("dbirth", C.c_void_p), ("occ", C.c_void_p),
                 ("fx", C.c_void_p), ("fy", C.c_void_p), ("fz", C.c_void_p),
                 ("pe", C.c_void_p), ("life_hist", C.c_void_p), ("nhist", C.c_int32),
-                ("step", C.c_int64), ("mol", C.c_void_p)]
+                ("step", C.c_int64), ("mol", C.c_void_p), ("fscale", C.c_void_p),
+                ("vabs", C.c_double)]
 
 
 class SweepStats(C.Structure):
@@ -235,6 +236,7 @@ class OracleSystem:
         self.fy = np.zeros(n)
         self.fz = np.zeros(n)
         self.pe = np.zeros(n)
+        self.fscale = np.zeros(n)
         self.life_hist = np.zeros(nhist, dtype=np.int64)
         self.mol = molecules(n, s.static_bonds)
         self.step = 0
@@ -244,7 +246,7 @@ class OracleSystem:
     def _sync_ptrs(self):
         S = self._state
         for f in ("x", "y", "z", "vx", "vy", "vz", "img", "type", "sp", "sbt", "dp", "drx",
-                  "dbirth", "occ", "fx", "fy", "fz", "pe", "life_hist", "mol"):
+                  "dbirth", "occ", "fx", "fy", "fz", "pe", "life_hist", "mol", "fscale"):
             setattr(S, f, _ptr(getattr(self, f)))
         S.nhist = self.life_hist.size
         S.step = self.step
@@ -328,7 +330,8 @@ class OracleSystem:
         rc = lib().orc_forces(C.byref(self.params), C.byref(self._state), _ptr(e[0:1]),
                               _ptr(e[1:2]), _ptr(e[2:3]))
         f = np.stack([self.fx, self.fy, self.fz], axis=1).copy()
-        return f, dict(e_pair=e[0], e_bond=e[1], virial=e[2], status=rc)
+        return f, dict(e_pair=e[0], e_bond=e[1], virial=e[2], status=rc,
+                       fscale=self.fscale.copy(), virial_scale=float(self._state.vabs))
 
     def run(self, nsteps):
         self._sync_ptrs()

@@ -919,6 +919,14 @@ static void orc_force_visit(int64_t j, void *vctx)
     S->fx[i] -= fr * dx; S->fy[i] -= fr * dy; S->fz[i] -= fr * dz;
     S->fx[j] += fr * dx; S->fy[j] += fr * dy; S->fz[j] += fr * dz;
     if (S->pe) { S->pe[i] += 0.5 * u; S->pe[j] += 0.5 * u; }
+    {
+        /* |F| and r |dF/dr| of the pair force F(r) = 24 eps (2 s12 - s6) / r */
+        double r = sqrt(r2);
+        double f = fabs(fr) * r;
+        double g = 24.0 * eps * fabs(7.0 * s6 - 26.0 * s12) / r;
+        if (S->fscale) { S->fscale[i] += f + g; S->fscale[j] += f + g; }
+        S->vabs += r * (f + g);
+    }
     c->epair += u;
     c->vir += fr * r2;
 }
@@ -930,20 +938,28 @@ static int orc_bond_pair(const orc_params *P, orc_state *S, int64_t i, int64_t j
     double dx, dy, dz;
     double r2 = orc_dist2(P, S, i, j, &dx, &dy, &dz);
     double k = P->bk[bt], r0 = P->br0[bt];
-    double fb, u;
+    double fb, u, g;   /* g = r |dF/dr| of the bond force F(r) = -dU/dr */
     if (P->bkind[bt] == ORC_HARMONIC) {
         double r = sqrt(r2);
         fb = k * (r - r0) / r;       /* (dU/dr)/r, pulls i towards j when stretched */
         u = 0.5 * k * (r - r0) * (r - r0);
+        g = k * r;
     } else {
         double q = r2 / (r0 * r0);
         if (q >= 1.0) return ORC_ERR_FENE;
         fb = k / (1.0 - q);
         u = -0.5 * k * r0 * r0 * log(1.0 - q);
+        g = k * sqrt(r2) * (1.0 + q) / ((1.0 - q) * (1.0 - q));
     }
     S->fx[i] += fb * dx; S->fy[i] += fb * dy; S->fz[i] += fb * dz;
     S->fx[j] -= fb * dx; S->fy[j] -= fb * dy; S->fz[j] -= fb * dz;
     if (S->pe) { S->pe[i] += 0.5 * u; S->pe[j] += 0.5 * u; }
+    {
+        double r = sqrt(r2);
+        double f = fabs(fb) * r;
+        if (S->fscale) { S->fscale[i] += f + g; S->fscale[j] += f + g; }
+        S->vabs += r * (f + g);
+    }
     *eb += u;
     *vir -= fb * r2;
     return 0;
@@ -962,7 +978,9 @@ int orc_forces(const orc_params *P, orc_state *S, double *e_pair, double *e_bond
     for (int64_t i = 0; i < n; ++i) {
         S->fx[i] = S->fy[i] = S->fz[i] = 0.0;
         if (S->pe) S->pe[i] = 0.0;
+        if (S->fscale) S->fscale[i] = 0.0;
     }
+    S->vabs = 0.0;
     orc_grid g;
     if (orc_grid_build(P, S, rcmax > 0 ? rcmax : 1.0, &g) != 0) return ORC_ERR_ARG;
     orc_force_ctx c;

@@ -74,6 +74,12 @@ typedef struct {
     int64_t step;
     const int32_t *mol;         /* molecule id per particle: the connected components of the
                                  * static bonds; read by reactions with self_avoid */
+    double *fscale;             /* nullable: orc_forces writes, per particle, the sensitivity scale
+                                 * G_i = sum_j (|F_ij| + r_ij |dF_ij/dr|) over every pair and bond
+                                 * force on it: relative perturbations of at most e in every
+                                 * separation and in every term change F_i by at most ~e G_i */
+    double vabs;                /* written by orc_forces: sum over pairs and bonds of
+                                 * r (|F| + r |dF/dr|), the same scale for the virial */
 } orc_state;
 
 typedef struct {
