@@ -44,14 +44,19 @@ __global__ void k_pair_partial(int n, const double *__restrict__ pos3, const int
     const double xi = pos3[3 * i], yi = pos3[3 * i + 1], zi = pos3[3 * i + 2];
     const int ti = type[i];
     double e = 0.0, w = 0.0;
-    for (int j = 0; j < n; ++j) {
+    // a type outside [0, ntypes) would index past the pair table: such a
+    // particle takes part in no pair
+    const bool ti_ok = (unsigned)ti < (unsigned)T.ntypes;
+    for (int j = 0; ti_ok && j < n; ++j) {
         if (j == i) continue;
+        const int tj = type[j];
+        if ((unsigned)tj >= (unsigned)T.ntypes) continue;
         double dx = pos3[3 * j] - xi, dy = pos3[3 * j + 1] - yi, dz = pos3[3 * j + 2] - zi;
         dx -= T.L[0] * rint(dx / T.L[0]);
         dy -= T.L[1] * rint(dy / T.L[1]);
         dz -= T.L[2] * rint(dz / T.L[2]);
         const double r2 = dx * dx + dy * dy + dz * dz;
-        const int k = ti * snap::kMaxTypes + type[j];
+        const int k = ti * snap::kMaxTypes + tj;
         if (r2 >= T.rc2[k]) continue;
         const double s2 = T.sig2[k] / r2;
         const double s6 = s2 * s2 * s2;
