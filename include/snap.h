@@ -192,6 +192,19 @@ snap_status snap_set_slip(snap_ctx *, int32_t reaction, double a);
 snap_status snap_set_melting(snap_ctx *, int32_t reaction, double lambda, double t_melt,
                              double kon_init, double koff_init, double kon_melt, double koff_melt);
 
+/* Temperature of the sweep (Sec. II.B: T in Eq. 3 is the instantaneous
+ * kinetic temperature when the updater triggers).  on = 0 (default): every
+ * replica's set-point kT.  on = 1: at the start of every sweep each replica's
+ * T = sum_i |v_i|^2 / (3 n) over its half-step velocities v_{t-1/2}, summed
+ * deterministically (each |v_i|^2 in FP64 rounded to the nearest multiple of
+ * 2^-32 and the integers added exactly; sums of |v_i|^2 up to ~2^31 per
+ * replica), so the sweep stays independent of thread order.  That T enters
+ * Eq. 3, the slip factor, and the melting switch, which is then re-evaluated
+ * every sweep (Eqs. gT, kT, 2, probabilities capped at 1).  T = 0 gives the
+ * factor [U_b <= 0].  Other values of on return SNAP_ERR_ARG; the
+ * Metropolis-Hastings move set (snap_set_mh) excludes on = 1 (SNAP_ERR_STATE). */
+snap_status snap_set_kinetic_temperature(snap_ctx *, int32_t on);
+
 /* Per-replica rates of one reaction (batched sweeps over the bond energy). */
 snap_status snap_set_reaction_rates(snap_ctx *, int32_t reaction, int32_t replica,
                                     double p_on0, double p_off);

@@ -45,7 +45,9 @@ class Reaction(C.Structure):
     _fields_ = [("type_a", C.c_int32), ("type_b", C.c_int32), ("bond_type", C.c_int32),
                 ("r_min", C.c_double), ("r_max", C.c_double),
                 ("p_on0", C.c_double), ("p_off", C.c_double), ("self_avoid", C.c_int32),
-                ("slip_a", C.c_double)]
+                ("slip_a", C.c_double), ("melt", C.c_int32), ("melt_lambda", C.c_double),
+                ("melt_t", C.c_double), ("kon_init", C.c_double), ("koff_init", C.c_double),
+                ("kon_melt", C.c_double), ("koff_melt", C.c_double)]
 
 
 class Params(C.Structure):
@@ -57,7 +59,7 @@ class Params(C.Structure):
                 ("valence", C.c_int32 * MAX_TYPES), ("nbtypes", C.c_int32),
                 ("bkind", C.c_int32 * MAX_BTYPES), ("bk", C.c_double * MAX_BTYPES),
                 ("br0", C.c_double * MAX_BTYPES), ("nrx", C.c_int32),
-                ("rx", Reaction * MAX_RX), ("bond_period", C.c_int32)]
+                ("rx", Reaction * MAX_RX), ("bond_period", C.c_int32), ("kinetic_T", C.c_int32)]
 
 
 class State(C.Structure):
@@ -121,6 +123,10 @@ def lib():
                                         C.c_int64, C.c_void_p, C.c_int32]
         _lib.orc_candidates.restype = C.c_int32
         _lib.orc_mh_sweep.argtypes = [C.POINTER(Params), C.POINTER(State), C.c_int64, C.POINTER(MHStats)]
+        _lib.orc_kinetic_T.argtypes = [C.POINTER(Params), C.POINTER(State)]
+        _lib.orc_kinetic_T.restype = C.c_double
+        _lib.orc_tanh.argtypes = [C.c_double]
+        _lib.orc_tanh.restype = C.c_double
     return _lib
 
 
@@ -142,6 +148,10 @@ def u53(w0, w1):
 
 def exp(x: float) -> float:
     return lib().orc_exp(float(x))
+
+
+def tanh(x: float) -> float:
+    return lib().orc_tanh(float(x))
 
 
 def log(x: float) -> float:
@@ -205,9 +215,12 @@ class OracleSystem:
                 pon, poff = melting_rates(float(s.kT), *r.melt, int(s.bond_period), float(s.dt))
             else:
                 pon, poff = rates_from_eps(r.eps, p_on0)
+            melt = getattr(r, "melt", None)
             P.rx[i] = Reaction(r.type_a, r.type_b, r.bond_type, r.r_min, r.r_max, pon, poff,
-                               r.self_avoid, float(getattr(r, "slip_a", 0.0)))
+                               r.self_avoid, float(getattr(r, "slip_a", 0.0)),
+                               1 if melt is not None else 0, *(map(float, melt) if melt is not None else [0.0] * 6))
         P.bond_period = int(s.bond_period)
+        P.kinetic_T = int(getattr(s, "kinetic_T", 0))
         self.params = P
         self.n = n
         self.x = np.ascontiguousarray(s.pos[:, 0], dtype=np.float64).copy()
@@ -323,6 +336,16 @@ class OracleSystem:
         if rc != 0:
             raise RuntimeError(f"orc_mh_sweep failed: {rc}")
         return st.as_dict()
+
+    def kinetic_T(self):
+        """The instantaneous kinetic temperature a sweep would use now."""
+        self._sync_ptrs()
+        return lib().orc_kinetic_T(C.byref(self.params), C.byref(self._state))
+
+    def set_velocities(self, vel):
+        self.vx[:] = vel[:, 0]
+        self.vy[:] = vel[:, 1]
+        self.vz[:] = vel[:, 2]
 
     def forces(self):
         self._sync_ptrs()

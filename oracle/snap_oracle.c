@@ -236,31 +236,66 @@ static double orc_rest_length(const orc_params *P, int32_t bt)
     return P->bkind[bt] == ORC_HARMONIC ? P->br0[bt] : 0.0;
 }
 
-/* Eq. (3): P_on(r) = P_on^0 exp(-U_b(r)/kT); at kT = 0 the factor is [U_b <= 0]. */
-static double orc_p_on(const orc_params *P, const orc_reaction *R, double r)
+/* Eq. (3): P_on(r) = P_on^0 exp(-U_b(r)/kT); at kT = 0 the factor is [U_b <= 0].
+ * T is the sweep's temperature (set-point or kinetic) and p_on0 the sweep's rate. */
+static double orc_p_on(const orc_params *P, const orc_reaction *R, double r, double T, double p_on0)
 {
     double U = orc_dyn_energy(P, R->bond_type, r);
-    if (P->kT > 0.0) {
-        double a = U / P->kT;
-        return R->p_on0 * orc_exp(-a);
+    if (T > 0.0) {
+        double a = U / T;
+        return p_on0 * orc_exp(-a);
     }
-    return (U <= 0.0) ? R->p_on0 : 0.0;
+    return (U <= 0.0) ? p_on0 : 0.0;
+}
+
+double orc_kinetic_T(const orc_params *P, const orc_state *S)
+{
+    int64_t n = P->n;
+    if (n <= 0) return 0.0;
+    uint64_t sum = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double v2 = (S->vx[i] * S->vx[i] + S->vy[i] * S->vy[i]) + S->vz[i] * S->vz[i];
+        sum += (uint64_t)llrint(v2 * 0x1.0p32);
+    }
+    return ((double)(int64_t)sum * 0x1.0p-32) / (double)(3 * n);
+}
+
+double orc_tanh(double x)
+{
+    double ax = fabs(x);
+    double e = orc_exp(-2.0 * ax);
+    double t = (1.0 - e) / (1.0 + e);
+    return x < 0.0 ? -t : t;
+}
+
+/* Melting switch, Eqs. (gT)-(kT), at temperature T, with Eq. (2):
+ * g = (tanh(lambda (T - T_melt)) + 1) / 2, k = k_init (1 - g) + k_melt g,
+ * P = k n dt (capped at 1). */
+static void orc_melt_rates(const orc_params *P, const orc_reaction *R, double T, double *pon, double *poff)
+{
+    double nd = (double)P->bond_period * P->dt;
+    double g = 0.5 * (orc_tanh(R->melt_lambda * (T - R->melt_t)) + 1.0);
+    double kon = R->kon_init * (1.0 - g) + R->kon_melt * g;
+    double koff = R->koff_init * (1.0 - g) + R->koff_melt * g;
+    double a = kon * nd, b = koff * nd;
+    *pon = a < 1.0 ? a : 1.0;
+    *poff = b < 1.0 ? b : 1.0;
 }
 
 /* Slip bond, Eq. (slip): a bond at separation r breaks with
  * P_off(r) = P_off^0 exp(a sqrt(U_b(r)/kT)), capped at 1.  As kT -> 0 the
  * factor tends to 1 for U_b = 0 and to infinity (P_off -> 1) for U_b > 0; at
  * kT = 0 it takes those limits.  An exponent of 700 or more caps at once. */
-static double orc_p_off(const orc_params *P, const orc_reaction *R, double r)
+static double orc_p_off(const orc_params *P, const orc_reaction *R, double r, double T, double p_off)
 {
-    if (R->slip_a == 0.0 || R->p_off == 0.0) return R->p_off;
+    if (R->slip_a == 0.0 || p_off == 0.0) return p_off;
     double U = orc_dyn_energy(P, R->bond_type, r);
     double x;
-    if (P->kT > 0.0) x = U / P->kT;
+    if (T > 0.0) x = U / T;
     else x = (U > 0.0) ? INFINITY : 0.0;
     double e = R->slip_a * sqrt(x);
     if (!(e < 700.0)) return 1.0;
-    double p = R->p_off * orc_exp(e);
+    double p = p_off * orc_exp(e);
     return p < 1.0 ? p : 1.0;
 }
 
@@ -519,11 +554,18 @@ int orc_sweep(const orc_params *P, orc_state *S, int64_t step, orc_sweep_stats *
     if (tr && tr->order)
         for (int a = 0; a < P->nrx; ++a) tr->order[a] = order[a];
 
+    /* the temperature of this sweep (Sec. II.B): kinetic, from the velocities
+     * as the sweep begins, or the set-point; with the kinetic temperature a
+     * melting switch is re-evaluated at it */
+    double T = P->kinetic_T ? orc_kinetic_T(P, S) : P->kT;
+
     for (int slot = 0; slot < P->nrx; ++slot) {
         int32_t a = order[slot];
         const orc_reaction *R = &P->rx[a];
         double rmin2 = R->r_min * R->r_min, rmax2 = R->r_max * R->r_max;
         double r0 = orc_rest_length(P, R->bond_type);
+        double p_on0 = R->p_on0, p_off0 = R->p_off;
+        if (P->kinetic_T && R->melt) orc_melt_rates(P, R, T, &p_on0, &p_off0);
 
         /* (a) proposal — occupancies as they stand when the reaction begins */
         for (int64_t i = 0; i < n; ++i) {
@@ -576,7 +618,7 @@ int orc_sweep(const orc_params *P, orc_state *S, int64_t step, orc_sweep_stats *
             if (tr && slot == 0 && tr->matched) { tr->matched[i] = (int32_t)j; tr->matched[j] = (int32_t)i; }
             orc_pair_draw(P, a, ORC_FORM, step, lo, hi, w);
             double u = orc_u53(w[0], w[1]);
-            double pon = orc_p_on(P, R, prop_r[i]);
+            double pon = orc_p_on(P, R, prop_r[i], T, p_on0);
             if (u < pon) {
                 fpart[i] = (int32_t)j;
                 fpart[j] = (int32_t)i;
@@ -600,10 +642,10 @@ int orc_sweep(const orc_params *P, orc_state *S, int64_t step, orc_sweep_stats *
                 local.break_tested++;
                 uint32_t w[4];
                 orc_pair_draw(P, a, ORC_BREAK, step, i, j, w);
-                double p_off = R->p_off;
+                double p_off = p_off0;
                 if (R->slip_a != 0.0) {
                     double dx, dy, dz;
-                    p_off = orc_p_off(P, R, sqrt(orc_dist2(P, S, i, j, &dx, &dy, &dz)));
+                    p_off = orc_p_off(P, R, sqrt(orc_dist2(P, S, i, j, &dx, &dy, &dz)), T, p_off0);
                 }
                 if (orc_u53(w[0], w[1]) < p_off) brk[i * ORC_VMAX + s] = 1;
             }

@@ -36,6 +36,10 @@ typedef struct {
     double p_on0, p_off;       /* per-sweep probabilities, Eq. (2) */
     int32_t self_avoid;        /* 1: sites of one molecule (orc_state.mol) do not react with each other */
     double slip_a;             /* slip bond, Eq. (slip): P_off(r) = p_off exp(a sqrt(U_b(r)/kT)); 0: off */
+    int32_t melt;              /* 1: melting switch, Eqs. (gT)-(kT), re-evaluated every sweep at the
+                                * kinetic temperature (orc_params.kinetic_T); p_on0/p_off above hold
+                                * the set-point rates used otherwise */
+    double melt_lambda, melt_t, kon_init, koff_init, kon_melt, koff_melt;
 } orc_reaction;
 
 typedef struct {
@@ -54,6 +58,9 @@ typedef struct {
     int32_t nrx;
     orc_reaction rx[ORC_MAX_RX];
     int32_t bond_period;
+    int32_t kinetic_T;         /* 1: T in Eq. (3), the slip factor and g(T) is the instantaneous kinetic
+                                * temperature of the half-step velocities (orc_kinetic_T), evaluated at
+                                * the start of every sweep; 0: the set-point kT */
 } orc_params;
 
 typedef struct {
@@ -109,6 +116,15 @@ double orc_u53(uint32_t w0, uint32_t w1);
 /* exp(x) by Cody–Waite ln2 reduction and a degree-13 Taylor polynomial. */
 double orc_exp(double x);
 double orc_log(double x);
+/* Instantaneous kinetic temperature of the half-step velocities (Sec. II.B: T
+ * is the kinetic temperature when the updater triggers), summed
+ * deterministically: every particle's v^2 = (vx^2 + vy^2) + vz^2 is rounded to
+ * the nearest multiple of 2^-32 and the integers are added exactly in int64;
+ * T = sum 2^-32 / (3 n) (3 n degrees of freedom: the Langevin thermostat
+ * conserves no momentum).  Exact for any summation order. */
+double orc_kinetic_T(const orc_params *P, const orc_state *S);
+/* tanh(x) = (1 - e^{-2|x|}) / (1 + e^{-2|x|}) with the sign of x, with orc_exp. */
+double orc_tanh(double x);
 /* Bond energy U_b(r) of bond type bt. */
 double orc_bond_energy(const orc_params *P, int32_t bt, double r);
 

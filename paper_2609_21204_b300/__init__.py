@@ -219,6 +219,12 @@ class Snap:
     def step(self, nsteps=1):
         self._check(self._lib.snap_step(self._ctx, int(nsteps)))
 
+    def set_kinetic_temperature(self, on=True):
+        """Use the instantaneous kinetic temperature (deterministic fixed-point
+        sum over the half-step velocities) in every sweep instead of the
+        set-point kT (Sec. II.B)."""
+        self._check(self._lib.snap_set_kinetic_temperature(self._ctx, 1 if on else 0))
+
     def set_retry_limit(self, limit):
         """Retry limit of the push-mode compare-and-swap loop (default 65536);
         reaching it makes the step return SNAP_ERR_TIMEOUT without taking it."""
@@ -495,6 +501,8 @@ def from_system(sysdef, precision="mixed", p_on0=1.0, skin=None, **kw) -> Snap:
             sim.set_slip(a, r.slip_a)
         if getattr(r, "melt", None) is not None:
             sim.set_melting(a, *r.melt)
+    if getattr(s0, "kinetic_T", 0):
+        sim.set_kinetic_temperature(True)
     pos = np.concatenate([s.pos for s in systems])
     vel = np.concatenate([s.vel for s in systems])
     types = np.concatenate([s.types for s in systems])

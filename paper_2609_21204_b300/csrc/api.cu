@@ -25,6 +25,7 @@ struct RxHost {
     int self_avoid;
     double slip_a = 0.0;    // slip-bond modifier, Eq. (slip)
     bool melting = false;   // rates from the melting switch, Eqs. (gT)-(kT)
+    double melt[6] = {0, 0, 0, 0, 0, 0};   // lambda, T_melt, k_on^init, k_off^init, k_on^melt, k_off^melt
 };
 
 struct RepHost {
@@ -92,6 +93,7 @@ struct snap_ctx {
     int nbr_cap = 0;
     int rnbr_cap = 0;
     int cas_cap = 1 << 16;           // push-mode compare-and-swap retries (snap_set_retry_limit)
+    int kinetic_T = 0;               // sweep temperature: 0 set-point, 1 kinetic (snap_set_kinetic_temperature)
 };
 
 namespace {
@@ -186,6 +188,7 @@ snap_status upload_reps(snap_ctx *c)
         D.tag_off = R.tag_off;
         D.n = R.n;
         D.kT = R.kT;
+        D.t_sweep = R.kT;
         D.noise_c = std::sqrt(((2.0 * c->cfg.gamma) * R.kT) / c->cfg.dt);
         D.key0 = (uint32_t)(R.seed & 0xFFFFFFFFull);
         D.key1hi = (uint32_t)(((R.seed >> 32) & 0xFFFFull) << 16);
@@ -274,6 +277,18 @@ void fill_params(snap_ctx *c)
     P.pdist_rows = std::max<int64_t>(c->n, 1) / 5 + 1;
     P.has_static = c->n_static > 0 ? 1 : 0;   // push mode needs a side 4x scarcer: <= n / 5 sites
     P.cas_cap = c->cas_cap;
+    P.kinetic_T = c->kinetic_T;
+    P.period_dt = (double)c->cfg.bond_period * c->cfg.dt;
+    for (size_t a = 0; a < c->rx.size(); ++a) {
+        if (!c->rx[a].melting) continue;
+        P.melt_mask |= 1 << a;
+        P.melt_lambda[a] = c->rx[a].melt[0];
+        P.melt_t[a] = c->rx[a].melt[1];
+        P.kon_init[a] = c->rx[a].melt[2];
+        P.koff_init[a] = c->rx[a].melt[3];
+        P.kon_melt[a] = c->rx[a].melt[4];
+        P.koff_melt[a] = c->rx[a].melt[5];
+    }
 }
 
 // everything that depends on the model (cut-offs -> cell grids -> capacities)
@@ -951,14 +966,14 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
               alloc_arr(c, A.site_list, n) && alloc_arr(c, A.list_count, 1) &&
               alloc_arr(c, A.cont, n * kContenders) && alloc_arr(c, A.ncont, n) &&
               alloc_arr(c, A.life_hist, (size_t)c->cfg.lifetime_bins) && alloc_arr(c, A.e_part, 4 * n) &&
-              alloc_arr(c, c->d_red, 8);
+              alloc_arr(c, A.ksum, (size_t)nrep) && alloc_arr(c, c->d_red, 8);
     c->d_reps = static_cast<RepDev *>(dalloc(c, sizeof(RepDev) * nrep));
     if (!ok || !c->d_reps) return bail(SNAP_ERR_OOM, "work arrays");
     A.reps = c->d_reps;
     // B shares the non-permuted arrays with A
     DevArrays &B = c->B;
     B.rtag = A.rtag; B.ref4 = A.ref4; B.force = A.force; B.status = A.status; B.need_rebuild = A.need_rebuild;
-    B.step = A.step; B.reps = A.reps; B.order = A.order;
+    B.step = A.step; B.reps = A.reps; B.order = A.order; B.ksum = A.ksum;
     if (cudaMemsetAsync(A.status, 0, 4, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.step, 0, 8, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.need_rebuild, 0, 4, c->stream) != cudaSuccess ||
@@ -972,6 +987,7 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
         cudaMemsetAsync(A.brk, 0, sizeof(uint32_t) * n, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.best, 0, sizeof(unsigned long long) * n, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.life_hist, 0, sizeof(unsigned long long) * c->cfg.lifetime_bins, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.ksum, 0, sizeof(unsigned long long) * nrep, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {
         cudaGetLastError();
         return bail(SNAP_ERR_CUDA, "init memset");
@@ -1145,7 +1161,12 @@ extern "C" snap_status snap_set_melting(snap_ctx *c, int32_t a, double lambda, d
     c->rx[a].pon = pon[0];
     c->rx[a].poff = poff[0];
     c->rx[a].melting = true;
-    if (c->ready) return upload_reps(c);
+    for (int k = 0; k < 6; ++k) c->rx[a].melt[k] = v[k];
+    if (c->ready) {
+        fill_params(c);       // the switch's parameters, for the kinetic temperature
+        c->graph_dirty = true;
+        return upload_reps(c);
+    }
     return SNAP_OK;
 }
 
@@ -1300,6 +1321,20 @@ extern "C" snap_status snap_step(snap_ctx *c, int64_t nsteps)
             set_need_rebuild(c);
             return code;
         }
+    }
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_set_kinetic_temperature(snap_ctx *c, int32_t on)
+{
+    if (!c) return SNAP_ERR_ARG;
+    if (on != 0 && on != 1) return fail(c, SNAP_ERR_ARG, "on must be 0 or 1");
+    if (on && c->mh_mode) return fail(c, SNAP_ERR_STATE, "Metropolis-Hastings mode uses the set-point temperature");
+    c->kinetic_T = on;
+    c->graph_dirty = true;
+    if (c->ready) {
+        fill_params(c);
+        return upload_reps(c);   // set-point rates back in place (the kinetic sweeps overwrite melting rates)
     }
     return SNAP_OK;
 }
@@ -1769,6 +1804,8 @@ extern "C" snap_status snap_set_mh(snap_ctx *c, int32_t mode, const snap_mlp *ml
             return fail(c, SNAP_ERR_ARG, "Metropolis-Hastings mode does not support the slip bond");
         if (c->bkind[c->rx[0].bt] != SNAP_HARMONIC)
             return fail(c, SNAP_ERR_ARG, "Metropolis-Hastings mode needs a harmonic bond type");
+        if (c->kinetic_T)
+            return fail(c, SNAP_ERR_STATE, "Metropolis-Hastings mode uses the set-point temperature");
         const double side = 2.0 * c->rx[0].rmax + 0.05;
         int nc[3];
         for (int d = 0; d < 3; ++d) {

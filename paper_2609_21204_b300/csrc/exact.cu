@@ -97,7 +97,30 @@ __global__ void k_sweep_begin(DevParams P, DevArrays A)
         }
     }
     if (r >= P.nrep) return;
-    const RepDev &R = A.reps[r];
+    RepDev &R = A.reps[r];
+    // the temperature of this sweep (Sec. II.B): the set-point, or the kinetic
+    // temperature from the fixed-point sum k_kin_sum left, with the melting
+    // switch re-evaluated at it
+    double T = R.kT;
+    if (P.kinetic_T) {
+        const unsigned long long q = A.ksum[r];
+        A.ksum[r] = 0ull;
+        T = __ddiv_rn(__dmul_rn(__ll2double_rn((long long)q), 0x1.0p-32), (double)(3 * R.n));
+        for (int a = 0; a < P.nrx; ++a) {
+            if (!((P.melt_mask >> a) & 1)) continue;
+            const double g = __dmul_rn(0.5, __dadd_rn(tanh_cw(__dmul_rn(P.melt_lambda[a], __dsub_rn(T, P.melt_t[a]))),
+                                                      1.0));
+            const double kon = __dadd_rn(__dmul_rn(P.kon_init[a], __dsub_rn(1.0, g)), __dmul_rn(P.kon_melt[a], g));
+            const double koff = __dadd_rn(__dmul_rn(P.koff_init[a], __dsub_rn(1.0, g)), __dmul_rn(P.koff_melt[a], g));
+            double pon = __dmul_rn(kon, P.period_dt), poff = __dmul_rn(koff, P.period_dt);
+            pon = pon < 1.0 ? pon : 1.0;
+            poff = poff < 1.0 ? poff : 1.0;
+            R.p_on0[a] = pon;
+            R.p_off[a] = poff;
+            R.off_thresh[a] = (unsigned long long)ceil(__dmul_rn(poff, 0x1.0p53));
+        }
+    }
+    R.t_sweep = T;
     int ord[kMaxRx];
     for (int a = 0; a < P.nrx; ++a) ord[a] = a;
     for (int k = P.nrx - 1; k >= 1; --k) {
@@ -108,6 +131,42 @@ __global__ void k_sweep_begin(DevParams P, DevArrays A)
         ord[j] = t;
     }
     for (int a = 0; a < kMaxRx; ++a) A.rx_order[r * kMaxRx + a] = a < P.nrx ? ord[a] : 0;
+}
+
+// Kinetic temperature of the half-step velocities (Sec. II.B), summed
+// deterministically: each particle's v^2 = (vx^2 + vy^2) + vz^2 in FP64 is
+// rounded to the nearest multiple of 2^-32 and the integers are added exactly
+// (64-bit integer atomics: any order gives the same sum).  k_sweep_begin turns
+// the sum into T = sum 2^-32 / (3 n) and clears it.
+template <bool FORCED>
+__global__ void k_kin_sum(DevParams P, DevArrays A)
+{
+    long long step;
+    if (!sweep_active<FORCED>(P, A, step)) return;
+    const long long i = gtid();
+    unsigned long long q = 0ull;
+    int rp = 0;
+    if (i < P.n) {
+        rp = rep_of(P, A, i);
+        double vx, vy, vz;
+        if (P.screen) {
+            const float4 v = A.v4[i];
+            vx = v.x; vy = v.y; vz = v.z;
+        } else {
+            vx = A.vx[i]; vy = A.vy[i]; vz = A.vz[i];
+        }
+        const double v2 = __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz));
+        q = (unsigned long long)__double2ll_rn(__dmul_rn(v2, 0x1.0p32));
+    }
+    // one atomic per warp when the warp holds one replica, else per lane
+    const int rp0 = __shfl_sync(0xFFFFFFFFu, rp, 0);
+    if (__all_sync(0xFFFFFFFFu, rp == rp0)) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
+        if ((threadIdx.x & 31) == 0 && q) atomicAdd(&A.ksum[rp0], q);
+    } else if (q) {
+        atomicAdd(&A.ksum[rp], q);
+    }
 }
 
 // exact FP64 squared separation, as the definition states it:
@@ -625,7 +684,7 @@ __device__ __forceinline__ void break_particle(const DevParams &P, DevArrays &A,
         bool brk;
         if (SLIP) {
             const int bt = P.rx_bt[a];
-            const double pr = slip_p_off(R.p_off[a], P.bk[bt], P.br0[bt], R.kT, P.rx_slip[a],
+            const double pr = slip_p_off(R.p_off[a], P.bk[bt], P.br0[bt], R.t_sweep, P.rx_slip[a],
                                          __dsqrt_rn(exact_r2(A, R, (int)i, j)));
             brk = (double)m < __dmul_rn(pr, 0x1p53);
         } else {
@@ -737,7 +796,7 @@ __global__ void k_accept(DevParams P, DevArrays A, int slot)
                     const double d = A.prop[c] == j ? A.prop_d[c] : A.prop_d[j];
                     const double U = dyn_bond_u(P, P.rx_bt[a], d);
                     double pon;
-                    if (R.kT > 0.0) pon = __dmul_rn(R.p_on0[a], exp_cw(-__ddiv_rn(U, R.kT)));
+                    if (R.t_sweep > 0.0) pon = __dmul_rn(R.p_on0[a], exp_cw(-__ddiv_rn(U, R.t_sweep)));
                     else pon = (U <= 0.0) ? R.p_on0[a] : 0.0;
                     if (u < pon) {
                         ++formed;
@@ -768,8 +827,8 @@ __global__ void k_accept(DevParams P, DevArrays A, int slot)
                     const double u = u53(w.x, w.y);
                     const double U = dyn_bond_u(P, P.rx_bt[a], A.prop_d[i]);
                     double pon;
-                    if (R.kT > 0.0) {
-                        const double e = __ddiv_rn(U, R.kT);
+                    if (R.t_sweep > 0.0) {
+                        const double e = __ddiv_rn(U, R.t_sweep);
                         pon = __dmul_rn(R.p_on0[a], exp_cw(-e));
                     } else {
                         pon = (U <= 0.0) ? R.p_on0[a] : 0.0;
@@ -828,6 +887,7 @@ inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block 
 template <bool FORCED>
 void sweep_begin(const DevParams &P, const DevArrays &A, Launch L)
 {
+    if (P.kinetic_T && P.n > 0) k_kin_sum<FORCED><<<grid_for(P.n, 256), 256, 0, L.stream>>>(P, A);
     k_sweep_begin<FORCED><<<grid_for(std::max<long long>(P.n, P.nrep), kSweepBeginBlock), kSweepBeginBlock, 0,
                             L.stream>>>(P, A);
 }

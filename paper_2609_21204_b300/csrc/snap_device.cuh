@@ -68,6 +68,12 @@ struct DevParams {
     int64_t pdist_rows;     // pushing sites whose pair distances fit the pdist scratch
     int32_t has_static;     // any static bonds (else their slots are neither gathered nor read)
     int32_t cas_cap;        // retries of the push-mode 16-byte compare-and-swap before SNAP_ERR_TIMEOUT
+    // kinetic temperature (Sec. II.B) and the melting switch re-evaluated at it (Eqs. gT-kT)
+    int32_t kinetic_T;      // 1: T of the sweep is the kinetic temperature of the half-step velocities
+    int32_t melt_mask;      // bit a set: reaction a has the melting switch
+    double period_dt;       // n dt of Eq. 2
+    double melt_lambda[kMaxRx], melt_t[kMaxRx];
+    double kon_init[kMaxRx], koff_init[kMaxRx], kon_melt[kMaxRx], koff_melt[kMaxRx];
 };
 
 struct RepDev {
@@ -79,6 +85,7 @@ struct RepDev {
     int32_t pad0;
     int64_t tag_off, n;
     double kT, noise_c;     // set-point kT and sqrt(2 gamma kT / dt)
+    double t_sweep;         // T of the current sweep: kT, or the kinetic temperature (k_sweep_begin)
     uint32_t key0, key1hi;  // Philox key words derived from the seed
     double p_on0[kMaxRx], p_off[kMaxRx];
     unsigned long long off_thresh[kMaxRx];   // ceil(p_off * 2^53): break iff 53-bit draw < this
@@ -133,7 +140,8 @@ struct DevArrays {
     unsigned long long *counters;   // sweep counters, see Counter
     unsigned long long *life_hist;
     double *e_part;                 // per-particle energy scratch
-    const RepDev *reps;
+    RepDev *reps;                   // per replica; k_sweep_begin updates t_sweep (and melting rates)
+    unsigned long long *ksum;       // per replica: fixed-point sum of v^2 (2^-32 units) for the kinetic T
     // Metropolis–Hastings mode (single system)
     int32_t *mh_key, *mh_count, *mh_start, *mh_cursor, *mh_order, *mh_bsum, *mh_gate;
     int32_t *mv_type, *mv_i, *mv_j, *mv_n, *mv_b, *mv_c, *mv_cand;   // per move (active cell)
@@ -237,6 +245,17 @@ __device__ __forceinline__ double exp_cw(double x)
     const int ki = (int)k;
     const int h = ki / 2;
     return __dmul_rn(__dmul_rn(s, pow2_exact(h)), pow2_exact(ki - h));
+}
+
+// tanh(x) = (1 - e^{-2|x|}) / (1 + e^{-2|x|}) with the sign of x, on exp_cw:
+// correctly rounded operations only, so it is reproducible bit for bit (the
+// melting switch g(T) of Eq. gT at the kinetic temperature).
+__device__ __forceinline__ double tanh_cw(double x)
+{
+    const double ax = fabs(x);
+    const double e = exp_cw(__dmul_rn(-2.0, ax));
+    const double t = __ddiv_rn(__dsub_rn(1.0, e), __dadd_rn(1.0, e));
+    return x < 0.0 ? -t : t;
 }
 
 // ------------------------------------------------------------ log

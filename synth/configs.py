@@ -63,6 +63,7 @@ class System:
     dt: float = 0.005
     seed: int = 20260921
     bond_period: int = 1
+    kinetic_T: int = 0      # 1: the sweep uses the instantaneous kinetic temperature (Sec. II.B)
     skin: float = 0.3
     meta: dict = field(default_factory=dict)
 
