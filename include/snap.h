@@ -59,13 +59,13 @@ typedef enum {
     SNAP_ERR_CUDA = 3,           /* a CUDA runtime call failed */
     SNAP_ERR_OOM = 4,            /* device allocation failed */
     SNAP_ERR_NLIST_OVERFLOW = 5, /* neighbour capacity exceeded (grown and retried internally) */
-    SNAP_ERR_FENE_OVERSTRETCH = 6,
+    SNAP_ERR_FENE_OVERSTRETCH = 6, /* a bond outside its potential's finite range (FENE, FENEWCA, Tether) */
     SNAP_ERR_NONFINITE = 7,      /* a position became NaN/Inf */
     SNAP_ERR_TIMEOUT = 8
 } snap_status;
 
 enum { SNAP_FP64 = 0, SNAP_MIXED = 1 };     /* precision modes */
-enum { SNAP_HARMONIC = 0, SNAP_FENE = 1 };  /* bond kinds */
+enum { SNAP_HARMONIC = 0, SNAP_FENE = 1, SNAP_FENEWCA = 2, SNAP_TETHER = 3 };  /* bond kinds */
 
 #define SNAP_MAX_TYPES 8
 #define SNAP_MAX_BOND_TYPES 8
@@ -146,9 +146,33 @@ snap_status snap_set_valence(snap_ctx *, const int32_t *valence);
 
 /* Bond type bt: SNAP_HARMONIC U = k/2 (r - r0)^2, or SNAP_FENE
  * U = -k R0^2/2 ln(1 - (r/R0)^2) with r0_or_R0 = R0.  Either kind may be a
- * static bond or the bond type of a reaction (snap_add_reaction). */
+ * static bond or the bond type of a reaction (snap_add_reaction).  The other
+ * kinds take snap_set_bond_params_ex (SNAP_ERR_ARG here). */
 snap_status snap_set_bond_params(snap_ctx *, int32_t bt, int32_t kind, double k,
                                  double r0_or_R0);
+
+/* Bond type bt of any kind (Sec. II.B: the updater accepts the harmonic,
+ * FENEWCA and Tether evaluators of HOOMD-blue; the potentials below are those
+ * of HOOMD-blue's documentation), params[nparams] host doubles:
+ *   SNAP_HARMONIC (2): k, r0            U = k/2 (r - r0)^2
+ *   SNAP_FENE     (2): k, R0            U = -k R0^2/2 ln(1 - (r/R0)^2)
+ *   SNAP_FENEWCA  (5): k, R0, eps, sigma, delta; with s = r - delta,
+ *       U = -k R0^2/2 ln(1 - (s/R0)^2) + 4 eps [(sigma/s)^12 - (sigma/s)^6] + eps
+ *       (the WCA bracket for s < 2^(1/6) sigma only)
+ *   SNAP_TETHER   (5): k_b, l_min, l_c1, l_c0, l_max,
+ *       U = k_b e^{1/(l_c0 - r)} / (l_max - r) for r > l_c0, plus
+ *           k_b e^{1/(r - l_c1)} / (r - l_min) for r < l_c1, 0 in between.
+ * Requirements: finite values; k >= 0 and R0 (l_min) > 0; FENEWCA eps >= 0,
+ * sigma > 0, delta >= 0; Tether l_min < l_c1 < l_c0 < l_max; else
+ * SNAP_ERR_ARG.  A bond outside the finite range of its potential (FENE and
+ * FENEWCA at s >= R0 or s <= 0, Tether at r <= l_min or r >= l_max) latches
+ * SNAP_ERR_FENE_OVERSTRETCH in force evaluations and is never formed by a
+ * reaction (U_b = +inf in Eq. 3).  A proposal aims at the minimum of the
+ * energy: r0 (harmonic), 0 (FENE), delta + s* with s* the root of dU/ds below
+ * min(2^(1/6) sigma, R0) (FENEWCA; delta when eps = 0), (l_c1 + l_c0)/2, the
+ * middle of the zero-energy interval (Tether). */
+snap_status snap_set_bond_params_ex(snap_ctx *, int32_t bt, int32_t kind, const double *params,
+                                    int32_t nparams);
 
 /* Static bonds: nb tag pairs (2*nb ints) of bond type bt; at most
  * SNAP_MAX_STATIC per particle.  Never change during the run. */

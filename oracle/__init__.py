@@ -26,7 +26,7 @@ MAX_BTYPES = 8
 MAX_RX = 8
 VMAX = 4
 SMAX = 4
-HARMONIC, FENE = 0, 1
+HARMONIC, FENE, FENEWCA, TETHER = 0, 1, 2, 3
 FORM, BREAK, MATCH, ORDER, LANGEVIN = 1, 2, 3, 4, 5
 
 
@@ -58,7 +58,8 @@ class Params(C.Structure):
                 ("rcut", C.c_double * (MAX_TYPES * MAX_TYPES)),
                 ("valence", C.c_int32 * MAX_TYPES), ("nbtypes", C.c_int32),
                 ("bkind", C.c_int32 * MAX_BTYPES), ("bk", C.c_double * MAX_BTYPES),
-                ("br0", C.c_double * MAX_BTYPES), ("nrx", C.c_int32),
+                ("br0", C.c_double * MAX_BTYPES), ("bx", (C.c_double * 3) * MAX_BTYPES),
+                ("nrx", C.c_int32),
                 ("rx", Reaction * MAX_RX), ("bond_period", C.c_int32), ("kinetic_T", C.c_int32)]
 
 
@@ -111,6 +112,8 @@ def lib():
         _lib.orc_log.restype = C.c_double
         _lib.orc_bond_energy.argtypes = [C.POINTER(Params), C.c_int32, C.c_double]
         _lib.orc_bond_energy.restype = C.c_double
+        _lib.orc_aim_separation.argtypes = [C.POINTER(Params), C.c_int32]
+        _lib.orc_aim_separation.restype = C.c_double
         _lib.orc_sweep.argtypes = [C.POINTER(Params), C.POINTER(State), C.c_int64,
                                    C.POINTER(SweepStats), C.c_void_p]
         _lib.orc_forces.argtypes = [C.POINTER(Params), C.POINTER(State), C.c_void_p,
@@ -209,6 +212,8 @@ class OracleSystem:
         P.nbtypes = len(s.bond_types)
         for i, bt in enumerate(s.bond_types):
             P.bkind[i], P.bk[i], P.br0[i] = int(bt.kind), float(bt.k), float(bt.r0)
+            for q, v in enumerate(getattr(bt, "extra", ()) or ()):
+                P.bx[i][q] = float(v)
         P.nrx = len(s.reactions)
         for i, r in enumerate(s.reactions):
             if getattr(r, "melt", None) is not None:
@@ -384,3 +389,6 @@ class OracleSystem:
 
     def bond_energy(self, bond_type, r):
         return lib().orc_bond_energy(C.byref(self.params), int(bond_type), float(r))
+
+    def aim_separation(self, bond_type):
+        return lib().orc_aim_separation(C.byref(self.params), int(bond_type))

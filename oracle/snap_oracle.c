@@ -202,17 +202,70 @@ double orc_log(double x)
 
 /* ------------------------------------------------------- bond energies */
 
-double orc_bond_energy(const orc_params *P, int32_t bt, double r)
+/* FENEWCA and Tether: the bond potentials HOOMD-blue documents under those
+ * names, which Sec. II.B names as evaluators the updater accepts.
+ *   FENEWCA (k, R0, eps, sigma, delta), s = r - delta:
+ *     U = -k R0^2/2 ln(1 - (s/R0)^2) + [4 eps ((sigma/s)^12 - (sigma/s)^6) + eps] for s < 2^(1/6) sigma
+ *   Tether (k_b, l_min, l_c1, l_c0, l_max):
+ *     U = k_b e^{1/(l_c0 - r)} / (l_max - r) for r > l_c0 and k_b e^{1/(r - l_c1)} / (r - l_min)
+ *     for r < l_c1, 0 in between.
+ * U, dU/dr and d2U/dr2 with libm; returns ORC_ERR_FENE outside the finite
+ * range (s <= 0 or s >= R0; r <= l_min or r >= l_max). */
+static const double ORC_TWO_SIXTH = 0x1.1f59ac3c7d6c0p+0;   /* 2^(1/6) */
+
+static int orc_bond_terms(const orc_params *P, int32_t bt, double r, double *U, double *dU, double *d2U)
 {
     double k = P->bk[bt], r0 = P->br0[bt];
-    if (P->bkind[bt] == ORC_HARMONIC) {
-        double dr = r - r0;
-        return 0.5 * k * dr * dr;
+    int kind = P->bkind[bt];
+    *U = *dU = *d2U = 0.0;
+    if (kind == ORC_HARMONIC) {
+        *U = 0.5 * k * (r - r0) * (r - r0);
+        *dU = k * (r - r0);
+        *d2U = k;
+        return ORC_OK;
     }
-    /* FENE: -1/2 k R0^2 ln(1 - (r/R0)^2) */
-    double q = (r * r) / (r0 * r0);
-    if (q >= 1.0) return INFINITY;
-    return -0.5 * k * r0 * r0 * log(1.0 - q);
+    if (kind == ORC_FENE || kind == ORC_FENEWCA) {
+        double s = kind == ORC_FENE ? r : r - P->bx[bt][2];
+        double q = (s * s) / (r0 * r0);
+        if (q >= 1.0 || (kind == ORC_FENEWCA && s <= 0.0)) return ORC_ERR_FENE;
+        *U = -0.5 * k * r0 * r0 * log(1.0 - q);
+        *dU = k * s / (1.0 - q);
+        *d2U = k * (1.0 + q) / ((1.0 - q) * (1.0 - q));
+        if (kind == ORC_FENEWCA) {
+            double eps = P->bx[bt][0], sig = P->bx[bt][1];
+            if (s < sig * ORC_TWO_SIXTH) {
+                double sr6 = pow(sig / s, 6.0), sr12 = sr6 * sr6;
+                *U += 4.0 * eps * (sr12 - sr6) + eps;
+                *dU -= 24.0 * eps * (2.0 * sr12 - sr6) / s;
+                *d2U += 24.0 * eps * (26.0 * sr12 - 7.0 * sr6) / (s * s);
+            }
+        }
+        return ORC_OK;
+    }
+    /* Tether */
+    double lmin = r0, lc1 = P->bx[bt][0], lc0 = P->bx[bt][1], lmax = P->bx[bt][2];
+    if (r <= lmin || r >= lmax) return ORC_ERR_FENE;
+    if (r > lc0) {
+        double a = lc0 - r, b = lmax - r;
+        double h = 1.0 / (a * a) + 1.0 / b;
+        *U = k * exp(1.0 / a) / b;
+        *dU = *U * h;
+        *d2U = *dU * h + *U * (2.0 / (a * a * a) + 1.0 / (b * b));
+    } else if (r < lc1) {
+        double c = r - lc1, e = r - lmin;
+        double h = 1.0 / (c * c) + 1.0 / e;
+        *U = k * exp(1.0 / c) / e;
+        *dU = -*U * h;
+        *d2U = -*dU * h + *U * (2.0 / (c * c * c) + 1.0 / (e * e));
+    }
+    return ORC_OK;
+}
+
+double orc_bond_energy(const orc_params *P, int32_t bt, double r)
+{
+    double U, dU, d2U;
+    if (orc_bond_terms(P, bt, r, &U, &dU, &d2U) != ORC_OK) return INFINITY;
+    return U;
 }
 
 /* U_b of a dynamic bond for Eq. (3): harmonic 1/2 k (r - r0)^2, or FENE
@@ -220,21 +273,73 @@ double orc_bond_energy(const orc_params *P, int32_t bt, double r)
 static double orc_dyn_energy(const orc_params *P, int32_t bt, double r)
 {
     double k = P->bk[bt], r0 = P->br0[bt];
-    if (P->bkind[bt] == ORC_HARMONIC) {
+    int kind = P->bkind[bt];
+    if (kind == ORC_HARMONIC) {
         double dr = r - r0;
         return 0.5 * k * dr * dr;
     }
-    double q = (r * r) / (r0 * r0);
-    if (!(q < 1.0)) return INFINITY;
-    return -0.5 * k * r0 * r0 * orc_log(1.0 - q);
+    if (kind == ORC_FENE) {
+        double q = (r * r) / (r0 * r0);
+        if (!(q < 1.0)) return INFINITY;
+        return -0.5 * k * r0 * r0 * orc_log(1.0 - q);
+    }
+    if (kind == ORC_FENEWCA) {
+        double eps = P->bx[bt][0], sig = P->bx[bt][1];
+        double s = r - P->bx[bt][2];
+        double q = (s * s) / (r0 * r0);
+        if (!(q < 1.0) || !(s > 0.0)) return INFINITY;
+        double U = -0.5 * k * r0 * r0 * orc_log(1.0 - q);
+        if (s < sig * ORC_TWO_SIXTH) {
+            double sr2 = (sig * sig) / (s * s);
+            double sr6 = (sr2 * sr2) * sr2;
+            U = U + (4.0 * eps * (sr6 * sr6 - sr6) + eps);
+        }
+        return U;
+    }
+    /* Tether */
+    double lmin = r0, lc1 = P->bx[bt][0], lc0 = P->bx[bt][1], lmax = P->bx[bt][2];
+    if (!(r > lmin) || !(r < lmax)) return INFINITY;
+    if (r > lc0) {
+        double a = lc0 - r, b = lmax - r;
+        return (k * orc_exp(1.0 / a)) / b;
+    }
+    if (r < lc1) {
+        double c = r - lc1, e = r - lmin;
+        return (k * orc_exp(1.0 / c)) / e;
+    }
+    return 0.0;
 }
 
-/* The separation a proposal aims at (Sec. II.C: |r - r0| is minimised): the
- * rest length of a harmonic bond; 0, the minimum of the FENE term, for FENE. */
+/* The separation a proposal aims at (Sec. II.C: |r - r0| is minimised, r0
+ * read from the bond potential), read as the minimum of the bond energy: the
+ * rest length (harmonic); 0 (FENE); for FENEWCA delta + s*, s* the root of
+ * dU/ds on (0, min(2^(1/6) sigma, R0)) by bisection to the last bit (delta when
+ * eps = 0); for Tether the middle of its zero-energy interval [l_c1, l_c0]. */
 static double orc_rest_length(const orc_params *P, int32_t bt)
 {
-    return P->bkind[bt] == ORC_HARMONIC ? P->br0[bt] : 0.0;
+    int kind = P->bkind[bt];
+    if (kind == ORC_HARMONIC) return P->br0[bt];
+    if (kind == ORC_FENE) return 0.0;
+    if (kind == ORC_TETHER) return 0.5 * (P->bx[bt][0] + P->bx[bt][1]);
+    double k = P->bk[bt], R0 = P->br0[bt], eps = P->bx[bt][0], sig = P->bx[bt][1], delta = P->bx[bt][2];
+    if (eps == 0.0) return delta;
+    double lo = 0.0, hi = sig * ORC_TWO_SIXTH;
+    if (R0 < hi) hi = R0;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        double q = (mid * mid) / (R0 * R0);
+        double f1 = (k * mid) / (1.0 - q);
+        double sr2 = (sig * sig) / (mid * mid);
+        double sr6 = (sr2 * sr2) * sr2;
+        double f2 = ((24.0 * eps) * ((2.0 * sr6) * sr6 - sr6)) / mid;
+        if (f1 - f2 > 0.0) hi = mid;
+        else lo = mid;
+    }
+    return delta + hi;
 }
+
+double orc_aim_separation(const orc_params *P, int32_t bt) { return orc_rest_length(P, bt); }
 
 /* Eq. (3): P_on(r) = P_on^0 exp(-U_b(r)/kT); at kT = 0 the factor is [U_b <= 0].
  * T is the sweep's temperature (set-point or kinetic) and p_on0 the sweep's rate. */
@@ -981,7 +1086,12 @@ static int orc_bond_pair(const orc_params *P, orc_state *S, int64_t i, int64_t j
     double r2 = orc_dist2(P, S, i, j, &dx, &dy, &dz);
     double k = P->bk[bt], r0 = P->br0[bt];
     double fb, u, g;   /* g = r |dF/dr| of the bond force F(r) = -dU/dr */
-    if (P->bkind[bt] == ORC_HARMONIC) {
+    if (P->bkind[bt] >= ORC_FENEWCA) {
+        double r = sqrt(r2), dU, d2U;
+        if (orc_bond_terms(P, bt, r, &u, &dU, &d2U) != ORC_OK) return ORC_ERR_FENE;
+        fb = dU / r;
+        g = r * fabs(d2U);
+    } else if (P->bkind[bt] == ORC_HARMONIC) {
         double r = sqrt(r2);
         fb = k * (r - r0) / r;       /* (dU/dr)/r, pulls i towards j when stretched */
         u = 0.5 * k * (r - r0) * (r - r0);

@@ -24,7 +24,7 @@ extern "C" {
 #define ORC_VMAX 4      /* dynamic-bond slots per particle */
 #define ORC_SMAX 4      /* static-bond slots per particle */
 
-enum { ORC_HARMONIC = 0, ORC_FENE = 1 };
+enum { ORC_HARMONIC = 0, ORC_FENE = 1, ORC_FENEWCA = 2, ORC_TETHER = 3 };
 /* Philox key streams (second key word carries (reaction << 8) | stream) */
 enum { ORC_FORM = 1, ORC_BREAK = 2, ORC_MATCH = 3, ORC_ORDER = 4, ORC_LANGEVIN = 5,
        ORC_MH_SEL = 6, ORC_MH_ACC = 7, ORC_MH_OWN = 8 };
@@ -54,7 +54,8 @@ typedef struct {
     int32_t valence[ORC_MAX_TYPES];
     int32_t nbtypes;
     int32_t bkind[ORC_MAX_BTYPES];
-    double bk[ORC_MAX_BTYPES], br0[ORC_MAX_BTYPES];
+    double bk[ORC_MAX_BTYPES], br0[ORC_MAX_BTYPES];   /* harmonic k, r0; FENE(WCA) k, R0; Tether k_b, l_min */
+    double bx[ORC_MAX_BTYPES][3];                      /* FENEWCA eps, sigma, delta; Tether l_c1, l_c0, l_max */
     int32_t nrx;
     orc_reaction rx[ORC_MAX_RX];
     int32_t bond_period;
@@ -125,8 +126,12 @@ double orc_log(double x);
 double orc_kinetic_T(const orc_params *P, const orc_state *S);
 /* tanh(x) = (1 - e^{-2|x|}) / (1 + e^{-2|x|}) with the sign of x, with orc_exp. */
 double orc_tanh(double x);
-/* Bond energy U_b(r) of bond type bt. */
+/* Bond energy U_b(r) of bond type bt (libm exp and log; +inf outside the
+ * potential's finite range). */
 double orc_bond_energy(const orc_params *P, int32_t bt, double r);
+/* The separation a proposal of a reaction with bond type bt aims at (the
+ * minimum of the bond energy; see the sweep). */
+double orc_aim_separation(const orc_params *P, int32_t bt);
 
 int orc_sweep(const orc_params *P, orc_state *S, int64_t step, orc_sweep_stats *st,
               orc_trace *tr);

@@ -166,8 +166,11 @@ class Snap:
         v = np.ascontiguousarray(valence, dtype=np.int32)
         self._check(self._lib.snap_set_valence(self._ctx, v.ctypes.data))
 
-    def set_bond_params(self, bt, kind, k, r0):
-        self._check(self._lib.snap_set_bond_params(self._ctx, int(bt), int(kind), float(k), float(r0)))
+    def set_bond_params(self, bt, kind, k, r0, extra=()):
+        """Bond type bt: harmonic (k, r0), FENE (k, R0), FENEWCA (k, R0, extra =
+        (eps, sigma, delta)) or Tether (k_b, l_min, extra = (l_c1, l_c0, l_max))."""
+        p = np.array([k, r0, *extra], dtype=np.float64)
+        self._check(self._lib.snap_set_bond_params_ex(self._ctx, int(bt), int(kind), p.ctypes.data, p.size))
 
     def add_static_bonds(self, pairs, bt):
         p = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
@@ -480,7 +483,7 @@ def from_system(sysdef, precision="mixed", p_on0=1.0, skin=None, **kw) -> Snap:
     sim.set_types(s0.sigma, s0.eps_pair, s0.rcut)
     sim.set_valence(s0.valence)
     for i, bt in enumerate(s0.bond_types):
-        sim.set_bond_params(i, bt.kind, bt.k, bt.r0)
+        sim.set_bond_params(i, bt.kind, bt.k, bt.r0, getattr(bt, "extra", ()) or ())
     off = 0
     for s in systems:
         if s.static_bonds.shape[0]:

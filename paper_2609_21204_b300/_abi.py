@@ -52,6 +52,7 @@ SIGNATURES = {
     "snap_set_types": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "snap_set_valence": (C.c_int, [_P, _P]),
     "snap_set_bond_params": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_double, C.c_double]),
+    "snap_set_bond_params_ex": (C.c_int, [_P, C.c_int32, C.c_int32, _P, C.c_int32]),
     "snap_add_static_bonds": (C.c_int, [_P, C.c_int64, _P, C.c_int32]),
     "snap_add_reaction": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
                                     C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_int32)]),

@@ -55,6 +55,7 @@ struct snap_ctx {
     int valence[kMaxTypes]{};
     int bkind[kMaxBondTypes]{};
     double bk[kMaxBondTypes]{}, br0[kMaxBondTypes]{};
+    double bx[kMaxBondTypes][3]{};   // FENEWCA: eps, sigma, delta; Tether: l_c1, l_c0, l_max
     bool bset[kMaxBondTypes]{};
     std::vector<RxHost> rx;
     std::vector<std::vector<double>> rep_pon, rep_poff;  // [reaction][replica]
@@ -207,6 +208,36 @@ snap_status upload_reps(snap_ctx *c)
     return SNAP_OK;
 }
 
+// The separation a proposal aims at (Sec. II.C: the partner minimising
+// |r - r0|, r0 read from the bond potential), read as the minimum of the bond
+// energy: r0 (harmonic); 0 (FENE); for FENEWCA delta + s*, s* the root of
+// dU/ds on (0, min(2^(1/6) sigma, R0)) found by bisection to the last bit (dU/ds
+// rises there from -inf; delta itself when eps = 0); for Tether, whose energy
+// is zero on [l_c1, l_c0], the middle of that interval.  The oracle computes
+// the same value with the same operations.
+double aim_separation(const snap_ctx *c, int bt)
+{
+    const int kind = c->bkind[bt];
+    if (kind == SNAP_HARMONIC) return c->br0[bt];
+    if (kind == SNAP_FENE) return 0.0;
+    if (kind == SNAP_TETHER) return 0.5 * (c->bx[bt][0] + c->bx[bt][1]);
+    const double k = c->bk[bt], R0 = c->br0[bt], eps = c->bx[bt][0], sig = c->bx[bt][1], delta = c->bx[bt][2];
+    if (eps == 0.0) return delta;
+    double lo = 0.0, hi = std::min(sig * kTwoSixth, R0);
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        const double q = (mid * mid) / (R0 * R0);
+        const double f1 = (k * mid) / (1.0 - q);
+        const double sr2 = (sig * sig) / (mid * mid);
+        const double sr6 = (sr2 * sr2) * sr2;
+        const double f2 = ((24.0 * eps) * ((2.0 * sr6) * sr6 - sr6)) / mid;
+        if (f1 - f2 > 0.0) hi = mid;
+        else lo = mid;
+    }
+    return delta + hi;
+}
+
 void fill_params(snap_ctx *c)
 {
     DevParams &P = c->P;
@@ -244,6 +275,10 @@ void fill_params(snap_ctx *c)
         P.br0[b] = c->br0[b];
         P.bkf[b] = (float)c->bk[b];
         P.br0f[b] = (float)c->br0[b];
+        for (int k = 0; k < 3; ++k) {
+            P.bx[b][k] = c->bx[b][k];
+            P.bxf[b][k] = (float)c->bx[b][k];
+        }
     }
     for (size_t a = 0; a < c->rx.size(); ++a) {
         P.rx_ta[a] = c->rx[a].ta;
@@ -251,8 +286,8 @@ void fill_params(snap_ctx *c)
         P.rx_bt[a] = c->rx[a].bt;
         P.rx_self[a] = c->rx[a].self_avoid;
         P.rx_slip[a] = c->rx[a].slip_a;
-        // proposals aim at the minimum of the bond term: r0 (harmonic), 0 (FENE)
-        P.rx_r0[a] = c->bkind[c->rx[a].bt] == SNAP_HARMONIC ? c->br0[c->rx[a].bt] : 0.0;
+        // proposals aim at the minimum of the bond energy
+        P.rx_r0[a] = aim_separation(c, c->rx[a].bt);
         if (c->rx[a].slip_a != 0.0) P.slip_mask |= 1 << a;
         P.rx_rmin2[a] = c->rx[a].rmin * c->rx[a].rmin;
         P.rx_rmax2[a] = c->rx[a].rmax * c->rx[a].rmax;
@@ -655,7 +690,9 @@ snap_status status_to_code(snap_ctx *c, uint32_t st)
 {
     if (st == 0) return SNAP_OK;
     if (st & kStNonfinite) return fail(c, SNAP_ERR_NONFINITE, "non-finite position");
-    if (st & kStFene) return fail(c, SNAP_ERR_FENE_OVERSTRETCH, "FENE bond stretched beyond R0");
+    if (st & kStFene)
+        return fail(c, SNAP_ERR_FENE_OVERSTRETCH,
+                    "a bond outside the finite range of its potential (FENE/FENEWCA beyond R0, Tether at l_min or l_max)");
     if (st & kStOverflow) return fail(c, SNAP_ERR_NLIST_OVERFLOW, "neighbour list overflow");
     if (st & kStTimeout) return fail(c, SNAP_ERR_TIMEOUT, "a bounded device retry loop gave up");
     return fail(c, SNAP_ERR_STATE, "unknown device status");
@@ -1037,25 +1074,49 @@ extern "C" snap_status snap_set_valence(snap_ctx *c, const int32_t *valence)
     return SNAP_OK;
 }
 
-extern "C" snap_status snap_set_bond_params(snap_ctx *c, int32_t bt, int32_t kind, double k, double r0)
+extern "C" snap_status snap_set_bond_params_ex(snap_ctx *c, int32_t bt, int32_t kind, const double *params,
+                                               int32_t nparams)
 {
     if (!c) return SNAP_ERR_ARG;
     if (bt < 0 || bt >= kMaxBondTypes) return fail(c, SNAP_ERR_ARG, "bond type out of range");
-    if (kind != SNAP_HARMONIC && kind != SNAP_FENE) return fail(c, SNAP_ERR_ARG, "unknown bond kind");
-    if (!(k >= 0.0) || !(r0 > 0.0) || !std::isfinite(k) || !std::isfinite(r0))
-        return fail(c, SNAP_ERR_ARG, "bond parameters must be finite, k >= 0, r0 > 0");
+    const int need = (kind == SNAP_HARMONIC || kind == SNAP_FENE) ? 2 : (kind == SNAP_FENEWCA || kind == SNAP_TETHER) ? 5 : -1;
+    if (need < 0) return fail(c, SNAP_ERR_ARG, "unknown bond kind");
+    if (!params || nparams != need) return fail(c, SNAP_ERR_ARG, "wrong number of bond parameters for this kind");
+    for (int q = 0; q < need; ++q)
+        if (!std::isfinite(params[q])) return fail(c, SNAP_ERR_ARG, "bond parameters must be finite");
+    const double k = params[0], r0 = params[1];
+    if (!(k >= 0.0) || !(r0 > 0.0)) return fail(c, SNAP_ERR_ARG, "bond parameters need k >= 0 and a length > 0");
+    double x[3] = {0.0, 0.0, 0.0};
+    if (kind == SNAP_FENEWCA) {
+        x[0] = params[2]; x[1] = params[3]; x[2] = params[4];
+        if (!(x[0] >= 0.0) || !(x[1] > 0.0) || !(x[2] >= 0.0))
+            return fail(c, SNAP_ERR_ARG, "FENEWCA needs eps >= 0, sigma > 0, delta >= 0");
+    } else if (kind == SNAP_TETHER) {
+        x[0] = params[2]; x[1] = params[3]; x[2] = params[4];
+        if (!(r0 < x[0] && x[0] < x[1] && x[1] < x[2]))
+            return fail(c, SNAP_ERR_ARG, "Tether needs l_min < l_c1 < l_c0 < l_max");
+    }
     for (const auto &r : c->rx)
         if (r.bt == bt && kind != SNAP_HARMONIC && (r.slip_a != 0.0 || c->mh_mode != 0))
             return fail(c, SNAP_ERR_ARG, "the slip bond and Metropolis-Hastings moves need a harmonic bond type");
     c->bkind[bt] = kind;
     c->bk[bt] = k;
     c->br0[bt] = r0;
+    for (int q = 0; q < 3; ++q) c->bx[bt][q] = x[q];
     c->bset[bt] = true;
     if (c->ready) {
         fill_params(c);
         c->graph_dirty = true;
     }
     return SNAP_OK;
+}
+
+extern "C" snap_status snap_set_bond_params(snap_ctx *c, int32_t bt, int32_t kind, double k, double r0)
+{
+    if (c && kind != SNAP_HARMONIC && kind != SNAP_FENE)
+        return fail(c, SNAP_ERR_ARG, "FENEWCA and Tether take their parameters through snap_set_bond_params_ex");
+    const double p[2] = {k, r0};
+    return snap_set_bond_params_ex(c, bt, kind, p, 2);
 }
 
 extern "C" snap_status snap_add_static_bonds(snap_ctx *c, int64_t nb, const int32_t *pairs, int32_t bt)

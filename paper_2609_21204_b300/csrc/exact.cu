@@ -750,17 +750,57 @@ __global__ void __launch_bounds__(256) k_resolve(DevParams P, DevArrays A, int s
     else pull_exact(P, A, slot, step);
 }
 
-// U_b of a proposed dynamic bond from d = |r - r0| (Eq. 3): harmonic
-// k d^2 / 2 (the sign of r - r0 cancels exactly); FENE, whose proposals aim
-// at r0 = 0 so that d = r, -k R0^2 ln(1 - (r/R0)^2) / 2 with this library's
-// logarithm, +inf at r >= R0.
-__device__ __forceinline__ double dyn_bond_u(const DevParams &P, int bt, double d)
+// U_b of a proposed dynamic bond (Eq. 3), every operation one IEEE rounding
+// in a fixed order (the oracle evaluates the same expressions).  Harmonic
+// from d = |r - r0|: k d^2 / 2 (the sign of r - r0 cancels exactly); FENE,
+// whose proposals aim at 0 so that d = r: -k R0^2 ln(1 - (r/R0)^2) / 2 with
+// this library's logarithm, +inf at r >= R0.  FENEWCA and Tether from the
+// separation r itself (HOOMD-blue's potentials of those names; +inf outside
+// their finite range), with this library's exp and log.
+__device__ __forceinline__ double dyn_bond_u(const DevParams &P, int bt, double d, double r)
 {
-    if (P.bkind[bt] == 0) return __dmul_rn(__dmul_rn(__dmul_rn(0.5, P.bk[bt]), d), d);
+    const double inf = __longlong_as_double(0x7FF0000000000000ll);
+    const int kind = P.bkind[bt];
+    if (kind == kHarmonic) return __dmul_rn(__dmul_rn(__dmul_rn(0.5, P.bk[bt]), d), d);
     const double R0 = P.br0[bt];
-    const double q = __ddiv_rn(__dmul_rn(d, d), __dmul_rn(R0, R0));
-    if (!(q < 1.0)) return __longlong_as_double(0x7FF0000000000000ll);
-    return __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(-0.5, P.bk[bt]), R0), R0), log_cw(__dsub_rn(1.0, q)));
+    if (kind == kFene) {
+        const double q = __ddiv_rn(__dmul_rn(d, d), __dmul_rn(R0, R0));
+        if (!(q < 1.0)) return inf;
+        return __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(-0.5, P.bk[bt]), R0), R0), log_cw(__dsub_rn(1.0, q)));
+    }
+    if (kind == kFeneWca) {
+        const double eps = P.bx[bt][0], sig = P.bx[bt][1];
+        const double s = __dsub_rn(r, P.bx[bt][2]);
+        const double q = __ddiv_rn(__dmul_rn(s, s), __dmul_rn(R0, R0));
+        if (!(q < 1.0) || !(s > 0.0)) return inf;
+        double U = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(-0.5, P.bk[bt]), R0), R0), log_cw(__dsub_rn(1.0, q)));
+        if (s < __dmul_rn(sig, kTwoSixth)) {
+            const double sr2 = __ddiv_rn(__dmul_rn(sig, sig), __dmul_rn(s, s));
+            const double sr6 = __dmul_rn(__dmul_rn(sr2, sr2), sr2);
+            U = __dadd_rn(U, __dadd_rn(__dmul_rn(__dmul_rn(4.0, eps), __dsub_rn(__dmul_rn(sr6, sr6), sr6)), eps));
+        }
+        return U;
+    }
+    // Tether: k_b = bk, l_min = br0, (l_c1, l_c0, l_max) = bx
+    const double lmin = R0, lc1 = P.bx[bt][0], lc0 = P.bx[bt][1], lmax = P.bx[bt][2];
+    if (!(r > lmin) || !(r < lmax)) return inf;
+    if (r > lc0) {
+        const double a = __dsub_rn(lc0, r), b = __dsub_rn(lmax, r);
+        return __ddiv_rn(__dmul_rn(P.bk[bt], exp_cw(__ddiv_rn(1.0, a))), b);
+    }
+    if (r < lc1) {
+        const double c = __dsub_rn(r, lc1), e = __dsub_rn(r, lmin);
+        return __ddiv_rn(__dmul_rn(P.bk[bt], exp_cw(__ddiv_rn(1.0, c))), e);
+    }
+    return 0.0;
+}
+
+// the separation r of the pair (i, j), needed by the bond kinds whose energy
+// is not a function of |r - r0| alone
+__device__ __forceinline__ double accept_r(const DevParams &P, const DevArrays &A, const RepDev &R, int bt, int i,
+                                          int j)
+{
+    return P.bkind[bt] >= kFeneWca ? __dsqrt_rn(exact_r2(A, R, i, j)) : 0.0;
 }
 
 // Acceptance (Eq. 3) of the surviving edges: in scan mode one thread per
@@ -794,7 +834,8 @@ __global__ void k_accept(DevParams P, DevArrays A, int slot)
                     const double u = u53(w.x, w.y);
                     // U_b from d = |r - r0| of whichever end proposed the edge
                     const double d = A.prop[c] == j ? A.prop_d[c] : A.prop_d[j];
-                    const double U = dyn_bond_u(P, P.rx_bt[a], d);
+                    const int bt = P.rx_bt[a];
+                    const double U = dyn_bond_u(P, bt, d, accept_r(P, A, R, bt, c, j));
                     double pon;
                     if (R.t_sweep > 0.0) pon = __dmul_rn(R.p_on0[a], exp_cw(-__ddiv_rn(U, R.t_sweep)));
                     else pon = (U <= 0.0) ? R.p_on0[a] : 0.0;
@@ -825,7 +866,8 @@ __global__ void k_accept(DevParams P, DevArrays A, int slot)
                     const uint32_t lo = ti < tj ? ti : tj, hi = ti < tj ? tj : ti;
                     const U4 w = pair_draw(R, a, kForm, step, lo, hi);
                     const double u = u53(w.x, w.y);
-                    const double U = dyn_bond_u(P, P.rx_bt[a], A.prop_d[i]);
+                    const int bt = P.rx_bt[a];
+                    const double U = dyn_bond_u(P, bt, A.prop_d[i], accept_r(P, A, R, bt, i, j));
                     double pon;
                     if (R.t_sweep > 0.0) {
                         const double e = __ddiv_rn(U, R.t_sweep);

@@ -453,25 +453,85 @@ __device__ __forceinline__ void separation(const V &pi, const V &pj, const RepDe
     dz = (pj.z - pi.z) + (R)sz * Num<R>::w(Rp, 2);
 }
 
-// bond force factor (dU/dr)/r; returns false on FENE overstretch
+template <typename R> __device__ __forceinline__ R exp_(R v);
+template <> __device__ __forceinline__ float exp_<float>(float v) { return expf(v); }
+template <> __device__ __forceinline__ double exp_<double>(double v) { return exp(v); }
+
+// bond force factor (dU/dr)/r and energy u; returns false when the bond is
+// outside the finite range of its potential (FENE / FENEWCA overstretch, a
+// Tether bond at or beyond l_min or l_max).  FENEWCA and Tether are the bond
+// potentials HOOMD-blue documents under those names (Sec. II.B of the DyBond-v2
+// paper lists them as the evaluators it accepts):
+//   FENEWCA: U = -k R0^2/2 ln(1 - (s/R0)^2) + [4 eps ((sig/s)^12 - (sig/s)^6) + eps] for
+//            s = r - delta < 2^(1/6) sig (the bracket is 0 beyond);
+//   Tether:  U = k_b e^{1/(l_c0 - r)} / (l_max - r) for r > l_c0
+//              + k_b e^{1/(r - l_c1)} / (r - l_min) for r < l_c1 (0 in between).
 template <typename R>
 __device__ __forceinline__ bool bond_factor(const DevParams &P, int bt, R r2, R &fb, double &u)
 {
     const R k = Num<R>::bk(P, bt), r0 = Num<R>::br0(P, bt);
-    if (P.bkind[bt] == 0) {
+    const int kind = P.bkind[bt];
+    if (kind == kHarmonic) {
         const R r = Num<R>::sqrt_(r2);
         fb = k * (r - r0) / r;
         u = 0.5 * (double)k * ((double)r - (double)r0) * ((double)r - (double)r0);
         return true;
     }
-    const R q = r2 / (r0 * r0);
-    if (!(q < (R)1)) {
+    if (kind == kFene) {
+        const R q = r2 / (r0 * r0);
+        if (!(q < (R)1)) {
+            fb = 0;
+            u = 0.0;
+            return false;
+        }
+        fb = k / ((R)1 - q);
+        u = -0.5 * (double)k * (double)r0 * (double)r0 * log(1.0 - (double)q);
+        return true;
+    }
+    const R r = Num<R>::sqrt_(r2);
+    const R x0 = sizeof(R) == 4 ? (R)P.bxf[bt][0] : (R)P.bx[bt][0];
+    const R x1 = sizeof(R) == 4 ? (R)P.bxf[bt][1] : (R)P.bx[bt][1];
+    const R x2 = sizeof(R) == 4 ? (R)P.bxf[bt][2] : (R)P.bx[bt][2];
+    if (kind == kFeneWca) {
+        const R eps = x0, sig = x1, s = r - x2;
+        const R q = s * s / (r0 * r0);
+        if (!(q < (R)1) || !(s > (R)0)) {
+            fb = 0;
+            u = 0.0;
+            return false;
+        }
+        R du = k * s / ((R)1 - q);   // dU/dr
+        u = -0.5 * (double)k * (double)r0 * (double)r0 * log(1.0 - (double)q);
+        if (s < sig * (R)kTwoSixth) {
+            const R sr2 = sig * sig / (s * s);
+            const R sr6 = sr2 * sr2 * sr2;
+            du -= (R)24 * eps * ((R)2 * sr6 * sr6 - sr6) / s;
+            const double d6 = (double)sr6;
+            u += 4.0 * (double)eps * (d6 * d6 - d6) + (double)eps;
+        }
+        fb = du / r;
+        return true;
+    }
+    // Tether: k_b = k, l_min = r0, l_c1 = x0, l_c0 = x1, l_max = x2
+    if (!(r > r0) || !(r < x2)) {
         fb = 0;
         u = 0.0;
         return false;
     }
-    fb = k / ((R)1 - q);
-    u = -0.5 * (double)k * (double)r0 * (double)r0 * log(1.0 - (double)q);
+    R du = 0;
+    u = 0.0;
+    if (r > x1) {
+        const R a = x1 - r, b = x2 - r;
+        const R U = k * exp_<R>((R)1 / a) / b;
+        du = U * ((R)1 / (a * a) + (R)1 / b);
+        u = (double)U;
+    } else if (r < x0) {
+        const R c = r - x0, e = r - r0;
+        const R U = k * exp_<R>((R)1 / c) / e;
+        du = -U * ((R)1 / (c * c) + (R)1 / e);
+        u = (double)U;
+    }
+    fb = du / r;
     return true;
 }
 

@@ -42,9 +42,11 @@ struct DevParams {
     double rc2d[kMaxTypes * kMaxTypes];
     double sig2d[kMaxTypes * kMaxTypes], eps24d[kMaxTypes * kMaxTypes], shiftd[kMaxTypes * kMaxTypes];
     // bond types
-    int32_t bkind[kMaxBondTypes];   // 0: harmonic, 1: FENE (the C ABI's bond kinds)
-    double bk[kMaxBondTypes], br0[kMaxBondTypes];
+    int32_t bkind[kMaxBondTypes];   // 0 harmonic, 1 FENE, 2 FENEWCA, 3 Tether (the C ABI's bond kinds)
+    double bk[kMaxBondTypes], br0[kMaxBondTypes];   // harmonic k, r0; FENE(WCA) k, R0; Tether k_b, l_min
     float bkf[kMaxBondTypes], br0f[kMaxBondTypes];
+    double bx[kMaxBondTypes][3];    // FENEWCA: eps, sigma, delta; Tether: l_c1, l_c0, l_max
+    float bxf[kMaxBondTypes][3];
     // reactions
     int32_t rx_ta[kMaxRx], rx_tb[kMaxRx], rx_bt[kMaxRx];
     int32_t rx_self[kMaxRx];   // 1: sites of one molecule do not react with each other (Sec. II.D)
@@ -154,6 +156,8 @@ struct DevArrays {
 };
 
 constexpr int kMhCand = 16;         // candidates per MH move or logged event
+constexpr double kTwoSixth = 0x1.1f59ac3c7d6c0p+0;   // 2^(1/6), the WCA cut in units of sigma
+enum BondKind { kHarmonic = 0, kFene = 1, kFeneWca = 2, kTether = 3 };
 
 constexpr int kContenders = 4;
 constexpr int kPushSlots = 64;     // push mode: pair distances kept per pushing site

@@ -19,6 +19,8 @@ from .placement import rsa, random_walk_chains
 
 HARMONIC = 0
 FENE = 1
+FENEWCA = 2
+TETHER = 3
 
 
 @dataclass
@@ -37,9 +39,10 @@ class Reaction:
 
 @dataclass
 class BondType:
-    kind: int             # HARMONIC or FENE
-    k: float
-    r0: float             # rest length (harmonic) or maximum extension R0 (FENE)
+    kind: int             # HARMONIC, FENE, FENEWCA or TETHER
+    k: float              # k (k_b for TETHER)
+    r0: float             # rest length (harmonic), maximum extension R0 (FENE, FENEWCA), l_min (TETHER)
+    extra: tuple = ()     # FENEWCA: (eps, sigma, delta); TETHER: (l_c1, l_c0, l_max)
 
 
 @dataclass
