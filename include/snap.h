@@ -315,6 +315,22 @@ snap_status snap_get_images(snap_ctx *, int32_t *img3);
 snap_status snap_get_neighbors(snap_ctx *, int32_t *tag_pairs, int64_t cap, int64_t *n_out);
 
 snap_status snap_get_stats(snap_ctx *, snap_stats *out);
+
+/* Pair-distance histogram behind g(r) of replica `replica` (0 for one
+ * system), the structural observable whose agreement with the FP64 reference
+ * the method is checked by: hist[nbins] (host, written) receives, for every
+ * unordered pair of one particle of type_a and one of type_b (two distinct
+ * particles when type_a == type_b) at separation r < r_max, one count in bin
+ * floor(r / dr), dr = r_max / nbins.  r is the exact FP64 minimum-image
+ * separation of the current positions (the one the sweep's window test uses),
+ * so the counts are a pure function of the positions.  The call forces a
+ * neighbour-list rebuild first (in SNAP_MIXED mode that re-rounds the FP32
+ * coordinates, as every rebuild does).  g(r) = counts / (pairs of an ideal
+ * gas of the same composition in each spherical shell).  r_max must lie in
+ * (0, w - 0.002], w the replica's smallest neighbour-cell edge; bad types,
+ * replica or nbins outside 1..2^20 return SNAP_ERR_ARG. */
+snap_status snap_get_rdf(snap_ctx *, int32_t replica, int32_t type_a, int32_t type_b, double r_max,
+                         int32_t nbins, int64_t *hist);
 snap_status snap_get_energy(snap_ctx *, snap_energy *out);
 /* Bond lifetimes (in sweeps) of every bond broken so far; bins[nbins], last
  * bin collects the tail. */

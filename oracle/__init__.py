@@ -126,6 +126,8 @@ def lib():
                                         C.c_int64, C.c_void_p, C.c_int32]
         _lib.orc_candidates.restype = C.c_int32
         _lib.orc_mh_sweep.argtypes = [C.POINTER(Params), C.POINTER(State), C.c_int64, C.POINTER(MHStats)]
+        _lib.orc_rdf.argtypes = [C.POINTER(Params), C.POINTER(State), C.c_int32, C.c_int32, C.c_double,
+                                 C.c_int32, C.c_void_p]
         _lib.orc_kinetic_T.argtypes = [C.POINTER(Params), C.POINTER(State)]
         _lib.orc_kinetic_T.restype = C.c_double
         _lib.orc_tanh.argtypes = [C.c_double]
@@ -175,6 +177,17 @@ def melting_rates(T, lam, t_melt, kon_init, koff_init, kon_melt, koff_melt, n, d
     kon = kon_init * (1.0 - g) + kon_melt * g
     koff = koff_init * (1.0 - g) + koff_melt * g
     return kon * n * dt, koff * n * dt
+
+
+def rdf_normalise(counts, n_a, n_b, same, volume, r_max):
+    """g(r) from pair counts: counts over the pair count an ideal gas of the
+    same composition would put in each spherical shell (N_a N_b / V, or
+    N_a (N_a - 1) / 2 / V for one type, times the shell volume)."""
+    nb = len(counts)
+    edges = np.linspace(0.0, r_max, nb + 1)
+    shell = 4.0 / 3.0 * math.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+    pairs = n_a * (n_a - 1) / 2.0 if same else float(n_a) * n_b
+    return np.asarray(counts, dtype=np.float64) / (pairs / volume * shell)
 
 
 def molecules(n, static_bonds):
@@ -341,6 +354,16 @@ class OracleSystem:
         if rc != 0:
             raise RuntimeError(f"orc_mh_sweep failed: {rc}")
         return st.as_dict()
+
+    def rdf_counts(self, type_a, type_b, r_max, nbins):
+        """Pair counts per distance bin behind g(r) (see orc_rdf)."""
+        self._sync_ptrs()
+        h = np.zeros(int(nbins), dtype=np.int64)
+        rc = lib().orc_rdf(C.byref(self.params), C.byref(self._state), int(type_a), int(type_b),
+                           float(r_max), int(nbins), _ptr(h))
+        if rc != 0:
+            raise RuntimeError("orc_rdf failed")
+        return h
 
     def kinetic_T(self):
         """The instantaneous kinetic temperature a sweep would use now."""

@@ -1229,6 +1229,55 @@ int orc_run(const orc_params *P, orc_state *S, int64_t nsteps, double *ke_out)
     return err;
 }
 
+/* ---------------------------------------------------------- observables */
+
+typedef struct {
+    const orc_params *P;
+    const orc_state *S;
+    int64_t i;
+    int32_t tb, same;
+    double rmax2, rmax, dr;
+    int32_t nbins;
+    int64_t *hist;
+} orc_rdf_ctx;
+
+static void orc_rdf_visit(int64_t j, void *vctx)
+{
+    orc_rdf_ctx *c = (orc_rdf_ctx *)vctx;
+    if (c->S->type[j] != c->tb) return;
+    if (c->same && j <= c->i) return;
+    double dx, dy, dz;
+    double r2 = orc_dist2(c->P, c->S, c->i, j, &dx, &dy, &dz);
+    if (!(r2 < c->rmax2)) return;
+    double r = sqrt(r2);
+    if (!(r < c->rmax)) return;
+    int64_t b = (int64_t)(r / c->dr);
+    if (b < c->nbins) c->hist[b]++;
+}
+
+/* Pair-distance histogram behind g(r): every unordered pair of one particle
+ * of type ta and one of type tb (two distinct particles of type ta when
+ * ta == tb) with r < r_max adds one to bin floor(r / dr), dr = r_max / nbins;
+ * r = sqrt of the same FP64 r^2 as the sweep's window test.  Counts are added
+ * to hist (the caller clears it). */
+int orc_rdf(const orc_params *P, const orc_state *S, int32_t ta, int32_t tb, double rmax, int32_t nbins,
+            int64_t *hist)
+{
+    if (!(rmax > 0.0) || nbins <= 0 || !hist) return ORC_ERR_ARG;
+    orc_grid g;
+    if (orc_grid_build(P, S, rmax, &g) != 0) return ORC_ERR_ARG;
+    orc_rdf_ctx c;
+    c.P = P; c.S = S; c.tb = tb; c.same = ta == tb;
+    c.rmax = rmax; c.rmax2 = rmax * rmax; c.dr = rmax / (double)nbins; c.nbins = nbins; c.hist = hist;
+    for (int64_t i = 0; i < P->n; ++i) {
+        if (S->type[i] != ta) continue;
+        c.i = i;
+        orc_grid_visit(P, S, &g, i, orc_rdf_visit, &c);
+    }
+    orc_grid_free(&g);
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------ pair sets */
 
 typedef struct {

@@ -148,6 +148,10 @@ typedef struct {
  * owned-pair move set.  Returns ORC_ERR_ARG if the box is too small. */
 int orc_mh_sweep(const orc_params *P, orc_state *S, int64_t step, orc_mh_stats *st);
 
+/* Pair-distance histogram behind g(r): unordered pairs of types (ta, tb) with
+ * r < rmax, bin floor(r / (rmax / nbins)); counts are added to hist[nbins]. */
+int orc_rdf(const orc_params *P, const orc_state *S, int32_t ta, int32_t tb, double rmax, int32_t nbins,
+            int64_t *hist);
 /* All unordered pairs (i<j) with r < rc_ij + extra, written as tag pairs.
    Returns the count (writes at most cap pairs). */
 int64_t orc_pairs_within(const orc_params *P, const orc_state *S, double extra,

@@ -320,6 +320,13 @@ class Snap:
         self._check(self._lib.snap_get_energy(self._ctx, C.byref(e)))
         return dict(e_pair=e.e_pair, e_bond=e.e_bond, kinetic=e.kinetic, virial=e.virial)
 
+    def rdf_counts(self, type_a, type_b, r_max, nbins, replica=0):
+        """Pair counts per distance bin behind g(r) (snap_get_rdf)."""
+        h = np.zeros(int(nbins), dtype=np.int64)
+        self._check(self._lib.snap_get_rdf(self._ctx, int(replica), int(type_a), int(type_b), float(r_max),
+                                           int(nbins), h.ctypes.data))
+        return h
+
     def lifetime_hist(self, nbins=256):
         h = np.zeros(nbins, dtype=np.int64)
         self._check(self._lib.snap_get_lifetime_hist(self._ctx, h.ctypes.data, int(nbins)))

@@ -75,6 +75,7 @@ SIGNATURES = {
     "snap_get_images": (C.c_int, [_P, _P]),
     "snap_get_neighbors": (C.c_int, [_P, _P, C.c_int64, C.POINTER(C.c_int64)]),
     "snap_get_stats": (C.c_int, [_P, C.POINTER(Stats)]),
+    "snap_get_rdf": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int32, _P]),
     "snap_get_energy": (C.c_int, [_P, C.POINTER(Energy)]),
     "snap_get_lifetime_hist": (C.c_int, [_P, _P, C.c_int32]),
     "snap_get_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),

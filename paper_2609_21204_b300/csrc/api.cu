@@ -1682,6 +1682,42 @@ extern "C" snap_status snap_get_neighbors(snap_ctx *c, int32_t *pairs, int64_t c
     return SNAP_OK;
 }
 
+extern "C" snap_status snap_get_rdf(snap_ctx *c, int32_t replica, int32_t type_a, int32_t type_b, double r_max,
+                                    int32_t nbins, int64_t *hist)
+{
+    snap_status s = check_ready(c);
+    if (s != SNAP_OK) return s;
+    if (!hist) return fail(c, SNAP_ERR_ARG, "hist is NULL");
+    if (replica < 0 || replica >= (int)c->reps.size()) return fail(c, SNAP_ERR_ARG, "replica out of range");
+    if (type_a < 0 || type_a >= c->ntypes || type_b < 0 || type_b >= c->ntypes)
+        return fail(c, SNAP_ERR_ARG, "type out of range");
+    if (nbins < 1 || nbins > (1 << 20)) return fail(c, SNAP_ERR_ARG, "nbins must lie in 1..2^20");
+    const RepHost &R = c->reps[replica];
+    double wmin = 1e300;
+    for (int d = 0; d < 3; ++d) wmin = std::min(wmin, R.L[d] / (double)R.nc[d]);
+    if (!(r_max > 0.0) || !(r_max <= wmin - 2e-3))
+        return fail(c, SNAP_ERR_ARG, "r_max must lie in (0, cell width - 0.002] (cell width " + std::to_string(wmin) + ")");
+    // a forced rebuild files every particle in its current cell
+    if ((s = set_need_rebuild(c)) != SNAP_OK) return s;
+    s = run_with_retry(c, [&] { seq_rebuild(c); });
+    if (s != SNAP_OK) return s;
+    unsigned long long *d_hist = static_cast<unsigned long long *>(dalloc(c, sizeof(unsigned long long) * nbins));
+    if (!d_hist) return fail(c, SNAP_ERR_OOM, "histogram");
+    std::vector<unsigned long long> h(nbins);
+    cudaError_t e = cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * nbins, c->stream);
+    if (e == cudaSuccess) {
+        launch_rdf(c->P, c->A, replica, type_a, type_b, r_max, nbins, d_hist, launch(c));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), d_hist, sizeof(unsigned long long) * nbins, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dfree(c, d_hist);
+    if (e != cudaSuccess) return fail(c, SNAP_ERR_CUDA, cudaGetErrorString(e));
+    for (int b = 0; b < nbins; ++b) hist[b] = (int64_t)h[b];
+    return SNAP_OK;
+}
+
 extern "C" snap_status snap_get_stats(snap_ctx *c, snap_stats *out)
 {
     if (!c || !out) return SNAP_ERR_ARG;

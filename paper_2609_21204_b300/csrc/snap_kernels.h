@@ -53,6 +53,10 @@ void launch_step_md(const DevParams &P, const DevArrays &A, bool fp64, Launch L)
 void launch_step_end(const DevArrays &A, Launch L);
 void launch_reduce_cols(const double *src, int ncol, long long n, double *out, Launch L);
 
+// ---- observables (observe.cu): pair-distance histogram behind g(r) of one replica ----
+void launch_rdf(const DevParams &P, const DevArrays &A, int rep, int ta, int tb, double rmax, int nbins,
+                unsigned long long *hist, Launch L);
+
 // ---- tag-order I/O: dst[rtag[t]] = src[t] (in), dst[t] = src[rtag[t]] (out) ----
 template <typename T> void launch_in(T *dst_sorted, const T *src_tag, const int32_t *rtag, long long n, Launch L);
 template <typename T> void launch_out(T *dst_tag, const T *src_sorted, const int32_t *rtag, long long n, Launch L);
