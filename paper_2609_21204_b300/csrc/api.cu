@@ -191,6 +191,7 @@ snap_status upload_reps(snap_ctx *c)
         D.kT = R.kT;
         D.t_sweep = R.kT;
         D.noise_c = std::sqrt(((2.0 * c->cfg.gamma) * R.kT) / c->cfg.dt);
+        D.noise_cf = (float)D.noise_c;
         D.key0 = (uint32_t)(R.seed & 0xFFFFFFFFull);
         D.key1hi = (uint32_t)(((R.seed >> 32) & 0xFFFFull) << 16);
         for (int d = 0; d < 3; ++d) D.mh_nc[d] = c->mh_nc[d];
@@ -296,6 +297,9 @@ void fill_params(snap_ctx *c)
     P.half_dt = 0.5 * c->cfg.dt;
     P.gamma = c->cfg.gamma;
     P.sqrt3 = std::sqrt(3.0);
+    P.dtf = (float)P.dt;
+    P.gammaf = (float)P.gamma;
+    P.sqrt3f = (float)P.sqrt3;
     const double dmax = 0.5 * skin - 1e-4;
     P.disp2f = (float)(dmax * dmax);
     P.nbr_cap = c->nbr_cap;

@@ -55,7 +55,7 @@ __device__ __forceinline__ int4 apply_particle(const DevParams &P, DevArrays &A,
     }
     if (f >= 0) {
         const int rp = rep_of(P, A, i);
-        const int a = A.rx_order[rp * kMaxRx + slot];
+        const int a = rx_at(P, A, rp, slot);
         const int pt = A.tag[f];
         int s = m;
         while (s > 0 && np[s - 1] > pt) {

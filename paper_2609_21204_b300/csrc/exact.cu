@@ -245,7 +245,7 @@ constexpr int kPushRatio = 4;
 __device__ __forceinline__ int push_type(const DevParams &P, const DevArrays &A, int slot)
 {
     if (P.nrep != 1 || P.nrx != 1) return -1;
-    const int a = A.rx_order[slot];
+    const int a = rx_at(P, A, 0, slot);
     const int ta = P.rx_ta[a], tb = P.rx_tb[a];
     if (ta == tb) return -1;
     const long long ca = A.avail_count[ta], cb = A.avail_count[tb];
@@ -310,7 +310,7 @@ __device__ __forceinline__ void pull_propose(const DevParams &P, DevArrays &A, i
         int best = -1, ncont = 0;
         double best_d = 0.0;
         const int rp = rep_of(P, A, i);
-        const int a = A.rx_order[rp * kMaxRx + slot];
+        const int a = rx_at(P, A, rp, slot);
         const int ti = A.type[i];
         const int ta = P.rx_ta[a], tb = P.rx_tb[a];
         if ((ti == ta || ti == tb) && A.occ[i] < P.valence[ti]) {
@@ -408,7 +408,7 @@ __device__ __forceinline__ void pull_exact(const DevParams &P, DevArrays &A, int
         const int i = A.site_list[q];
         const int nc = A.ncont[i];
         const int rp = rep_of(P, A, i);
-        const int a = A.rx_order[rp * kMaxRx + slot];
+        const int a = rx_at(P, A, rp, slot);
         const RepDev &R = A.reps[rp];
         if (nc == 0) {
             // FP64 mode: the proposal was decided in k_propose
@@ -495,9 +495,10 @@ __device__ __forceinline__ ulonglong2 cas128(ulonglong2 *p, ulonglong2 cmp, ulon
 // pusher lowered the key; the retries are bounded by the pushers of one site
 // (the cap, 2^16 unless snap_set_retry_limit lowers it, only guards against a
 // defect, and latches a status bit).
-__device__ __forceinline__ void atomic_min_key(ulonglong2 *p, unsigned long long d, unsigned long long t,
-                                               uint32_t *status, int cap)
+__device__ __forceinline__ void atomic_min_key(const DevParams &P, const DevArrays &A, int j, unsigned long long d,
+                                               unsigned long long t, int cap)
 {
+    ulonglong2 *p = &A.pkey[j];
     ulonglong2 cur = *p;
     for (int it = 0; it < cap; ++it) {
         if (!key_less(d, t, cur.x, cur.y)) return;
@@ -505,7 +506,7 @@ __device__ __forceinline__ void atomic_min_key(ulonglong2 *p, unsigned long long
         if (old.x == cur.x && old.y == cur.y) return;
         cur = old;
     }
-    atomicOr(status, (uint32_t)kStTimeout);
+    atomicOr(A.status, (uint32_t)kStTimeout);
 }
 
 // Push mode, pass 1: one warp per pushing site (from the compacted list),
@@ -515,7 +516,7 @@ __device__ __forceinline__ void atomic_min_key(ulonglong2 *p, unsigned long long
 // pair distances are kept for pass 2.
 __device__ __forceinline__ void push_pass1(const DevParams &P, DevArrays &A, int slot, long long step, int s)
 {
-    const int a = A.rx_order[slot];
+    const int a = rx_at(P, A, 0, slot);
     const int ta = P.rx_ta[a], tb = P.rx_tb[a];
     const RepDev &R = A.reps[0];
     const double rmin2 = P.rx_rmin2[a], rmax2 = P.rx_rmax2[a];
@@ -557,7 +558,7 @@ __device__ __forceinline__ void push_pass1(const DevParams &P, DevArrays &A, int
                 if (maybe && r2 >= rmin2 && r2 <= rmax2) {
                     inwin += 2;
                     d = (unsigned long long)__double_as_longlong(fabs(__dsub_rn(__dsqrt_rn(r2), r0)));
-                    atomic_min_key(&A.pkey[j], d, me, A.status, P.cas_cap);
+                    atomic_min_key(P, A, j, d, me, P.cas_cap);
                     const unsigned long long tj = (unsigned long long)(uint32_t)A.tag[j];
                     if (key_less(d, tj, bd, bt)) {
                         bd = d;
@@ -587,7 +588,7 @@ __device__ __forceinline__ void push_pass1(const DevParams &P, DevArrays &A, int
 // keys are cleared by k_apply.
 __device__ __forceinline__ void push_pass2(const DevParams &P, DevArrays &A, int slot, long long step, int s)
 {
-    const int a = A.rx_order[slot];
+    const int a = rx_at(P, A, 0, slot);
     const int ta = P.rx_ta[a], tb = P.rx_tb[a];
     const RepDev &R = A.reps[0];
     const double rmin2 = P.rx_rmin2[a], rmax2 = P.rx_rmax2[a];
@@ -663,7 +664,7 @@ __device__ __forceinline__ void break_particle(const DevParams &P, DevArrays &A,
     const int4 dp = A.dp[i];
     if (dp.x < 0) return;
     const int rp = rep_of(P, A, i);
-    const int a = A.rx_order[rp * kMaxRx + slot];
+    const int a = rx_at(P, A, rp, slot);
     if ((((P.slip_mask >> a) & 1) != 0) != SLIP) return;
     const RepDev &R = A.reps[rp];
     const int me = A.tag[i];
@@ -680,9 +681,10 @@ __device__ __forceinline__ void break_particle(const DevParams &P, DevArrays &A,
         // with the slip modifier P_off depends on r and m < p_off 2^53 is tested in
         // FP64 (both sides exact)
         const unsigned long long m = ((unsigned long long)w.x << 21) | (unsigned long long)(w.y >> 11);
-        const int j = A.rtag[p];
+        int j = -1;
         bool brk;
         if (SLIP) {
+            j = A.rtag[p];
             const int bt = P.rx_bt[a];
             const double pr = slip_p_off(R.p_off[a], P.bk[bt], P.br0[bt], R.t_sweep, P.rx_slip[a],
                                          __dsqrt_rn(exact_r2(A, R, (int)i, j)));
@@ -691,6 +693,7 @@ __device__ __forceinline__ void break_particle(const DevParams &P, DevArrays &A,
             brk = m < R.off_thresh[a];
         }
         if (brk) {
+            if (!SLIP) j = A.rtag[p];     // the partner's index only for a bond that breaks
             atomicOr(&A.brk[i], 1u << s);
             const int4 q = A.dp[j];
             const int qv[4] = {q.x, q.y, q.z, q.w};
@@ -822,7 +825,7 @@ __global__ void k_accept(DevParams P, DevArrays A, int slot)
             const int c = A.avail_list[(long long)ps * P.n + g];
             const unsigned long long bc = A.best[c];
             if (bc != 0ull) {
-                const int a = A.rx_order[slot];
+                const int a = rx_at(P, A, 0, slot);
                 const RepDev &R = A.reps[0];
                 const uint32_t tc = (uint32_t)(A.tag[c] - R.tag_off), tj = (uint32_t)bc;
                 const int j = A.rtag[tj + R.tag_off];
@@ -854,7 +857,7 @@ __global__ void k_accept(DevParams P, DevArrays A, int slot)
         const int j = A.prop[i];
         if (j >= 0) {
             const int rp = rep_of(P, A, i);
-            const int a = A.rx_order[rp * kMaxRx + slot];
+            const int a = rx_at(P, A, rp, slot);
             const RepDev &R = A.reps[rp];
             const uint32_t ti = (uint32_t)(A.tag[i] - R.tag_off), tj = (uint32_t)(A.tag[j] - R.tag_off);
             // a mutual proposal is one edge, handled by its smaller tag

@@ -105,7 +105,7 @@ __device__ __forceinline__ void integrate_mixed(const DevParams &P, DevArrays &A
 {
     const U4 w = langevin_draw(Rp, A, i, step);
     float4 v = A.v4[i];
-    const float cn = (float)Rp.noise_c, g = (float)P.gamma, s3 = (float)P.sqrt3, dt = (float)P.dt;
+    const float cn = Rp.noise_cf, g = P.gammaf, s3 = P.sqrt3f, dt = P.dtf;   // rounded on the host
     // xi = sqrt(3) (2u - 1) with u = (w >> 8 + 1/2) 2^-24 in (0, 1)
     const float ux = fmaf((float)(w.x >> 8), 0x1.0p-24f, 0x1.0p-25f);
     const float uy = fmaf((float)(w.y >> 8), 0x1.0p-24f, 0x1.0p-25f);

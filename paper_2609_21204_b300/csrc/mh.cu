@@ -468,7 +468,7 @@ __global__ void k_log_events(DevParams P, DevArrays A, int slot)
         const int j = A.prop[(int)i];
         if (j < 0 || A.fpart[i] != j) continue;
         const int rp = rep_of(P, A, i);
-        const int a = A.rx_order[rp * kMaxRx + slot];
+        const int a = rx_at(P, A, rp, slot);
         const RepDev &R = A.reps[rp];
         int ci[kMhCand];
         double cr[kMhCand];

@@ -56,6 +56,7 @@ struct DevParams {
     double rx_rmin2[kMaxRx], rx_rmax2[kMaxRx];
     // integrator
     double dt, half_dt, gamma, sqrt3;
+    float dtf, gammaf, sqrt3f;   // the same, rounded to FP32 (mixed-mode kick)
     float disp2f;           // squared displacement that triggers a rebuild
     int32_t nbr_cap;        // force-list entries per particle
     int32_t rnbr_cap;       // reactive-list entries per particle
@@ -88,6 +89,7 @@ struct RepDev {
     int64_t tag_off, n;
     double kT, noise_c;     // set-point kT and sqrt(2 gamma kT / dt)
     double t_sweep;         // T of the current sweep: kT, or the kinetic temperature (k_sweep_begin)
+    float noise_cf;         // noise_c rounded to FP32 (mixed-mode kick)
     uint32_t key0, key1hi;  // Philox key words derived from the seed
     double p_on0[kMaxRx], p_off[kMaxRx];
     unsigned long long off_thresh[kMaxRx];   // ceil(p_off * 2^53): break iff 53-bit draw < this
@@ -352,6 +354,13 @@ __device__ __forceinline__ bool status_ok(const uint32_t *st) { return *(volatil
 __device__ __forceinline__ int rep_of(const DevParams &P, const DevArrays &A, long long i)
 {
     return P.nrep > 1 ? A.rep[i] : 0;
+}
+
+// reaction processed in slot `slot` of replica rp's sweep (with one reaction
+// the order is the identity and no load is needed)
+__device__ __forceinline__ int rx_at(const DevParams &P, const DevArrays &A, int rp, int slot)
+{
+    return P.nrx == 1 ? 0 : A.rx_order[rp * kMaxRx + slot];
 }
 
 // warp-aggregated 64-bit counter increment (one atomic per full warp)
