@@ -65,6 +65,8 @@ def parse():
                     help="formation events logged for training the proposal network (0: skip the leg)")
     ap.add_argument("--learned-epochs", type=int, default=10)
     ap.add_argument("--mh-steps", type=int, default=500)
+    ap.add_argument("--no-small-legs", dest="small_legs", action="store_false",
+                    help="skip the A+B association and telechelic network legs")
     ap.add_argument("--competing-n", type=int, default=262144,
                     help="particles of the four-reaction soup leg (0: skip the leg)")
     ap.add_argument("--competing-steps", type=int, default=1000)
@@ -306,7 +308,124 @@ def _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream):
             "value": sum_all(float(nb)) * args.batch_steps / t, "unit": UNIT,
             "ms_per_step": t * 1e3 / args.batch_steps, "steps": args.batch_steps,
             "particles": nb, "replicas": len(batch), "n_bonds": st["n_bonds"],
-            "autotune": {k: tune[k] for k in ("block_size", "skin", "cached", "key")}}
+            "autotune": {k: tune[k] for k in ("block_size", "skin", "cached", "key")},
+            "vs_oracle": _smallest_replicas_vs_oracle(snap, batch)}
+
+
+def _smallest_replicas_vs_oracle(snap, batch):
+    """Bonded fraction of chain ends of the 8 smallest replicas, from a fresh
+    batched run of all replicas with the sampling of the stored FP64 oracle
+    runs of those replicas alone (tests/golden/telechelic_sweep_smallest8.json,
+    written by the oracle), as z-scores with both error bars."""
+    gold = json.loads((ROOT / "tests" / "golden" / "telechelic_sweep_smallest8.json").read_text())
+    offs = np.concatenate([[0], np.cumsum([s.n for s in batch])])
+    sim = snap.from_system(batch, precision="mixed")
+    sim.step(gold["burn_in"])
+    idx = [g["replica"] for g in gold["runs"]]
+    series = {r: [] for r in idx}
+    for _ in range((gold["steps"] - gold["burn_in"]) // gold["every"]):
+        sim.step(gold["every"])
+        b = sim.bonds()
+        for r in idx:
+            series[r].append(int(((b[:, 0] >= offs[r]) & (b[:, 0] < offs[r + 1])).sum()))
+    sim.close()
+    out = []
+    nb = gold["blocks"]
+    for g in gold["runs"]:
+        f = np.array(series[g["replica"]], dtype=np.float64) / g["n_ends"]
+        se = float(f.reshape(nb, -1).mean(1).std(ddof=1) / math.sqrt(nb))
+        z = (f.mean() - g["bonded_fraction"]) / math.sqrt(se ** 2 + g["bonded_fraction_se"] ** 2 + 1e-12)
+        out.append({"replica": g["replica"], "n": g["n"], "eps": round(g["eps"], 3),
+                    "bonded_fraction": float(f.mean()), "se": se,
+                    "oracle": g["bonded_fraction"], "oracle_se": g["bonded_fraction_se"], "z": float(z)})
+    return {"replicas": out, "max_abs_z": max(abs(x["z"]) for x in out),
+            "what": "bonded fraction of chain ends, steps %d-%d, mixed precision vs FP64 oracle" %
+                    (gold["burn_in"], gold["steps"])}
+
+
+def _run_assoc_ab(args, torch, snap, max_all, sum_all, stream):
+    """A+B association (500 A + 500 B at number density 0.1, eps 5 kT, window
+    r <= 1.3, 10^4 steps): graph-launched steps per second on the small system,
+    and the bonded fraction against the stored FP64 oracle runs of the same
+    seeds (tests/golden/assoc_ab_observables.json)."""
+    from synth import assoc_ab
+    gold = json.loads((ROOT / "tests" / "golden" / "assoc_ab_observables.json").read_text())
+    steps, burn, every, nb = gold["steps"], gold["burn_in"], gold["every"], gold["blocks"]
+    fr, se2, t_tot = [], [], 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for g in gold["runs"]:
+        s = assoc_ab(seed=g["seed"])
+        sim = snap.from_system(s, precision="mixed")
+        n_a = int((s.types == 0).sum())
+        sim.prepare()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(steps)                   # the timed 10^4 steps
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_tot += e0.elapsed_time(e1) / 1e3
+        sim.close()
+        sim = snap.from_system(s, precision="mixed")   # the same run again, sampled like the oracle's
+        sim.step(burn)
+        f = []
+        for _ in range((steps - burn) // every):
+            sim.step(every)
+            f.append(sim.stats()["n_bonds"] / n_a)
+        sim.close()
+        f = np.array(f)
+        fr.append(f.mean())
+        se2.append((f.reshape(nb, -1).mean(1).std(ddof=1) / math.sqrt(nb)) ** 2)
+    m, se = float(np.mean(fr)), float(math.sqrt(sum(se2)) / len(fr))
+    mo = float(np.mean([g["bonded_fraction"] for g in gold["runs"]]))
+    seo = float(math.sqrt(sum(g["bonded_fraction_se"] ** 2 for g in gold["runs"])) / len(gold["runs"]))
+    t = max_all(t_tot)
+    n = 1000 * len(gold["runs"])
+    return {"workload": "A+B association: 500 A + 500 B at number density 0.1, harmonic k=100 r0=1.1, "
+                        "r_max=1.3, eps=5 kT, valence 1, 10^4 steps, %d seeds" % len(gold["runs"]),
+            "value": sum_all(float(n)) * steps / t, "unit": UNIT, "steps_per_s": len(gold["runs"]) * steps / t,
+            "ms_per_step": t * 1e3 / (len(gold["runs"]) * steps),
+            "bonded_fraction": m, "bonded_fraction_se": se, "oracle_bonded_fraction": mo, "oracle_se": seo,
+            "z_vs_oracle": (m - mo) / math.sqrt(se ** 2 + seo ** 2),
+            "closed_form_ideal": 0.8110,
+            "note": "the ideal closed form neglects bonds carried past r_max, which break but cannot form"}
+
+
+def _run_telechelic(args, torch, snap, max_all, sum_all, stream):
+    """Telechelic network (2000 chains x 12 + 4000 crosslinkers, FP32 forces /
+    FP64 integration): steps per second over 10^4 steps, and the bonded
+    fraction of chain ends over steps 500-1000 against the stored FP64 oracle
+    run (tests/golden/telechelic_network.json)."""
+    from synth import telechelic
+    gold = json.loads((ROOT / "tests" / "golden" / "telechelic_network.json").read_text())
+    s = telechelic()
+    sim = snap.from_system(s, precision="mixed")
+    sim.step(gold["from"])
+    f = []
+    for _ in range((gold["steps"] - gold["from"]) // gold["every"]):
+        sim.step(gold["every"])
+        f.append(sim.stats()["n_bonds"] / gold["n_ends"])
+    f = np.array(f)
+    se = float(f.reshape(gold["blocks"], -1).mean(1).std(ddof=1) / math.sqrt(gold["blocks"]))
+    sim.prepare()
+    K = 10_000
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = max_all(e0.elapsed_time(e1) / 1e3)
+    sim.close()
+    return {"workload": "telechelic network: 2000 chains x 12 beads (FENE k=30 R0=1.5 + WCA) + 4000 X "
+                        "(valence 3), ends S valence 1, bead density 0.3, S-X harmonic k=100 r0=1.0 "
+                        "r_max=1.25, eps=8 kT",
+            "value": sum_all(float(s.n)) * K / t, "unit": UNIT, "ms_per_step": t * 1e3 / K, "steps": K,
+            "bonded_fraction_500_1000": float(f.mean()), "se": se,
+            "oracle": gold["bonded_fraction"], "oracle_se": gold["bonded_fraction_se"],
+            "z_vs_oracle": float((f.mean() - gold["bonded_fraction"]) /
+                                 math.sqrt(se ** 2 + gold["bonded_fraction_se"] ** 2))}
 
 
 def _run_competing(args, torch, snap, barrier, max_all, sum_all, stream):
@@ -467,24 +586,45 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
     s = build_system(args, rank_seed(20260921, rank))
     n = s.n
     K, W = args.steps, args.warmup
+    # a fixed untimed equilibration (bonds form from the bond-free start); its
+    # end state is where the launch shape and skin are tuned and timing starts
+    E = args.equil_steps
+    eq = snap.from_system(s, precision="mixed", block_size=args.block or 128, skin=args.skin or 0.5)
+    eq.step(E)
+    state = eq.get_state()
+    eq_check = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # the equilibrated state and the GPU's forces there, both precisions, for the
+        # comparison with the FP64 oracle in the CPU-baseline leg
+        eq_check = dict(pos=eq.positions(), vel=eq.velocities(), bonds=eq.bonds(), step=eq.stats()["step"],
+                        f_mixed=eq.forces())
+        e64 = snap.from_system(s, precision="fp64", block_size=args.block or 128, skin=args.skin or 0.5)
+        e64.set_state(state)
+        eq_check["f_fp64"] = e64.forces()
+        e64.close()
+        e1 = snap.from_system(s, precision="mixed", block_size=args.block or 128, skin=args.skin or 0.5)
+        e1.set_state(state)
+        e1.bond_update()                  # one sweep at the equilibrated state, step counter unchanged
+        eq_check["bonds_after_sweep"] = e1.bonds()
+        eq_check["sweep_stats"] = e1.stats()
+        e1.close()
+    eq.close()
     if args.block or args.skin:
         tune = {"block_size": args.block or 128, "skin": args.skin or s.skin, "cached": None,
                 "key": "set by flags"}
     else:
         from paper_2609_21204_b300 import autotune
-        tune = autotune.autotune(s, precision="mixed", blocks=(128, 256), skins=(0.3, 0.4, 0.5), steps=150,
-                                 warmup=50)
+        tune = autotune.autotune(s, precision="mixed", blocks=(128, 256), skins=(0.3, 0.4, 0.5, 0.6, 0.7),
+                                 steps=200, warmup=40, state=state)
 
     def make(precision):
         return snap.from_system(s, precision=precision, block_size=tune["block_size"], skin=tune["skin"])
 
     sim = make("mixed")
-
-    # a fixed untimed equilibration (bonds form from the bond-free start), the
-    # warm-up, then the step graphs of both buffer parities are captured and
-    # uploaded so that no capture falls inside the timed region
-    E = args.equil_steps
-    sim.step(E)
+    # the equilibrated state, the warm-up, then the step graphs of both buffer
+    # parities are captured and uploaded so that no capture falls inside the
+    # timed region
+    sim.set_state(state)
     sim.step(W)
     sim.prepare()
     st0 = sim.stats()
@@ -527,6 +667,12 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
     traffic = md_traffic_from_profile(n)
     sweep_pairs = st2["scanned"] + st2["break_tested"]
     bond_pairs_per_s = sweep_pairs / (ph["sweep"] / 1e3) if ph["sweep"] > 0 else None
+    # algorithmic bytes of one sweep: per particle the availability pass (type 4, occupancy 4,
+    # availability 1), the breaking draws (partner slots 16, reactions 4, tag 4) and the apply
+    # phase (break bits 4, formed partner 4, best key 8 + 8, proposal 4, push key 16, slots 16);
+    # per neighbour entry scanned by a free site: index 4, availability 1, coordinates 16
+    sweep_bytes = (9 + 24 + 60) * n + 21 * st2["scanned"]
+    sweep_gbs = sweep_bytes / (ph["sweep"] / 1e3) / 1e9 if ph["sweep"] > 0 else None
 
     # kernels launched: per step the rebuild condition, the sweep (begin + 4 per
     # reaction: proposals and break draws, resolution, acceptance, apply), the
@@ -546,6 +692,10 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
         "phases_ms_per_step": {k: round(v, 5) for k, v in ph.items()},
         "rebuild_ms_per_kernel": rebuild_ms,
         "bond_update_pairs_per_s": bond_pairs_per_s,
+        "sweep_roofline": {"bound": "hbm", "algorithmic_bytes_per_sweep": sweep_bytes, "achieved": sweep_gbs,
+                           "peak": measured_peaks()[0], "unit": "GB/s",
+                           "frac": sweep_gbs / measured_peaks()[0] if sweep_gbs else None,
+                           "sweep_ms": ph["sweep"], "note": "five kernels per sweep, each latency-bound"},
         "state_at_timing": {"equilibration_steps": E, "warmup_steps": W, "n_bonds": st0["n_bonds"],
                             "colloid_slot_occupancy": st0["n_bonds"] / (4.0 * args.n_c),
                             "graphs": "captured and uploaded for both buffer parities before the timed region"},
@@ -565,7 +715,7 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
         def fp64_leg():
             sim64 = make("fp64")
             try:
-                sim64.step(E)
+                sim64.set_state(state)
                 sim64.step(W)
                 sim64.prepare()
                 barrier()
@@ -586,24 +736,30 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
 
         run_leg(out, "fp64_plain", world, fp64_leg)
         sim = make("mixed")
-        sim.step(W)
+        sim.set_state(state)
     if batch is not None:
         sim.close()
         run_leg(out, "batched", world,
                 lambda: _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream))
         sim = make("mixed")
-        sim.step(W)
+        sim.set_state(state)
+    if args.small_legs:
+        sim.close()
+        run_leg(out, "assoc_ab", world, lambda: _run_assoc_ab(args, torch, snap, max_all, sum_all, stream))
+        run_leg(out, "telechelic", world, lambda: _run_telechelic(args, torch, snap, max_all, sum_all, stream))
+        sim = make("mixed")
+        sim.set_state(state)
     if args.competing_n > 0:
         sim.close()
         run_leg(out, "competing", world,
                 lambda: _run_competing(args, torch, snap, barrier, max_all, sum_all, stream))
         sim = make("mixed")
-        sim.step(W)
+        sim.set_state(state)
     if args.learned_events > 0:
         sim.close()
         run_leg(out, "learned", world, lambda: _run_learned(args, torch, snap, rank, stream))
         sim = make("mixed")
-        sim.step(W)
+        sim.set_state(state)
     if not args.no_e2e:
         # end to end through the C ABI with host buffers in pinned memory: every
         # step uploads positions + velocities, runs one step and reads the
@@ -612,31 +768,54 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
         pos, vel = pin(), pin()
         sim.positions(out=pos)
         sim.velocities(out=vel)
-        E = args.e2e_steps
+        n_e2e = args.e2e_steps
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(E):
+        for _ in range(n_e2e):
             sim.set_positions(pos, vel)
             sim.step(1)
             sim.positions(out=pos)
         torch.cuda.synchronize()
         te = max_all(time.perf_counter() - t0)
-        out["e2e"] = {"value": n_all * E / te, "unit": UNIT, "h2d_bytes_per_step": 48 * n,
-                      "d2h_bytes_per_step": 24 * n, "steps": E,
+        out["e2e"] = {"value": n_all * n_e2e / te, "unit": UNIT, "h2d_bytes_per_step": 48 * n,
+                      "d2h_bytes_per_step": 24 * n, "steps": n_e2e,
                       "what": "per step from pinned host buffers: snap_set_positions (positions + "
                               "velocities), snap_step(1) (the new positions force a list rebuild), "
                               "snap_get_positions (to host)"}
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         o = oracle.OracleSystem(s)
+        # the oracle at the GPU's equilibrated state: its forces against the GPU's in both
+        # precisions, and one sweep against the GPU's sweep there (untimed)
+        o.set_positions(eq_check["pos"])
+        o.set_velocities(eq_check["vel"])
+        o.set_bonds(eq_check["bonds"])
+        o.step = int(eq_check["step"])
+        f_o, e_o = o.forces()
+        errs = {}
+        for prec in ("mixed", "fp64"):
+            d = np.linalg.norm(eq_check["f_" + prec] - f_o, axis=1)
+            sc = e_o["fscale"]
+            errs[prec] = {"normwise": float(np.linalg.norm(d) / np.linalg.norm(f_o)),
+                          "max_per_particle_vs_sensitivity_scale": float(np.max(d[sc > 0] / sc[sc > 0]))}
+        st_o = o.sweep(step=o.step)
+        gs = eq_check["sweep_stats"]
+        out["oracle_check"] = {
+            "state": f"the equilibrated gel after {E} steps ({int(eq_check['bonds'].shape[0])} bonds)",
+            "forces": errs, "force_tolerance": {"mixed": 1e-5, "fp64": 1e-12},
+            "sweep_bit_exact": bool(np.array_equal(eq_check["bonds_after_sweep"], o.bonds()) and
+                                    all(gs[k] == st_o[k] for k in ("in_window", "proposals", "edges", "survivors",
+                                                                   "formed", "break_tested", "broken"))),
+            "sweep_counters": {k: int(st_o[k]) for k in ("proposals", "formed", "broken")}}
         t0 = time.perf_counter()
         o.run(args.cpu_steps)
         tc = time.perf_counter() - t0
         out["cpu_baseline"] = {"value": n * args.cpu_steps / tc, "unit": UNIT, "cores": 1,
                                "kind": "oracle",
                                "sample": f"{args.cpu_steps} full MD steps (sweep, forces, Langevin) "
-                                         f"of the same {n}-particle gel, single thread, FP64"}
+                                         f"of the same {n}-particle gel from its equilibrated state, "
+                                         "single thread, FP64"}
     if rank == 0:
         print(json.dumps(out), flush=True)
 

@@ -58,10 +58,14 @@ def choose(trials):
 
 
 def autotune(systems, precision="mixed", blocks=BLOCKS, skins=SKINS, steps=60, warmup=30,
-             cache_path: Path = DEFAULT_CACHE, use_cache=True, timer=None):
+             cache_path: Path = DEFAULT_CACHE, use_cache=True, timer=None, state=None):
     """Pick (block_size, skin) for these systems.  `systems` is one synth
-    System or a list of them (a batched context).  `timer(cfg) -> ms/step` may
-    replace the GPU timing (used by the host-side tests)."""
+    System or a list of them (a batched context).  `state` (bytes from
+    Snap.get_state of a context over the same systems) starts every trial from
+    that state instead of the systems' own coordinates, so that the choice is
+    made in the regime that will be run (e.g. an equilibrated gel rather than
+    its bond-free start).  `timer(cfg) -> ms/step` may replace the GPU timing
+    (used by the host-side tests)."""
     systems = systems if isinstance(systems, (list, tuple)) else [systems]
     n = sum(s.n for s in systems)
     vol = sum(float(s.box[0] * s.box[1] * s.box[2]) for s in systems)
@@ -74,7 +78,7 @@ def autotune(systems, precision="mixed", blocks=BLOCKS, skins=SKINS, steps=60, w
     if use_cache and key in cache:
         return dict(cache[key], cached=True, key=key)
     if timer is None:
-        timer = _gpu_timer(systems, precision, steps, warmup)
+        timer = _gpu_timer(systems, precision, steps, warmup, state)
     trials = []
     for skin in skins:
         for block in blocks:
@@ -92,7 +96,7 @@ def autotune(systems, precision="mixed", blocks=BLOCKS, skins=SKINS, steps=60, w
     return dict(best, cached=False, key=key)
 
 
-def _gpu_timer(systems, precision, steps, warmup):
+def _gpu_timer(systems, precision, steps, warmup, state=None):
     import torch
     from . import from_system
 
@@ -100,7 +104,10 @@ def _gpu_timer(systems, precision, steps, warmup):
         sim = from_system(systems if len(systems) > 1 else systems[0], precision=precision,
                           block_size=cfg["block_size"], skin=cfg["skin"])
         try:
+            if state is not None:
+                sim.set_state(state)
             sim.step(warmup)
+            sim.prepare()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             stream = torch.cuda.current_stream()

@@ -187,3 +187,24 @@ def test_batched_sweep_smallest_replicas_match_oracle(snapmod):
         se = f.reshape(blocks, -1).mean(1).std(ddof=1) / math.sqrt(blocks)
         z = (f.mean() - g["bonded_fraction"]) / math.sqrt(se ** 2 + g["bonded_fraction_se"] ** 2 + 1e-6)
         assert abs(z) < 4.0, (g["replica"], f.mean(), g["bonded_fraction"], se, g["bonded_fraction_se"])
+
+
+def test_telechelic_network_bonded_fraction_matches_oracle(snapmod):
+    """Telechelic network (2000 chains x 12 + 4000 crosslinkers), mixed precision:
+    the bonded fraction of chain ends over steps 500-1000 agrees with the FP64
+    oracle run (tests/golden/telechelic_network.json) within both error bars."""
+    from synth import telechelic
+    gold = json.loads((GOLDEN / "telechelic_network.json").read_text())
+    s = telechelic()
+    assert s.n == gold["n"]
+    sim = snapmod.from_system(s, precision="mixed")
+    sim.step(gold["from"])
+    f = []
+    for _ in range((gold["steps"] - gold["from"]) // gold["every"]):
+        sim.step(gold["every"])
+        f.append(sim.stats()["n_bonds"] / gold["n_ends"])
+    sim.close()
+    f = np.array(f)
+    se = f.reshape(gold["blocks"], -1).mean(1).std(ddof=1) / math.sqrt(gold["blocks"])
+    z = (f.mean() - gold["bonded_fraction"]) / math.sqrt(se ** 2 + gold["bonded_fraction_se"] ** 2)
+    assert abs(z) < 4.0, (f.mean(), gold["bonded_fraction"], se, gold["bonded_fraction_se"])
