@@ -1923,7 +1923,8 @@ extern "C" snap_status snap_set_mh(snap_ctx *c, int32_t mode, const snap_mlp *ml
             for (void *p : {(void *)A.mh_key, (void *)A.mh_count, (void *)A.mh_start, (void *)A.mh_cursor,
                             (void *)A.mh_order, (void *)A.mh_bsum, (void *)A.mh_gate, (void *)A.mv_type,
                             (void *)A.mv_i, (void *)A.mv_j, (void *)A.mv_n, (void *)A.mv_b, (void *)A.mv_c,
-                            (void *)A.mv_cand, (void *)A.mv_r, (void *)A.mv_feat, (void *)A.mv_logit})
+                            (void *)A.mv_cand, (void *)A.mv_r, (void *)A.mv_feat, (void *)A.mv_logit,
+                            (void *)A.mv_row0, (void *)A.mv_rows})
                 dfree(c, p);
             bool ok = alloc_arr(c, A.mh_key, n) && alloc_arr(c, A.mh_count, cells) &&
                       alloc_arr(c, A.mh_start, cells + 1) && alloc_arr(c, A.mh_cursor, cells) &&
@@ -1932,12 +1933,15 @@ extern "C" snap_status snap_set_mh(snap_ctx *c, int32_t mode, const snap_mlp *ml
                       alloc_arr(c, A.mv_n, moves) && alloc_arr(c, A.mv_b, moves) && alloc_arr(c, A.mv_c, moves) &&
                       alloc_arr(c, A.mv_cand, moves * kMhCand) && alloc_arr(c, A.mv_r, moves * kMhCand) &&
                       alloc_arr(c, A.mv_feat, moves * kMhCand * kMlpFeatures) &&
-                      alloc_arr(c, A.mv_logit, moves * kMhCand);
+                      alloc_arr(c, A.mv_logit, moves * kMhCand) && alloc_arr(c, A.mv_row0, moves) &&
+                      alloc_arr(c, A.mv_rows, 1);
             if (!ok) return fail(c, SNAP_ERR_OOM, "Metropolis-Hastings arrays");
             const int32_t one = 1;
             CUDA_TRY(c, cudaMemsetAsync(A.mh_count, 0, sizeof(int32_t) * cells, c->stream));
             CUDA_TRY(c, cudaMemsetAsync(A.mh_cursor, 0, sizeof(int32_t) * cells, c->stream));
             CUDA_TRY(c, cudaMemsetAsync(A.mv_feat, 0, sizeof(float) * moves * kMhCand * kMlpFeatures, c->stream));
+            CUDA_TRY(c, cudaMemsetAsync(A.mv_rows, 0, sizeof(int32_t), c->stream));
+            CUDA_TRY(c, cudaMemsetAsync(A.mv_row0, 0, sizeof(int32_t) * moves, c->stream));
             CUDA_TRY(c, cudaMemcpyAsync(A.mh_gate, &one, sizeof one, cudaMemcpyHostToDevice, c->stream));
             CUDA_TRY(c, cudaStreamSynchronize(c->stream));
             c->mh_alloc = true;

@@ -20,6 +20,8 @@
 // Active cells are more than 2 r_max apart, so their moves touch disjoint
 // particles and candidate sets: one thread per active cell.
 #include "snap_kernels.h"
+#include <algorithm>
+
 #include "snap_mlp.h"
 
 namespace snap {
@@ -181,6 +183,7 @@ __global__ void k_mh_key(DevParams P, DevArrays A)
     long long step;
     if (!mh_active<FORCED>(P, A, step)) return;
     const long long i = gtid();
+    if (i == 0 && A.mv_rows) *A.mv_rows = 0;   // the learned proposal's row count restarts every sweep
     if (i >= P.n) return;
     const int t = A.type[i];
     A.mh_key[i] = -1;
@@ -243,6 +246,7 @@ __global__ void __launch_bounds__(128) k_mh_select(DevParams P, DevArrays A)
     if (!mh_active<FORCED>(P, A, step)) return;
     const long long m = gtid();
     unsigned long long fa = 0, ba = 0;
+    int nrow = 0;                         // candidate rows this move gives the network
     if (m < P.mh_moves) {
         const RepDev &R = A.reps[0];
         const int a = 0;
@@ -270,14 +274,7 @@ __global__ void __launch_bounds__(128) k_mh_select(DevParams P, DevArrays A)
                         A.mv_b[m] = breakable(P, A, R, a, i, bj, br) + 1;
                         A.mv_c[m] = (int)(((unsigned long long)d1.z * (unsigned long long)n) >> 32);
                         type = 1;
-                        if (LEARNED) {
-                            const int ci = coord_count(P, A, R, a, i);
-                            for (int k = 0; k < n; ++k) {
-                                const int j = cand[k];
-                                pair_features(P, A, a, i, j, A.occ[i], A.occ[j], ci, coord_count(P, A, R, a, j),
-                                              cr[k], A.mv_feat + (m * kMhCand + k) * kMlpFeatures);
-                            }
-                        }
+                        nrow = n;
                     }
                 }
             } else {
@@ -300,24 +297,82 @@ __global__ void __launch_bounds__(128) k_mh_select(DevParams P, DevArrays A)
                         A.mv_c[m] = idx;
                         cr[idx] = br[pick];
                         type = 2;
-                        if (LEARNED) {
-                            const int ci = coord_count(P, A, R, a, i);
-                            for (int k = 0; k < n2; ++k) {
-                                const int q = cand[k];
-                                pair_features(P, A, a, i, q, A.occ[i] - 1, A.occ[q] - (q == j ? 1 : 0), ci,
-                                              coord_count(P, A, R, a, q), cr[k],
-                                              A.mv_feat + (m * kMhCand + k) * kMlpFeatures);
-                            }
-                        }
+                        nrow = n2;
                     }
                 }
             }
         }
         A.mv_type[m] = type;
     }
+    if (LEARNED) {
+        // Rows of live moves only, packed: one reservation per warp (moves with
+        // no candidate row give the network nothing to score); a row's logit
+        // depends on its own features alone, so where it lands does not matter.
+        int incl = nrow;
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        int base = 0;
+        if (lane == 31 && total > 0) base = atomicAdd(A.mv_rows, total);
+        base = __shfl_sync(0xFFFFFFFFu, base, 31);
+        if (nrow > 0) A.mv_row0[m] = base + incl - nrow;
+    }
     const int idx[2] = {cMhFormAtt, cMhBreakAtt};
     const unsigned long long v[2] = {fa, ba};
     warp_counts<2>(A.counters, idx, v);
+}
+
+// Features of the learned proposal's candidate rows, one warp per live move:
+// the coordination counts of the initiator and of each candidate (partner-type
+// particles inside the formation window, exact FP64 distances as everywhere in
+// the sweep) are counted by the 32 lanes over the particle's reactive list and
+// summed over the warp; lane k then writes candidate k's row.  (A thread per
+// move counting n + 1 lists one entry at a time held the FP64 pipe with one
+// lane active.)
+template <bool FORCED>
+__global__ void __launch_bounds__(128) k_mh_features(DevParams P, DevArrays A)
+{
+    long long step;
+    if (!mh_active<FORCED>(P, A, step)) return;
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    const RepDev &R = A.reps[0];
+    const int a = 0;
+    for (long long m = gtid() >> 5; m < P.mh_moves; m += nw) {
+        const int type = A.mv_type[m];
+        if (type == 0) continue;                         // uniform over the warp
+        const int i = A.mv_i[m], n = A.mv_n[m], row0 = A.mv_row0[m];
+        const int jb = type == 2 ? A.mv_j[m] : -1;       // break: features of the state without i-j
+        const int *cand = A.mv_cand + m * kMhCand;
+        int ci = 0, my_c = 0;
+        for (int p = 0; p <= n; ++p) {
+            const int x = p == 0 ? i : cand[p - 1];
+            const int pt = partner_type(P, a, A.type[x]);
+            const int nn = A.rnn[x];
+            int cnt = 0;
+            for (int k = lane; k < nn; k += 32) {
+                const int y = A.rnbr[(long long)k * P.nbr_stride + x];
+                if (A.type[y] != pt) continue;
+                const double r2 = exact_r2(A, R, x, y);
+                if (r2 >= P.rx_rmin2[a] && r2 <= P.rx_rmax2[a]) ++cnt;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+            if (p == 0) ci = cnt;
+            else if (lane == p - 1) my_c = cnt;
+        }
+        if (lane < n) {
+            const int q = cand[lane];
+            const int oi = type == 2 ? A.occ[i] - 1 : A.occ[i];
+            const int oq = A.occ[q] - (q == jb ? 1 : 0);
+            pair_features(P, A, a, i, q, oi, oq, ci, my_c, A.mv_r[m * kMhCand + lane],
+                          A.mv_feat + (long long)(row0 + lane) * kMlpFeatures);
+        }
+    }
 }
 
 // proposal probability of candidate k among n (softmax mixture or uniform)
@@ -400,7 +455,7 @@ __global__ void __launch_bounds__(128) k_mh_decide(DevParams P, DevArrays A)
         const U4 d2 = pair_draw(R, a, kMhAcc, step, (uint32_t)c, 0u);
         const double u = u53(d2.x, d2.y);
         const double K = __ddiv_rn(R.p_on0[a], R.p_off[a]);
-        const float *logit = A.mv_logit + m * kMhCand;
+        const float *logit = LEARNED ? A.mv_logit + A.mv_row0[m] : nullptr;
         if (type == 1) {
             int k = A.mv_c[m];
             if (LEARNED) {
@@ -516,7 +571,10 @@ void launch_mh_sweep(const DevParams &P, const DevArrays &A, bool forced, const 
     if (mlp) {
         if (forced) k_mh_select<true, true><<<gm, 128, 0, L.stream>>>(P, A);
         else k_mh_select<false, true><<<gm, 128, 0, L.stream>>>(P, A);
-        mlp_forward(*mlp, A.mv_feat, (long long)P.mh_moves * kMhCand, A.mv_logit, L.stream);
+        const unsigned gf = (unsigned)std::min<long long>((P.mh_moves + 3) / 4, 148LL * 16);
+        if (forced) k_mh_features<true><<<gf, 128, 0, L.stream>>>(P, A);
+        else k_mh_features<false><<<gf, 128, 0, L.stream>>>(P, A);
+        mlp_forward_counted(*mlp, A.mv_feat, A.mv_rows, (long long)P.mh_moves * kMhCand, A.mv_logit, L.stream);
         if (forced) k_mh_decide<true, true><<<gm, 128, 0, L.stream>>>(P, A);
         else k_mh_decide<false, true><<<gm, 128, 0, L.stream>>>(P, A);
     } else {

@@ -134,13 +134,19 @@ __device__ __forceinline__ void tile_forward(const SmemW &s, const float *X, lon
     y_hi = yhi + s.b3;
 }
 
-__global__ void __launch_bounds__(128) k_mlp_forward(MlpDev M, const float *X, long long rows, float *y)
+// rows_dev (nullable): the row count is read on the device (rows is then only
+// the capacity the grid was sized for); blocks without a tile return before
+// staging the weights.
+__global__ void __launch_bounds__(128) k_mlp_forward(MlpDev M, const float *X, long long rows, float *y,
+                                                     const int32_t *rows_dev)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemW &s = *reinterpret_cast<SmemW *>(smem_raw);
+    if (rows_dev) rows = min(rows, (long long)*rows_dev);
+    const long long ntile = (rows + 15) / 16;
+    if ((long long)blockIdx.x * (blockDim.x >> 5) >= ntile) return;   // uniform over the block
     load_weights(s, M);
     const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-    const long long ntile = (rows + 15) / 16;
     const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long tile = wid; tile < ntile; tile += nw) {
@@ -377,7 +383,17 @@ cudaError_t mlp_forward(const MlpDev &M, const float *X, long long rows, float *
     if (rows <= 0) return cudaSuccess;
     const long long tiles = (rows + 15) / 16;
     int blocks = (int)std::min<long long>((tiles + 3) / 4, 148 * 8);
-    k_mlp_forward<<<blocks, 128, mlp_forward_smem(), s>>>(M, X, rows, y);
+    k_mlp_forward<<<blocks, 128, mlp_forward_smem(), s>>>(M, X, rows, y, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_forward_counted(const MlpDev &M, const float *X, const int32_t *rows_dev, long long max_rows,
+                                float *y, cudaStream_t s)
+{
+    if (max_rows <= 0) return cudaSuccess;
+    const long long tiles = (max_rows + 15) / 16;
+    int blocks = (int)std::min<long long>((tiles + 3) / 4, 148 * 8);
+    k_mlp_forward<<<blocks, 128, mlp_forward_smem(), s>>>(M, X, max_rows, y, rows_dev);
     return cudaGetLastError();
 }
 

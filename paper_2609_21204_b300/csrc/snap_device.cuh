@@ -150,7 +150,9 @@ struct DevArrays {
     int32_t *mh_key, *mh_count, *mh_start, *mh_cursor, *mh_order, *mh_bsum, *mh_gate;
     int32_t *mv_type, *mv_i, *mv_j, *mv_n, *mv_b, *mv_c, *mv_cand;   // per move (active cell)
     double *mv_r;                   // kMhCand per move: separations of the candidates
-    float *mv_feat, *mv_logit;      // kMhCand x 12 features and logits per move
+    float *mv_feat, *mv_logit;      // features (12 per row) and logits of the candidate rows of all moves
+    int32_t *mv_row0;               // learned proposal: first row of move m's candidates
+    int32_t *mv_rows;               // learned proposal: rows reserved this sweep (compacted over live moves)
     // bond-formation event log (training data)
     float *ev_feat;                 // kMhCand x 12 per event
     int32_t *ev_n, *ev_label, *ev_count;

@@ -20,6 +20,9 @@ size_t mlp_forward_smem();
 size_t mlp_backward_smem();
 cudaError_t mlp_configure();
 cudaError_t mlp_forward(const MlpDev &M, const float *X, long long rows, float *y, cudaStream_t s);
+// the same with the row count read on the device (at most max_rows rows)
+cudaError_t mlp_forward_counted(const MlpDev &M, const float *X, const int32_t *rows_dev, long long max_rows,
+                                float *y, cudaStream_t s);
 cudaError_t mlp_loss_grad(const MlpDev &M, const float *X, long long rows, const int32_t *off, int32_t row_base,
                           const int32_t *label, long long events, float *y, float *dy, double *loss_sum,
                           cudaStream_t s);
