@@ -145,12 +145,21 @@ template <typename T> bool alloc_arr(snap_ctx *c, T *&p, size_t count)
 Launch launch(snap_ctx *c) { return Launch{c->stream, c->block}; }
 Launch launch_on(snap_ctx *c, cudaStream_t s) { return Launch{s, c->block}; }
 
-uint32_t morton3(uint32_t x, uint32_t y, uint32_t z)
+uint32_t morton2(uint32_t y, uint32_t z)
 {
     uint32_t m = 0;
-    for (int b = 0; b < 10; ++b)
-        m |= ((x >> b) & 1u) << (3 * b) | ((y >> b) & 1u) << (3 * b + 1) | ((z >> b) & 1u) << (3 * b + 2);
+    for (int b = 0; b < 10; ++b) m |= ((y >> b) & 1u) << (2 * b) | ((z >> b) & 1u) << (2 * b + 1);
     return m;
+}
+
+// Margin added to every list cut-off: 1e-4, or more where the FP32 wrapped
+// positions the list build compares are coarser (8 units in the last place of
+// the largest box edge).
+double list_margin(const snap_ctx *c)
+{
+    double lmax = 0.0;
+    for (const auto &R : c->reps) lmax = std::max({lmax, R.L[0], R.L[1], R.L[2]});
+    return std::max(1e-4, 8.0 * std::ldexp(1.0, std::ilogb(std::max(lmax, 1.0)) - 23));
 }
 
 double pair_rc(const snap_ctx *c, int a, int b)
@@ -249,15 +258,16 @@ void fill_params(snap_ctx *c)
     P.nhist = c->cfg.lifetime_bins;
     for (int t = 0; t < kMaxTypes; ++t) P.valence[t] = c->valence[t];
     const double skin = c->cfg.skin;
+    const double margin = list_margin(c);
     for (int a = 0; a < c->ntypes; ++a)
         for (int b = 0; b < c->ntypes; ++b) {
             const int k = a * kMaxTypes + b;
             const double rc = pair_rc(c, a, b);
             const double sig = 0.5 * (c->sigma[a] + c->sigma[b]);
             const double e = c->eps[k];
-            const double fl = rc + skin + 1e-4;
+            const double fl = rc + skin + margin;
             const double xc = reactive_cut(c, a, b);
-            const double xl = xc > 0.0 ? xc + skin + 1e-4 : 0.0;
+            const double xl = xc > 0.0 ? xc + skin + margin : 0.0;
             P.rc2d[k] = rc * rc;
             P.rc2f[k] = (float)(rc * rc);
             P.fl2f[k] = (float)(fl * fl);
@@ -379,7 +389,7 @@ snap_status ensure_ready(snap_ctx *c)
     rl_max = std::max(rf_max, rx_max);
     // the 1e-3 margin covers the FP32 cell assignment (a particle may sit up to
     // ~1e-4 outside the cell it is filed under)
-    const double cell_min = rl_max + c->cfg.skin + 1e-3;
+    const double cell_min = rl_max + c->cfg.skin + list_margin(c) + 1e-3;
     int off = 0;
     double dens_max = 0.0;
     for (auto &R : c->reps) {
@@ -403,17 +413,20 @@ snap_status ensure_ready(snap_ctx *c)
     };
     if (c->nbr_cap <= 0) c->nbr_cap = expect_cap(rf_max);
     if (c->rnbr_cap <= 0) c->rnbr_cap = rx_max > 0.0 ? expect_cap(rx_max) : 8;
-    // cell tables
+    // cell tables: cells ranked x innermost (the three cells of a row around a
+    // particle are one run of the sorted particles), rows in 2-D Morton order
+    // of (y, z) so that neighbouring rows stay close in memory
     std::vector<int32_t> rank_of(off);
     for (const auto &R : c->reps) {
         const int nx = R.nc[0], ny = R.nc[1], nz = R.nc[2];
-        std::vector<std::pair<uint32_t, int>> codes;
-        codes.reserve((size_t)nx * ny * nz);
+        std::vector<std::pair<uint32_t, int>> rows;
+        rows.reserve((size_t)ny * nz);
         for (int z = 0; z < nz; ++z)
-            for (int y = 0; y < ny; ++y)
-                for (int x = 0; x < nx; ++x) codes.emplace_back(morton3(x, y, z), (z * ny + y) * nx + x);
-        std::sort(codes.begin(), codes.end());
-        for (size_t k = 0; k < codes.size(); ++k) rank_of[R.cell_off + codes[k].second] = R.cell_off + (int)k;
+            for (int y = 0; y < ny; ++y) rows.emplace_back(morton2(y, z), z * ny + y);
+        std::sort(rows.begin(), rows.end());
+        for (size_t k = 0; k < rows.size(); ++k)
+            for (int x = 0; x < nx; ++x)
+                rank_of[R.cell_off + rows[k].second * nx + x] = R.cell_off + (int)k * nx + x;
     }
     DevArrays &A = c->A;
     const long long nkeys = (long long)off * c->ntypes;   // sort keys: type * ncell + cell
@@ -995,7 +1008,7 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
     }
     DevArrays &A = c->A;
     A.force = dalloc(c, v4 * n);
-    bool ok = A.force && alloc_arr(c, A.rtag, n) && alloc_arr(c, A.ref4, n) && alloc_arr(c, A.nn, n) && alloc_arr(c, A.rnn, n) && alloc_arr(c, A.avail, n) && alloc_arr(c, A.avail_count, kMaxTypes) &&
+    bool ok = A.force && alloc_arr(c, A.rtag, n) && alloc_arr(c, A.ref4, n) && alloc_arr(c, A.npos, n) && alloc_arr(c, A.nn, n) && alloc_arr(c, A.rnn, n) && alloc_arr(c, A.avail, n) && alloc_arr(c, A.avail_count, kMaxTypes) &&
               alloc_arr(c, A.avail_list, (size_t)kMaxTypes * n) &&
               alloc_arr(c, A.pkey, n) &&
               alloc_arr(c, A.pdist, (n / 5 + 1) * kPushSlots) &&
@@ -1013,7 +1026,7 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
     A.reps = c->d_reps;
     // B shares the non-permuted arrays with A
     DevArrays &B = c->B;
-    B.rtag = A.rtag; B.ref4 = A.ref4; B.force = A.force; B.status = A.status; B.need_rebuild = A.need_rebuild;
+    B.rtag = A.rtag; B.ref4 = A.ref4; B.npos = A.npos; B.force = A.force; B.status = A.status; B.need_rebuild = A.need_rebuild;
     B.step = A.step; B.reps = A.reps; B.order = A.order; B.ksum = A.ksum;
     if (cudaMemsetAsync(A.status, 0, 4, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.step, 0, 8, c->stream) != cudaSuccess ||

@@ -1,9 +1,10 @@
-// Cell list, Morton-ordered particle sort, neighbour list, pair + bond forces.
+// Cell list, row-ordered particle sort, neighbour list, pair + bond forces.
 //
-// Layout: particles are sorted by (type, Morton rank of their cell, tag),
-// with cells of side >= the largest neighbour cut-off.  Within one type the
-// 27 cells around a particle are nearby in memory, so neighbour gathers hit
-// L1/L2, and a warp holds particles of one type, so its lanes do similar work
+// Layout: particles are sorted by (type, rank of their cell, tag), with cells
+// of side >= the largest neighbour cut-off, ranked x innermost and rows in
+// 2-D Morton order of (y, z).  Within one type the 27 cells around a particle
+// are nearby in memory, so neighbour gathers hit L1/L2, the three cells of a
+// row are one run, and a warp holds particles of one type, so its lanes do similar work
 // (a colloid has ~2x the neighbours of a linker).  Positions
 // used by the force loop are stored relative to the origin of the particle's
 // cell (frozen between rebuilds) with the cell coordinates and type packed in
@@ -259,6 +260,7 @@ __global__ void k_gather(DevParams P, DevArrays A, DevArrays B)
     set_w_bits(p, pack_bits(t, cx, cy, cz));
     reinterpret_cast<V *>(B.pos4)[k] = p;
     A.ref4[k] = make_float4((float)rx, (float)ry, (float)rz, 0.f);
+    A.npos[k] = make_float4((float)x, (float)y, (float)z, __uint_as_float(pack_bits(t, cx, cy, cz)));
 }
 
 template <typename R>
@@ -287,31 +289,38 @@ __global__ void k_copyback(DevParams P, DevArrays A, DevArrays B)
 }
 
 // Two neighbour lists, column-major (entry k of particle i at k * stride + i):
-// the force list holds every j != i with r^2 < (pair cut + skin)^2 of the type
-// pair, the reactive list every j of a reaction-compatible type with
-// r^2 < (r_max + skin)^2.  The force loop then never visits pairs that are
-// only within reach of a bond, and the sweep never visits pairs that cannot
-// bond.  For each of the 27 surrounding cells and each type the particle's
-// distance to the cell box is compared with the larger of the two cut-offs
-// first, so short-ranged pairs (small spheres) skip most cells.  (A
-// warp-per-cell variant that tests every candidate of the 27 cells against
-// each home particle ran 1.8x slower on the colloid-linker gel: without the
-// per-particle culling it tests ~4x more pairs; a single loop whose passes
-// either open the next range or test one candidate, to keep the lanes in
-// step, ran 1.6x slower.)
-// Candidates s0..e-1 of one (cell, type) against particle i (offset o of the
-// cell): appended to the force list (F) and/or the reactive list (X).
-template <typename V, bool F, bool X>
-__device__ __forceinline__ int2 scan_range(const V *pos, int s0, int e, long long i, float ox, float oy, float oz,
-                                           float fcut2, float xcut2, int *nbr, int *rnbr, long long stride, int cap,
-                                           int rcap, int cnt, int rcnt)
+// the force list holds every j != i with r^2 < (pair cut + skin + margin)^2
+// of the type pair, the reactive list every j of a reaction-compatible type
+// with r^2 < (r_max + skin + margin)^2.  The force loop then never visits
+// pairs that are only within reach of a bond, and the sweep never visits
+// pairs that cannot bond.  Cells are ranked row by row (x innermost, rows in
+// 2-D Morton order of (y, z)), so for each of the 9 rows around a particle and
+// each type the admitted cells x-1..x+1 are one contiguous run of the sorted
+// particles: 18 candidate runs per particle instead of 54 single cells.  A
+// cell is admitted when the particle's distance to the cell box is below the
+// larger of the two cut-offs of the type pair, so short-ranged pairs (small
+// spheres) skip most cells.  Separations come from the FP32 wrapped positions
+// the rebuild stored (npos) plus a periodic shift per run; their error (a few
+// units in the last place of the box edge) is inside the list margin, and the
+// lists only need to hold every pair within reach.  (A warp-per-cell variant
+// that tests every candidate of the 27 cells against each home particle ran
+// 1.8x slower on the colloid-linker gel: without the per-particle culling it
+// tests ~4x more pairs.)
+// Candidates s0..e-1 against particle i, appended to the force list (F)
+// and/or the reactive list (X).  (Two candidates per pass, or running slot
+// pointers instead of slot arithmetic, measured no faster: the loop is bound
+// by the lanes' different trip counts, not by its instruction count.)
+template <bool F, bool X>
+__device__ __forceinline__ int2 scan_range(const float4 *npos, int s0, int e, long long i, float ox, float oy,
+                                           float oz, float fcut2, float xcut2, int *nbr, int *rnbr, long long stride,
+                                           int cap, int rcap, int cnt, int rcnt)
 {
     for (int j = s0; j < e; ++j) {
         if (j == i) continue;
-        const V q = pos[j];
-        const float ddx = (float)q.x + ox;
-        const float ddy = (float)q.y + oy;
-        const float ddz = (float)q.z + oz;
+        const float4 q = npos[j];
+        const float ddx = q.x + ox;
+        const float ddy = q.y + oy;
+        const float ddz = q.z + oz;
         const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
         if (F && r2 < fcut2) {
             if (cnt < cap) nbr[(long long)cnt * stride + i] = j;
@@ -325,79 +334,93 @@ __device__ __forceinline__ int2 scan_range(const V *pos, int s0, int e, long lon
     return make_int2(cnt, rcnt);
 }
 
-template <typename R>
+// a zero cut-off takes no pair (r^2 < 0 never holds): that list is skipped,
+// the same for every lane of a type-pure warp
+__device__ __forceinline__ int2 scan_lists(const float4 *npos, int s0, int e, long long i, float ox, float oy,
+                                           float oz, float fcut2, float xcut2, int *nbr, int *rnbr, long long stride,
+                                           int cap, int rcap, int2 c)
+{
+    if (xcut2 <= 0.f)
+        return scan_range<true, false>(npos, s0, e, i, ox, oy, oz, fcut2, xcut2, nbr, rnbr, stride, cap, rcap, c.x,
+                                       c.y);
+    if (fcut2 <= 0.f)
+        return scan_range<false, true>(npos, s0, e, i, ox, oy, oz, fcut2, xcut2, nbr, rnbr, stride, cap, rcap, c.x,
+                                       c.y);
+    return scan_range<true, true>(npos, s0, e, i, ox, oy, oz, fcut2, xcut2, nbr, rnbr, stride, cap, rcap, c.x, c.y);
+}
+
 __global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A)
 {
-    using V = typename Vec4<R>::T;
     if (!status_ok(A.status) || !*A.need_rebuild) return;   // uniform
     const long long i = gtid();
-    int cnt = 0, rcnt = 0;
+    int2 cc = make_int2(0, 0);
     const int cap = P.nbr_cap, rcap = P.rnbr_cap;
     if (i < P.n) {
-        const V *pos = reinterpret_cast<const V *>(A.pos4);
-        const V p = pos[i];
-        const uint32_t b = w_bits(p);
+        const float4 p = A.npos[i];
+        const uint32_t b = __float_as_uint(p.w);
         const int ti = bits_type(b), cx = bits_cx(b), cy = bits_cy(b), cz = bits_cz(b);
         const RepDev &Rp = A.reps[rep_of(P, A, i)];
         const int nx = Rp.nc[0], ny = Rp.nc[1], nz = Rp.nc[2];
         const float wx = Rp.wf[0], wy = Rp.wf[1], wz = Rp.wf[2];
-        const float pxf = (float)p.x, pyf = (float)p.y, pzf = (float)p.z;
+        const float Lx = (float)Rp.L[0], Ly = (float)Rp.L[1], Lz = (float)Rp.L[2];
         const long long stride = P.nbr_stride;
-        const float gxl = fmaxf(pxf, 0.f), gxu = fmaxf(wx - pxf, 0.f);
-        const float gyl = fmaxf(pyf, 0.f), gyu = fmaxf(wy - pyf, 0.f);
-        const float gzl = fmaxf(pzf, 0.f), gzu = fmaxf(wz - pzf, 0.f);
+        // distances to the faces of the home cell (the cell bits were taken from
+        // the same wrapped position: the cell test admits at least what it must)
+        const float rx = p.x - (float)cx * wx, ry = p.y - (float)cy * wy, rz = p.z - (float)cz * wz;
+        const float gxl = fmaxf(rx, 0.f), gxu = fmaxf(wx - rx, 0.f);
+        const float gyl = fmaxf(ry, 0.f), gyu = fmaxf(wy - ry, 0.f);
+        const float gzl = fmaxf(rz, 0.f), gzu = fmaxf(wz - rz, 0.f);
+        const float gxl2 = gxl * gxl, gxu2 = gxu * gxu;
         for (int dz = -1; dz <= 1; ++dz) {
             int zz = cz + dz;
-            zz += (zz < 0) ? nz : 0;
-            zz -= (zz >= nz) ? nz : 0;
+            float oz = -p.z;
+            if (zz < 0) { zz += nz; oz -= Lz; }
+            if (zz >= nz) { zz -= nz; oz += Lz; }
             const float gz = dz < 0 ? gzl : (dz > 0 ? gzu : 0.f);
             for (int dy = -1; dy <= 1; ++dy) {
                 int yy = cy + dy;
-                yy += (yy < 0) ? ny : 0;
-                yy -= (yy >= ny) ? ny : 0;
+                float oy = -p.y;
+                if (yy < 0) { yy += ny; oy -= Ly; }
+                if (yy >= ny) { yy -= ny; oy += Ly; }
                 const float gy = dy < 0 ? gyl : (dy > 0 ? gyu : 0.f);
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int xx = cx + dx;
-                    xx += (xx < 0) ? nx : 0;
-                    xx -= (xx >= nx) ? nx : 0;
-                    const float gx = dx < 0 ? gxl : (dx > 0 ? gxu : 0.f);
-                    const float d2 = gx * gx + gy * gy + gz * gz;
-                    const int c = A.rank_of[Rp.cell_off + (zz * ny + yy) * nx + xx];
-                    const float ox = dx * wx - pxf, oy = dy * wy - pyf, oz = dz * wz - pzf;
-                    for (int t = 0; t < P.ntypes; ++t) {
-                        const float fcut2 = P.fl2f[ti * kMaxTypes + t];
-                        const float xcut2 = P.xl2f[ti * kMaxTypes + t];
-                        if (d2 >= fmaxf(fcut2, xcut2)) continue;
-                        const int key = t * P.ncell + c;
-                        const int s0 = A.cell_start[key], e = A.cell_start[key + 1];
-                        // a zero cut-off takes no pair (r^2 < 0 never holds): such a
-                        // list is skipped, the same for every lane of a type-pure warp
-                        int2 cc;
-                        if (xcut2 <= 0.f)
-                            cc = scan_range<V, true, false>(pos, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr,
-                                                            stride, cap, rcap, cnt, rcnt);
-                        else if (fcut2 <= 0.f)
-                            cc = scan_range<V, false, true>(pos, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr,
-                                                            stride, cap, rcap, cnt, rcnt);
-                        else
-                            cc = scan_range<V, true, true>(pos, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr,
-                                                           stride, cap, rcap, cnt, rcnt);
-                        cnt = cc.x;
-                        rcnt = cc.y;
+                const float d2r = gy * gy + gz * gz;
+                // rank of the row's cell x = 0: the row's cells follow it in x order
+                const int row = A.rank_of[Rp.cell_off + (zz * ny + yy) * nx];
+                for (int t = 0; t < P.ntypes; ++t) {
+                    const float fcut2 = P.fl2f[ti * kMaxTypes + t];
+                    const float xcut2 = P.xl2f[ti * kMaxTypes + t];
+                    const float cut = fmaxf(fcut2, xcut2);
+                    if (d2r >= cut) continue;
+                    int xa = cx - (d2r + gxl2 < cut ? 1 : 0);
+                    int xb = cx + (d2r + gxu2 < cut ? 1 : 0);
+                    const int kb = t * P.ncell + row;
+                    // a cell across the periodic x boundary is its own run
+                    if (xa < 0) {
+                        const int k = kb + nx - 1;
+                        cc = scan_lists(A.npos, A.cell_start[k], A.cell_start[k + 1], i, -p.x - Lx, oy, oz, fcut2,
+                                        xcut2, A.nbr, A.rnbr, stride, cap, rcap, cc);
+                        xa = 0;
                     }
+                    if (xb >= nx) {
+                        cc = scan_lists(A.npos, A.cell_start[kb], A.cell_start[kb + 1], i, Lx - p.x, oy, oz, fcut2,
+                                        xcut2, A.nbr, A.rnbr, stride, cap, rcap, cc);
+                        xb = nx - 1;
+                    }
+                    cc = scan_lists(A.npos, A.cell_start[kb + xa], A.cell_start[kb + xb + 1], i, -p.x, oy, oz, fcut2,
+                                    xcut2, A.nbr, A.rnbr, stride, cap, rcap, cc);
                 }
             }
         }
-        A.nn[i] = min(cnt, cap);
-        A.rnn[i] = min(rcnt, rcap);
-        if (cnt > cap || rcnt > rcap) {
+        A.nn[i] = min(cc.x, cap);
+        A.rnn[i] = min(cc.y, rcap);
+        if (cc.x > cap || cc.y > rcap) {
             atomicOr(A.status, (uint32_t)kStOverflow);
-            atomicMax(&A.nbr_need[0], cnt);
-            atomicMax(&A.nbr_need[1], rcnt);
+            atomicMax(&A.nbr_need[0], cc.x);
+            atomicMax(&A.nbr_need[1], cc.y);
         }
     }
     const int idx[2] = {cNlistEntries, cRnlistEntries};
-    const unsigned long long v[2] = {(unsigned long long)min(cnt, cap), (unsigned long long)min(rcnt, rcap)};
+    const unsigned long long v[2] = {(unsigned long long)min(cc.x, cap), (unsigned long long)min(cc.y, rcap)};
     warp_counts<2>(A.counters, idx, v);
 }
 
@@ -788,10 +811,8 @@ void launch_copyback(const DevParams &P, const DevArrays &A, const DevArrays &B,
 void launch_nlist(const DevParams &P, const DevArrays &A, bool fp64, Launch L)
 {
     if (P.n == 0) return;
-    if (fp64)
-        k_nlist<double><<<grid_for(P.n, 256), 256, 0, L.stream>>>(P, A);
-    else
-        k_nlist<float><<<grid_for(P.n, 256), 256, 0, L.stream>>>(P, A);
+    (void)fp64;   // both precisions list from the FP32 wrapped positions
+    k_nlist<<<grid_for(P.n, 256), 256, 0, L.stream>>>(P, A);
 }
 
 void launch_rebuild_done(const DevArrays &A, Launch L) { k_rebuild_done<<<1, 1, 0, L.stream>>>(A); }

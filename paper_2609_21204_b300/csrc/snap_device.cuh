@@ -108,6 +108,7 @@ struct DevArrays {
     void *pos4;                     // float4 or double4_32a: coords relative to frozen cell origin, w = bits
     void *pos4n;                    // the second pos4 buffer: the fused step writes the new coordinates here
     float4 *ref4;                   // rel coords at the last rebuild (displacement test)
+    float4 *npos;                   // FP32 wrapped positions at the last rebuild, cell bits in w (list build)
     void *force;                    // float4 or double4_32a (w unused)
     int4 *sp;                       // static partner tags (-1 empty), kSmax per particle
     int32_t *sbt;                   // static bond types, 8 bits each, packed
