@@ -11,29 +11,44 @@
 
 namespace snap {
 
-// Runs for every thread of the grid (i >= n does nothing); returns the
-// particle's dynamic partners after the update.
-__device__ __forceinline__ int4 apply_particle(const DevParams &P, DevArrays &A, int slot, long long step,
-                                               long long i, unsigned long long &nbroken)
+// The scratch words of one particle that the apply phase reads.
+struct ApplyIn {
+    uint32_t b;        // break bits
+    int f;             // formed partner (sorted index) or -1
+    ulonglong2 k;      // push key
+    int4 dp;           // dynamic partners (tags)
+};
+
+__device__ __forceinline__ ApplyIn apply_load(const DevArrays &A, long long i)
 {
-    if (i == 0) *A.list_count = 0;   // next reaction starts an empty list
-    if (i < kMaxTypes && slot == P.nrx - 1) A.avail_count[i] = 0;   // the next sweep recounts
-    if (i >= P.n) return make_int4(-1, -1, -1, -1);
-    const uint32_t b = A.brk[i];
-    const int f = A.fpart[i];
-    // scratch for the next reaction
-    if (b != 0u) A.brk[i] = 0u;
-    if (f >= 0) A.fpart[i] = -1;
+    ApplyIn v;
+    v.b = A.brk[i];
+    v.f = A.fpart[i];
+    v.k = A.pkey[i];
+    v.dp = A.dp[i];
+    return v;
+}
+
+// The scratch of particle i cleared for the next reaction; returns whether
+// its bond slots change.
+__device__ __forceinline__ bool apply_clear(DevArrays &A, long long i, const ApplyIn &v)
+{
+    if (v.b != 0u) A.brk[i] = 0u;
+    if (v.f >= 0) A.fpart[i] = -1;
     A.best[i] = 0ull;
     A.prop[i] = -1;
-    const ulonglong2 k = A.pkey[i];
-    if (k.x != ~0ull || k.y != ~0ull) A.pkey[i] = make_ulonglong2(~0ull, ~0ull);
-    const int4 dp = A.dp[i];
-    if (b == 0u && f < 0) return dp;
+    if (v.k.x != ~0ull || v.k.y != ~0ull) A.pkey[i] = make_ulonglong2(~0ull, ~0ull);
+    return v.b != 0u || v.f >= 0;
+}
+
+// The slot update of a particle whose bonds change.
+__device__ __forceinline__ void apply_update(const DevParams &P, DevArrays &A, int slot, long long step, long long i,
+                                             const ApplyIn &v, unsigned long long &nbroken)
+{
     const int me = A.tag[i];
     const int4 db = A.dbirth[i];
     const int drx = A.drx[i];
-    const int pv[4] = {dp.x, dp.y, dp.z, dp.w};
+    const int pv[4] = {v.dp.x, v.dp.y, v.dp.z, v.dp.w};
     const int bv[4] = {db.x, db.y, db.z, db.w};
     int np[4] = {-1, -1, -1, -1}, nb[4] = {0, 0, 0, 0}, nr[4] = {0, 0, 0, 0};
     int m = 0;
@@ -41,7 +56,7 @@ __device__ __forceinline__ int4 apply_particle(const DevParams &P, DevArrays &A,
     for (int s = 0; s < kVmax; ++s) {
         const int p = pv[s];
         if (p < 0) continue;
-        if ((b >> s) & 1u) {
+        if ((v.b >> s) & 1u) {
             if (me < p) {
                 ++nbroken;
                 long long life = (long long)((uint32_t)step - (uint32_t)bv[s]) / P.period;
@@ -53,10 +68,10 @@ __device__ __forceinline__ int4 apply_particle(const DevParams &P, DevArrays &A,
         np[m] = p; nb[m] = bv[s]; nr[m] = (drx >> (8 * s)) & 0xFF;
         ++m;
     }
-    if (f >= 0) {
+    if (v.f >= 0) {
         const int rp = rep_of(P, A, i);
         const int a = rx_at(P, A, rp, slot);
-        const int pt = A.tag[f];
+        const int pt = A.tag[v.f];
         int s = m;
         while (s > 0 && np[s - 1] > pt) {
             np[s] = np[s - 1]; nb[s] = nb[s - 1]; nr[s] = nr[s - 1];
@@ -65,14 +80,12 @@ __device__ __forceinline__ int4 apply_particle(const DevParams &P, DevArrays &A,
         np[s] = pt; nb[s] = (int)(uint32_t)step; nr[s] = a;
         ++m;
     }
-    const int4 out = make_int4(np[0], np[1], np[2], np[3]);
-    A.dp[i] = out;
+    A.dp[i] = make_int4(np[0], np[1], np[2], np[3]);
     A.dbirth[i] = make_int4(nb[0], nb[1], nb[2], nb[3]);
     A.drx[i] = (nr[0] & 0xFF) | ((nr[1] & 0xFF) << 8) | ((nr[2] & 0xFF) << 16) | ((nr[3] & 0xFF) << 24);
     A.occ[i] = m;
     const int t = A.type[i];
     A.avail[i] = m < P.valence[t] ? (uint8_t)t : (uint8_t)0xFF;
-    return out;
 }
 
 }  // namespace snap

@@ -46,15 +46,20 @@ __device__ __forceinline__ bool sweep_active(const DevParams &P, const DevArrays
 constexpr int kListBlocks = 296;
 constexpr int kSweepBeginBlock = 256;
 
-// Sweep start (one thread per particle): counters reset, the reaction order
-// per replica (Fisher–Yates driven by Philox(ORDER) with counter (step, k), so
-// competing reactions are treated evenhandedly), the availability byte of
-// every particle (its type while it has a free valence slot, else 0xFF) with
-// the count per type.  The per-reaction scratch (best, fpart, brk, prop, the
-// push keys) starts clear and k_apply clears it after each reaction: a sweep
-// either runs to its end or (a latched status) none of its kernels act.
+// Sweep start: counters reset, the reaction order per replica
+// (Fisher–Yates driven by Philox(ORDER) with counter (step, k), so competing
+// reactions are treated evenhandedly), the availability byte of every
+// particle (its type while it has a free valence slot, else 0xFF) with the
+// count per type.  Each thread takes kBeginItems particles of its block's
+// tile, their loads issued together, so that the grid is one wave of resident
+// blocks instead of several waves of one dependent load chain each.  The
+// per-reaction scratch (best, fpart, brk, prop, the push keys) starts clear
+// and k_apply clears it after each reaction: a sweep either runs to its end
+// or (a latched status) none of its kernels act.
+constexpr int kBeginItems = 4;
+
 template <bool FORCED>
-__global__ void k_sweep_begin(DevParams P, DevArrays A)
+__global__ void __launch_bounds__(kSweepBeginBlock) k_sweep_begin(DevParams P, DevArrays A)
 {
     long long step;
     if (!sweep_active<FORCED>(P, A, step)) return;
@@ -65,23 +70,33 @@ __global__ void k_sweep_begin(DevParams P, DevArrays A)
         counter_add1(A.counters, cSweeps, 1ull);
         *A.list_count = 0;
     }
-    int av = -1;
-    if (r < P.n) {
-        const int t = A.type[r];
-        av = A.occ[r] < P.valence[t] ? t : -1;
-        A.avail[r] = av >= 0 ? (uint8_t)t : (uint8_t)0xFF;
+    const long long base = (long long)blockIdx.x * (kSweepBeginBlock * kBeginItems) + threadIdx.x;
+    int ty[kBeginItems], oc[kBeginItems], av[kBeginItems];
+#pragma unroll
+    for (int u = 0; u < kBeginItems; ++u) {
+        const long long q = base + u * kSweepBeginBlock;
+        ty[u] = q < P.n ? A.type[q] : -1;
+        oc[u] = q < P.n ? A.occ[q] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kBeginItems; ++u) {
+        const long long q = base + u * kSweepBeginBlock;
+        av[u] = (ty[u] >= 0 && oc[u] < P.valence[ty[u]]) ? ty[u] : -1;
+        if (q < P.n) A.avail[q] = av[u] >= 0 ? (uint8_t)av[u] : (uint8_t)0xFF;
     }
     // per-type counts and (single system, single reaction: the only case push
     // mode serves) compacted lists; one global atomic per block and type
     const bool lists = P.nrep == 1 && P.nrx == 1;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __shared__ int s_cnt[kMaxTypes], s_base[kMaxTypes], s_woff[kSweepBeginBlock / 32][kMaxTypes];
+    __shared__ int s_cnt[kMaxTypes], s_base[kMaxTypes], s_woff[kBeginItems][kSweepBeginBlock / 32][kMaxTypes];
     if (threadIdx.x < kMaxTypes) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int t = 0; t < P.ntypes; ++t) {
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, av == t);
-        if (lane == 0) s_woff[wid][t] = m ? atomicAdd(&s_cnt[t], __popc(m)) : 0;
-    }
+#pragma unroll
+    for (int u = 0; u < kBeginItems; ++u)
+        for (int t = 0; t < P.ntypes; ++t) {
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, av[u] == t);
+            if (lane == 0) s_woff[u][wid][t] = m ? atomicAdd(&s_cnt[t], __popc(m)) : 0;
+        }
     __syncthreads();
     if (threadIdx.x < P.ntypes) {
         const int t = threadIdx.x;
@@ -89,12 +104,14 @@ __global__ void k_sweep_begin(DevParams P, DevArrays A)
     }
     __syncthreads();
     if (lists) {
-        for (int t = 0; t < P.ntypes; ++t) {
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, av == t);
-            if (av == t)
-                A.avail_list[(long long)t * P.n + s_base[t] + s_woff[wid][t] + __popc(m & ((1u << lane) - 1u))] =
-                    (int)r;
-        }
+#pragma unroll
+        for (int u = 0; u < kBeginItems; ++u)
+            for (int t = 0; t < P.ntypes; ++t) {
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, av[u] == t);
+                if (av[u] == t)
+                    A.avail_list[(long long)t * P.n + s_base[t] + s_woff[u][wid][t] + __popc(m & ((1u << lane) - 1u))] =
+                        (int)(base + u * kSweepBeginBlock);
+            }
     }
     if (r >= P.nrep) return;
     RepDev &R = A.reps[r];
@@ -657,18 +674,18 @@ __device__ __forceinline__ double slip_p_off(double p0, double k, double r0, dou
 // SLIP: the draws of slip reactions (Eq. slip), which run in a kernel of
 // their own (k_break_slip) so that the proposal kernel, which hosts the
 // constant-P_off draws, keeps its registers; each kind skips the other's.
+// (dp, me, drx: the particle's slots, tag and packed reactions, loaded by the
+// caller so that several particles' loads can be in flight together.)
 template <bool SLIP>
 __device__ __forceinline__ void break_particle(const DevParams &P, DevArrays &A, int slot, long long step, long long i,
+                                               const int4 dp, const int me, const int drx,
                                                unsigned long long &tested)
 {
-    const int4 dp = A.dp[i];
     if (dp.x < 0) return;
     const int rp = rep_of(P, A, i);
     const int a = rx_at(P, A, rp, slot);
     if ((((P.slip_mask >> a) & 1) != 0) != SLIP) return;
     const RepDev &R = A.reps[rp];
-    const int me = A.tag[i];
-    const int drx = A.drx[i];
     const int pv[4] = {dp.x, dp.y, dp.z, dp.w};
 #pragma unroll
     for (int s = 0; s < kVmax; ++s) {
@@ -706,6 +723,36 @@ __device__ __forceinline__ void break_particle(const DevParams &P, DevArrays &A,
     }
 }
 
+// The breaking draws over all particles, grid-stride, kBreakItems particles
+// per thread and pass: the slot words of all of them are loaded first, then
+// the tags and reactions of the bonded ones, then the draws.
+constexpr int kBreakItems = 4;
+
+template <bool SLIP>
+__device__ __forceinline__ void break_pass(const DevParams &P, DevArrays &A, int slot, long long step,
+                                           unsigned long long &tested)
+{
+    const long long T = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = gtid(); i0 < P.n; i0 += T * kBreakItems) {
+        int4 dp[kBreakItems];
+        int me[kBreakItems], drx[kBreakItems];
+#pragma unroll
+        for (int u = 0; u < kBreakItems; ++u) {
+            const long long i = i0 + u * T;
+            dp[u] = i < P.n ? A.dp[i] : make_int4(-1, -1, -1, -1);
+        }
+#pragma unroll
+        for (int u = 0; u < kBreakItems; ++u) {
+            const long long i = i0 + u * T;
+            me[u] = dp[u].x >= 0 ? A.tag[i] : 0;
+            drx[u] = dp[u].x >= 0 ? A.drx[i] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kBreakItems; ++u)
+            break_particle<SLIP>(P, A, slot, step, i0 + u * T, dp[u], me[u], drx[u], tested);
+    }
+}
+
 // The two proposal kernels of a reaction: each runs the scan (pull) or the
 // push version of its phase, as push_type decides for this reaction, so the
 // mode that is not used costs no launch.  The first also draws the breaking
@@ -720,8 +767,7 @@ __global__ void __launch_bounds__(256, 4) k_proposals(DevParams P, DevArrays A, 
     if (s >= 0) push_pass1(P, A, slot, step, s);
     else pull_propose<SCREEN>(P, A, slot);
     unsigned long long tested = 0;
-    for (long long i = gtid(); i < P.n; i += (long long)gridDim.x * blockDim.x)
-        break_particle<false>(P, A, slot, step, i, tested);
+    break_pass<false>(P, A, slot, step, tested);
     const int idx[1] = {cBreakTested};
     const unsigned long long v[1] = {tested};
     warp_counts<1>(A.counters, idx, v);
@@ -736,8 +782,7 @@ __global__ void __launch_bounds__(256) k_break_slip(DevParams P, DevArrays A, in
     long long step;
     if (!sweep_active<FORCED>(P, A, step)) return;
     unsigned long long tested = 0;
-    for (long long i = gtid(); i < P.n; i += (long long)gridDim.x * blockDim.x)
-        break_particle<true>(P, A, slot, step, i, tested);
+    break_pass<true>(P, A, slot, step, tested);
     const int idx[1] = {cBreakTested};
     const unsigned long long v[1] = {tested};
     warp_counts<1>(A.counters, idx, v);
@@ -892,13 +937,37 @@ __global__ void k_accept(DevParams P, DevArrays A, int slot)
     warp_counts<4>(A.counters, idx, v);
 }
 
+// Apply phase: each thread takes kApplyItems particles of its block's tile,
+// the scratch loads of all of them issued before any is used (one wave of
+// resident blocks instead of several waves of one load chain each); the few
+// particles whose bonds change are updated after.
+constexpr int kApplyItems = 4;
+
 template <bool FORCED>
 __global__ void k_apply(DevParams P, DevArrays A, int slot)
 {
     long long step;
     if (!sweep_active<FORCED>(P, A, step)) return;
+    const long long g = gtid();
+    if (g == 0) *A.list_count = 0;   // next reaction starts an empty list
+    if (g < kMaxTypes && slot == P.nrx - 1) A.avail_count[g] = 0;   // the next sweep recounts
+    const long long base = (long long)blockIdx.x * (blockDim.x * kApplyItems) + threadIdx.x;
+    ApplyIn in[kApplyItems];
+#pragma unroll
+    for (int u = 0; u < kApplyItems; ++u) {
+        const long long i = base + u * blockDim.x;
+        if (i < P.n) in[u] = apply_load(A, i);
+    }
+    unsigned ch = 0u;
+#pragma unroll
+    for (int u = 0; u < kApplyItems; ++u) {
+        const long long i = base + u * blockDim.x;
+        if (i < P.n && apply_clear(A, i, in[u])) ch |= 1u << u;
+    }
     unsigned long long nbroken = 0;
-    apply_particle(P, A, slot, step, gtid(), nbroken);
+#pragma unroll
+    for (int u = 0; u < kApplyItems; ++u)
+        if ((ch >> u) & 1u) apply_update(P, A, slot, step, base + u * blockDim.x, in[u], nbroken);
     const int idx[2] = {cBroken, cBrokenTotal};
     const unsigned long long v[2] = {nbroken, nbroken};
     warp_counts<2>(A.counters, idx, v);
@@ -933,8 +1002,9 @@ template <bool FORCED>
 void sweep_begin(const DevParams &P, const DevArrays &A, Launch L)
 {
     if (P.kinetic_T && P.n > 0) k_kin_sum<FORCED><<<grid_for(P.n, 256), 256, 0, L.stream>>>(P, A);
-    k_sweep_begin<FORCED><<<grid_for(std::max<long long>(P.n, P.nrep), kSweepBeginBlock), kSweepBeginBlock, 0,
-                            L.stream>>>(P, A);
+    const long long nb = std::max<long long>((P.n + kSweepBeginBlock * kBeginItems - 1) / (kSweepBeginBlock * kBeginItems),
+                                             (P.nrep + kSweepBeginBlock - 1) / kSweepBeginBlock);
+    k_sweep_begin<FORCED><<<(unsigned)std::max<long long>(nb, 1), kSweepBeginBlock, 0, L.stream>>>(P, A);
 }
 
 template <bool FORCED>
@@ -953,7 +1023,7 @@ void sweep_reaction(const DevParams &P, const DevArrays &A, int slot, Launch L)
                         256, 0, L.stream>>>(P, A, slot);
     k_accept<FORCED><<<gl, 256, 0, L.stream>>>(P, A, slot);
     if (P.log_events) launch_log_events(P, A, slot, FORCED, L);
-    k_apply<FORCED><<<g, L.block, 0, L.stream>>>(P, A, slot);
+    k_apply<FORCED><<<std::max<unsigned>(1u, grid_for(P.n, L.block * kApplyItems)), L.block, 0, L.stream>>>(P, A, slot);
 }
 
 }  // namespace
