@@ -77,7 +77,7 @@ typedef void *(*snap_alloc_fn)(size_t bytes, void *user);
 typedef void (*snap_free_fn)(void *ptr, void *user);
 
 typedef struct {
-    int64_t n;               /* total particles (sum over replicas) */
+    int64_t n;               /* total particles (sum over replicas), below 2^27 */
     double box[3];           /* periodic box edges (single system; replica_box overrides) */
     double dt, kT, gamma;    /* time step, set-point temperature, Langevin friction */
     uint64_t seed;           /* Philox key; only the low 48 bits are used */

@@ -933,7 +933,7 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
     if (!out) return SNAP_ERR_ARG;
     *out = nullptr;
     if (!cfg) return SNAP_ERR_ARG;
-    if (cfg->n < 0 || cfg->n > (int64_t)INT32_MAX / 2) return SNAP_ERR_ARG;
+    if (cfg->n < 0 || cfg->n >= kMaxParticles) return SNAP_ERR_ARG;
     if (!(cfg->dt > 0.0) || !(cfg->kT >= 0.0) || !(cfg->gamma >= 0.0) || !(cfg->skin > 0.0)) return SNAP_ERR_ARG;
     if (cfg->precision != SNAP_FP64 && cfg->precision != SNAP_MIXED) return SNAP_ERR_ARG;
     if (cfg->bond_period < 1) return SNAP_ERR_ARG;
@@ -1015,7 +1015,7 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
               alloc_arr(c, A.cell_key, n) && alloc_arr(c, A.order, n) && alloc_arr(c, A.prop, n) &&
               alloc_arr(c, A.prop_d, n) && alloc_arr(c, A.prio, n) && alloc_arr(c, A.best, n) &&
               alloc_arr(c, A.fpart, n) && alloc_arr(c, A.brk, n) && alloc_arr(c, A.rx_order, (size_t)nrep * kMaxRx) &&
-              alloc_arr(c, A.step, 1) && alloc_arr(c, A.status, 1) && alloc_arr(c, A.need_rebuild, 1) &&
+              alloc_arr(c, A.step, 1) && alloc_arr(c, A.status, 1) && alloc_arr(c, A.need_rebuild, 1) && alloc_arr(c, A.list_fresh, 1) &&
               alloc_arr(c, A.nbr_need, 2) && alloc_arr(c, A.counters, (size_t)cNumCounters * kCopies) &&
               alloc_arr(c, A.site_list, n) && alloc_arr(c, A.list_count, 1) &&
               alloc_arr(c, A.cont, n * kContenders) && alloc_arr(c, A.ncont, n) &&
@@ -1031,6 +1031,7 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
     if (cudaMemsetAsync(A.status, 0, 4, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.step, 0, 8, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.need_rebuild, 0, 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.list_fresh, 0, 4, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.nbr_need, 0, 8, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.counters, 0, sizeof(unsigned long long) * cNumCounters * kCopies, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.list_count, 0, 4, c->stream) != cudaSuccess ||
@@ -1684,7 +1685,8 @@ extern "C" snap_status snap_get_neighbors(snap_ctx *c, int32_t *pairs, int64_t c
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
         for (int64_t i = 0; i < c->n; ++i)
             for (int k = 0; k < nn[i]; ++k) {
-                const int32_t a = tag[i], b = tag[nbr[(size_t)k * stride + i]];
+                // force-list entries carry the pair's cell shift above the index
+                const int32_t a = tag[i], b = tag[(uint32_t)nbr[(size_t)k * stride + i] & kIdxMask];
                 if (a < b) out.emplace_back(a, b);
             }
     }

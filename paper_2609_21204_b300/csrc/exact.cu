@@ -994,6 +994,7 @@ __global__ void k_step_end(DevArrays A)
 {
     if (!status_ok(A.status)) return;
     *A.step += 1;
+    *A.list_fresh = 0;   // the step's MD kernel has stored the force-list shift codes
 }
 
 inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }

@@ -434,6 +434,7 @@ __global__ void k_rebuild_done(DevArrays A)
     if (!status_ok(A.status)) return;
     if (*A.need_rebuild) {
         *A.need_rebuild = 0;
+        *A.list_fresh = 1;   // the next MD step stores the pairs' cell shifts
         counter_add1(A.counters, cBuilds, 1ull);
     }
 }
@@ -462,10 +463,10 @@ template <> struct Num<double> {
     __device__ static double rcp(double v) { return 1.0 / v; }
 };
 
-// separation (j - i) of two particles from their relative coords and cells
+// separation (j - i) of two particles from their relative coords and cells;
+// returns the code (sx + 1) + 3 (sy + 1) + 9 (sz + 1) of the cell shift
 template <typename R, typename V>
-__device__ __forceinline__ void separation(const V &pi, const V &pj, const RepDev &Rp, R &dx, R &dy,
-                                           R &dz)
+__device__ __forceinline__ uint32_t separation(const V &pi, const V &pj, const RepDev &Rp, R &dx, R &dy, R &dz)
 {
     const uint32_t bi = w_bits(pi), bj = w_bits(pj);
     const int sx = cell_delta(bits_cx(bj) - bits_cx(bi), Rp.nc[0]);
@@ -474,6 +475,7 @@ __device__ __forceinline__ void separation(const V &pi, const V &pj, const RepDe
     dx = (pj.x - pi.x) + (R)sx * Num<R>::w(Rp, 0);
     dy = (pj.y - pi.y) + (R)sy * Num<R>::w(Rp, 1);
     dz = (pj.z - pi.z) + (R)sz * Num<R>::w(Rp, 2);
+    return (uint32_t)((sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
 }
 
 template <typename R> __device__ __forceinline__ R exp_(R v);
@@ -558,20 +560,30 @@ __device__ __forceinline__ bool bond_factor(const DevParams &P, int bt, R r2, R 
     return true;
 }
 
+// How the force loop finds a pair's cell shift: from the code its list entry
+// carries (kShiftCoded), or from the cell bits of both particles, storing the
+// code in the entry for the steps that follow (kShiftStore: the first MD step
+// after a rebuild) or not (kShiftBits: force read-outs).  Force-list entries
+// hold the neighbour's index in the low kIdxBits bits and above them the code
+// (sx + 1) + 3 (sy + 1) + 9 (sz + 1) of the minimum-image shift between the
+// two frozen cells, fixed until the next rebuild like the cells themselves.
+enum ShiftMode { kShiftCoded = 0, kShiftStore = 1, kShiftBits = 2 };
+
 // Force on particle i: WCA/LJ pairs over the force list, static and dynamic
 // bonds; the energy terms when E.  Returns false (and latches the status) on
 // a FENE overstretch.
-template <typename R, bool E>
+template <typename R, bool E, int MODE>
 __device__ __forceinline__ bool force_particle(const DevParams &P, const DevArrays &A, long long i,
-                                               const typename Vec4<R>::T &pi, const RepDev &Rp, R &fx, R &fy, R &fz,
-                                               double &ep, double &eb, double &vir)
+                                               const typename Vec4<R>::T &pi, const RepDev &Rp,
+                                               const float4 *s_shift, R &fx, R &fy, R &fz, double &ep, double &eb,
+                                               double &vir)
 {
     using V = typename Vec4<R>::T;
     const V *pos = reinterpret_cast<const V *>(A.pos4);
     const int ti = bits_type(w_bits(pi));
     const int nn = A.nn[i];
     const long long stride = P.nbr_stride;
-    const int *nb = A.nbr + i;
+    int *nb = A.nbr + i;
     // bond partners first: their slot words and sorted indices are independent
     // of the pair loop, so the tag -> index loads overlap it
     const int4 dp = A.dp[i];
@@ -583,21 +595,34 @@ __device__ __forceinline__ bool force_particle(const DevParams &P, const DevArra
         for (int s = 0; s < kVmax; ++s) dj[s] = dpv[s] >= 0 ? A.rtag[dpv[s]] : -1;
     }
     // pairs in batches of four: four independent index loads, then four
-    // independent position loads, then the arithmetic in list order
+    // independent position loads, then the arithmetic in list order; the
+    // pair's cell shift comes with its list entry (s_shift: unit shifts by code)
+    const R wx = Num<R>::w(Rp, 0), wy = Num<R>::w(Rp, 1), wz = Num<R>::w(Rp, 2);
     for (int k0 = 0; k0 < nn; k0 += 4) {
-        int jj[4];
+        uint32_t ee[4];
         V pp[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) jj[u] = k0 + u < nn ? __ldg(nb + (long long)(k0 + u) * stride) : (int)i;
+        for (int u = 0; u < 4; ++u)
+            ee[u] = k0 + u >= nn ? (uint32_t)i | (13u << kIdxBits)
+                    : MODE == kShiftStore ? (uint32_t)nb[(long long)(k0 + u) * stride]   // rewritten below
+                                          : (uint32_t)__ldg(nb + (long long)(k0 + u) * stride);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) pp[u] = pos[jj[u]];
+        for (int u = 0; u < 4; ++u) pp[u] = pos[ee[u] & kIdxMask];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (k0 + u >= nn) break;
             const V pj = pp[u];
             const int tj = bits_type(w_bits(pj));
             R dx, dy, dz;
-            separation<R>(pi, pj, Rp, dx, dy, dz);
+            if (MODE == kShiftCoded) {
+                const float4 sh = s_shift[ee[u] >> kIdxBits];
+                dx = (pj.x - pi.x) + (R)sh.x * wx;
+                dy = (pj.y - pi.y) + (R)sh.y * wy;
+                dz = (pj.z - pi.z) + (R)sh.z * wz;
+            } else {
+                const uint32_t code = separation<R>(pi, pj, Rp, dx, dy, dz);
+                if (MODE == kShiftStore) nb[(long long)(k0 + u) * stride] = (int)((ee[u] & kIdxMask) | (code << kIdxBits));
+            }
             const R r2 = dx * dx + dy * dy + dz * dz;
             const int tt = ti * kMaxTypes + tj;
             if (r2 < Num<R>::rc2(P, tt)) {
@@ -662,6 +687,14 @@ __device__ __forceinline__ bool force_particle(const DevParams &P, const DevArra
     return !bad;
 }
 
+// unit cell shifts by force-list code: code = (sx + 1) + 3 (sy + 1) + 9 (sz + 1)
+__device__ __forceinline__ void fill_shift_table(float4 *s_shift)
+{
+    const int t = threadIdx.x;
+    if (t < 27) s_shift[t] = make_float4((float)(t % 3 - 1), (float)(t / 3 % 3 - 1), (float)(t / 9 - 1), 0.f);
+    __syncthreads();
+}
+
 template <typename R, bool E>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_force(DevParams P, DevArrays A)
 {
@@ -673,7 +706,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_force(DevParams
     const RepDev &Rp = A.reps[rep_of(P, A, i)];
     R fx = 0, fy = 0, fz = 0;
     double ep = 0.0, eb = 0.0, vir = 0.0;
-    force_particle<R, E>(P, A, i, pi, Rp, fx, fy, fz, ep, eb, vir);
+    force_particle<R, E, kShiftBits>(P, A, i, pi, Rp, nullptr, fx, fy, fz, ep, eb, vir);
     V f;
     f.x = fx; f.y = fy; f.z = fz; f.w = 0;
     reinterpret_cast<V *>(A.force)[i] = f;
@@ -700,6 +733,8 @@ template <typename R>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_step_md(DevParams P, DevArrays A)
 {
     using V = typename Vec4<R>::T;
+    __shared__ float4 s_shift[27];
+    fill_shift_table(s_shift);
     const long long i = gtid();
     if (i >= P.n) return;
     if (!status_ok(A.status)) return;
@@ -707,7 +742,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_step_md(DevPara
     const RepDev &Rp = A.reps[rep_of(P, A, i)];
     R fx = 0, fy = 0, fz = 0;
     double ep = 0.0, eb = 0.0, vir = 0.0;
-    if (!force_particle<R, false>(P, A, i, pi, Rp, fx, fy, fz, ep, eb, vir)) return;
+    // the first step after a rebuild works the pairs' cell shifts out and
+    // stores them in the list (the flag is the same for the whole grid)
+    const bool ok = *A.list_fresh
+                        ? force_particle<R, false, kShiftStore>(P, A, i, pi, Rp, s_shift, fx, fy, fz, ep, eb, vir)
+                        : force_particle<R, false, kShiftCoded>(P, A, i, pi, Rp, s_shift, fx, fy, fz, ep, eb, vir);
+    if (!ok) return;
     const long long step = *A.step;
     if constexpr (sizeof(R) == 8) {
         const double fv[3] = {fx, fy, fz};

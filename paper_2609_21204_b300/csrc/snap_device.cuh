@@ -141,6 +141,7 @@ struct DevArrays {
     long long *step;                // device step counter
     uint32_t *status;
     int32_t *need_rebuild;
+    int32_t *list_fresh;            // 1 from a rebuild until an MD step has stored the force-list shift codes
     int32_t *nbr_need;              // largest [force, reactive] count seen (overflow sizing)
     unsigned long long *counters;   // sweep counters, see Counter
     unsigned long long *life_hist;
@@ -319,6 +320,15 @@ __device__ __forceinline__ int bits_type(uint32_t b) { return (int)(b & 0xF); }
 __device__ __forceinline__ int bits_cx(uint32_t b) { return (int)((b >> 4) & 0x1FF); }
 __device__ __forceinline__ int bits_cy(uint32_t b) { return (int)((b >> 13) & 0x1FF); }
 __device__ __forceinline__ int bits_cz(uint32_t b) { return (int)((b >> 22) & 0x1FF); }
+
+// Force-list entries: the neighbour's sorted index in the low 27 bits and,
+// above them (once the first MD step after the rebuild has stored it), the
+// code (sx + 1) + 3 (sy + 1) + 9 (sz + 1) of the cell shift s in {-1, 0, 1}^3
+// that takes the neighbour's frozen cell next to the particle's (the minimum
+// image); fixed until the next rebuild, like the cells.
+constexpr int kIdxBits = 27;
+constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
+constexpr long long kMaxParticles = 1ll << kIdxBits;
 
 // minimum-image cell offset (cells frozen between rebuilds)
 __device__ __forceinline__ int cell_delta(int d, int nc)
