@@ -501,7 +501,9 @@ void seq_step(snap_ctx *c)
 
 // One captured step whose neighbour-list rebuild is the body of a conditional
 // (IF) node: between rebuilds the ten rebuild kernels are not launched at all.
-cudaError_t capture_step_conditional(snap_ctx *c)
+// first: the graph's first step; the others end the step before them in the
+// condition kernel, last: the graph's last step, which ends with k_step_end.
+cudaError_t capture_step_conditional(snap_ctx *c, bool first, bool last)
 {
     const Launch L = launch(c);
     cudaStreamCaptureStatus cs;
@@ -513,7 +515,7 @@ cudaError_t capture_step_conditional(snap_ctx *c)
     cudaGraphConditionalHandle h;
     e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
     if (e != cudaSuccess) return e;
-    launch_set_rebuild_cond(c->A, h, L);
+    launch_set_rebuild_cond(c->A, h, !first, L);
     e = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, &deps, nullptr, &nd);
     if (e != cudaSuccess) return e;
     cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
@@ -535,7 +537,7 @@ cudaError_t capture_step_conditional(snap_ctx *c)
     if (e != cudaSuccess) return e;
     seq_sweep(c, false);
     seq_md(c, L);
-    launch_step_end(c->A, L);
+    if (last) launch_step_end(c->A, L);
     return cudaGetLastError();
 }
 
@@ -594,7 +596,7 @@ snap_status build_graph(snap_ctx *c, int k)
             seq_step(c);
             ce = cudaGetLastError();
         } else {
-            ce = capture_step_conditional(c);
+            ce = capture_step_conditional(c, s == 0, s == kGraphSteps - 1);
         }
     }
     c->A.pos4 = pos4_0;   // an even number of swaps; also undoes a capture that stopped early

@@ -424,9 +424,17 @@ __global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A)
     warp_counts<2>(A.counters, idx, v);
 }
 
-__global__ void k_set_rebuild_cond(DevArrays A, cudaGraphConditionalHandle h)
+// Start of a captured step: with end_prev, first the end of the step before
+// it in the same graph (what k_step_end does, one launch fewer per step),
+// then the rebuild condition.
+__global__ void k_set_rebuild_cond(DevArrays A, cudaGraphConditionalHandle h, int end_prev)
 {
-    cudaGraphSetConditional(h, (status_ok(A.status) && *A.need_rebuild) ? 1u : 0u);
+    const bool ok = status_ok(A.status);
+    if (end_prev && ok) {
+        *A.step += 1;
+        *A.list_fresh = 0;
+    }
+    cudaGraphSetConditional(h, (ok && *A.need_rebuild) ? 1u : 0u);
 }
 
 __global__ void k_rebuild_done(DevArrays A)
@@ -857,9 +865,9 @@ void launch_nlist(const DevParams &P, const DevArrays &A, bool fp64, Launch L)
 
 void launch_rebuild_done(const DevArrays &A, Launch L) { k_rebuild_done<<<1, 1, 0, L.stream>>>(A); }
 
-void launch_set_rebuild_cond(const DevArrays &A, cudaGraphConditionalHandle h, Launch L)
+void launch_set_rebuild_cond(const DevArrays &A, cudaGraphConditionalHandle h, bool end_prev, Launch L)
 {
-    k_set_rebuild_cond<<<1, 1, 0, L.stream>>>(A, h);
+    k_set_rebuild_cond<<<1, 1, 0, L.stream>>>(A, h, end_prev ? 1 : 0);
 }
 
 void launch_step_md(const DevParams &P, const DevArrays &A, bool fp64, Launch L)

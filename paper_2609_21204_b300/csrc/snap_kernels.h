@@ -24,7 +24,7 @@ void launch_copyback(const DevParams &P, const DevArrays &A, const DevArrays &B,
 void launch_nlist(const DevParams &P, const DevArrays &A, bool fp64, Launch L);
 void launch_rebuild_done(const DevArrays &A, Launch L);
 // sets a graph conditional to (*need_rebuild && status == 0)
-void launch_set_rebuild_cond(const DevArrays &A, cudaGraphConditionalHandle h, Launch L);
+void launch_set_rebuild_cond(const DevArrays &A, cudaGraphConditionalHandle h, bool end_prev, Launch L);
 
 // exclusive scan of in[0..n) into out[0..n] (runs only when *gate != 0 and status is clear)
 void launch_scan(const int32_t *in, int32_t *out, int32_t *bsum, int n, const int32_t *gate, const uint32_t *status,
