@@ -286,7 +286,8 @@ snap_status snap_step_profiled(snap_ctx *, int64_t nsteps, double *ms);
 /* One neighbour-list rebuild at the current positions (forced), each kernel
  * timed with CUDA events: ms[SNAP_NREBUILD_PHASES] = [0] cell keys, [1] scan
  * of the cell counts, [2] scatter, [3] in-cell sort, [4] gather into sorted
- * order, [5] copy back, [6] neighbour lists, [7] done flag.  Changes nothing
+ * order, [5] empty (the copy back of the gathered arrays runs inside the
+ * list build), [6] neighbour lists and copy back, [7] done flag.  Changes nothing
  * but the particle order (the state is the same physical state). */
 #define SNAP_NREBUILD_PHASES 8
 snap_status snap_rebuild_profiled(snap_ctx *, double *ms);

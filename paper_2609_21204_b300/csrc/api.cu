@@ -461,8 +461,7 @@ void seq_rebuild(snap_ctx *c, cudaStream_t stream = nullptr)
     launch_scatter(c->P, c->A, L);
     launch_cell_sort(c->A, c->nkeys, L);
     launch_gather(c->P, c->A, c->B, c->fp64, L);
-    launch_copyback(c->P, c->A, c->B, c->fp64, L);
-    launch_nlist(c->P, c->A, c->fp64, L);
+    launch_nlist(c->P, c->A, c->B, c->fp64, L);   // copies the gathered arrays back too
     launch_rebuild_done(c->A, L);
 }
 
@@ -1526,9 +1525,8 @@ extern "C" snap_status snap_rebuild_profiled(snap_ctx *c, double *ms)
     cudaEventRecord(ev[4], c->stream);
     launch_gather(c->P, c->A, c->B, c->fp64, L);
     cudaEventRecord(ev[5], c->stream);
-    launch_copyback(c->P, c->A, c->B, c->fp64, L);
-    cudaEventRecord(ev[6], c->stream);
-    launch_nlist(c->P, c->A, c->fp64, L);
+    cudaEventRecord(ev[6], c->stream);             // the copy back runs inside the list build
+    launch_nlist(c->P, c->A, c->B, c->fp64, L);
     cudaEventRecord(ev[7], c->stream);
     launch_rebuild_done(c->A, L);
     cudaEventRecord(ev[8], c->stream);

@@ -263,13 +263,14 @@ __global__ void k_gather(DevParams P, DevArrays A, DevArrays B)
     A.npos[k] = make_float4((float)x, (float)y, (float)z, __uint_as_float(pack_bits(t, cx, cy, cz)));
 }
 
+// The gathered particle k copied back from the scratch arrays B into A (run
+// by the list build, which reads none of these arrays, at the end of each
+// thread's scan: the streaming copy overlaps the latency-bound list work
+// instead of taking a kernel of its own).
 template <typename R>
-__global__ void k_copyback(DevParams P, DevArrays A, DevArrays B)
+__device__ __forceinline__ void copyback_particle(const DevParams &P, DevArrays &A, const DevArrays &B, long long k)
 {
     using V = typename Vec4<R>::T;
-    const long long k = gtid();
-    if (k >= P.n) return;
-    if (!status_ok(A.status) || !*A.need_rebuild) return;
     A.x[k] = B.x[k]; A.y[k] = B.y[k]; A.z[k] = B.z[k];
     if (sizeof(R) == 8) {
         A.vx[k] = B.vx[k]; A.vy[k] = B.vy[k]; A.vz[k] = B.vz[k];
@@ -349,7 +350,8 @@ __device__ __forceinline__ int2 scan_lists(const float4 *npos, int s0, int e, lo
     return scan_range<true, true>(npos, s0, e, i, ox, oy, oz, fcut2, xcut2, nbr, rnbr, stride, cap, rcap, c.x, c.y);
 }
 
-__global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A)
+template <typename R>
+__global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A, DevArrays B)
 {
     if (!status_ok(A.status) || !*A.need_rebuild) return;   // uniform
     const long long i = gtid();
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A)
         const float4 p = A.npos[i];
         const uint32_t b = __float_as_uint(p.w);
         const int ti = bits_type(b), cx = bits_cx(b), cy = bits_cy(b), cz = bits_cz(b);
-        const RepDev &Rp = A.reps[rep_of(P, A, i)];
+        const RepDev &Rp = A.reps[rep_of(P, B, i)];   // B: the new order (A is copied back below)
         const int nx = Rp.nc[0], ny = Rp.nc[1], nz = Rp.nc[2];
         const float wx = Rp.wf[0], wy = Rp.wf[1], wz = Rp.wf[2];
         const float Lx = (float)Rp.L[0], Ly = (float)Rp.L[1], Lz = (float)Rp.L[2];
@@ -422,6 +424,7 @@ __global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A)
     const int idx[2] = {cNlistEntries, cRnlistEntries};
     const unsigned long long v[2] = {(unsigned long long)min(cc.x, cap), (unsigned long long)min(cc.y, rcap)};
     warp_counts<2>(A.counters, idx, v);
+    if (i < P.n) copyback_particle<R>(P, A, B, i);
 }
 
 // Start of a captured step: with end_prev, first the end of the step before
@@ -847,20 +850,15 @@ void launch_gather(const DevParams &P, const DevArrays &A, const DevArrays &B, b
         k_gather<float><<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A, B);
 }
 
-void launch_copyback(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, Launch L)
+// the lists (both precisions list from the FP32 wrapped positions) and the
+// copy back of the gathered arrays
+void launch_nlist(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, Launch L)
 {
     if (P.n == 0) return;
     if (fp64)
-        k_copyback<double><<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A, B);
+        k_nlist<double><<<grid_for(P.n, 256), 256, 0, L.stream>>>(P, A, B);
     else
-        k_copyback<float><<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A, B);
-}
-
-void launch_nlist(const DevParams &P, const DevArrays &A, bool fp64, Launch L)
-{
-    if (P.n == 0) return;
-    (void)fp64;   // both precisions list from the FP32 wrapped positions
-    k_nlist<<<grid_for(P.n, 256), 256, 0, L.stream>>>(P, A);
+        k_nlist<float><<<grid_for(P.n, 256), 256, 0, L.stream>>>(P, A, B);
 }
 
 void launch_rebuild_done(const DevArrays &A, Launch L) { k_rebuild_done<<<1, 1, 0, L.stream>>>(A); }
