@@ -329,10 +329,11 @@ __global__ void __launch_bounds__(128) k_mh_select(DevParams P, DevArrays A)
 // Features of the learned proposal's candidate rows, one warp per live move:
 // the coordination counts of the initiator and of each candidate (partner-type
 // particles inside the formation window, exact FP64 distances as everywhere in
-// the sweep) are counted by the 32 lanes over the particle's reactive list and
-// summed over the warp; lane k then writes candidate k's row.  (A thread per
-// move counting n + 1 lists one entry at a time held the FP64 pipe with one
-// lane active.)
+// the sweep) are counted by the 32 lanes over the concatenated reactive lists
+// of the n + 1 particles (a ballot per list and pass); lane k then writes
+// candidate k's row.  (A thread per move counting n + 1 lists one entry at a
+// time held the FP64 pipe with one lane active; walking the lists one after
+// the other chained n + 1 dependent load sequences.)
 template <bool FORCED>
 __global__ void __launch_bounds__(128) k_mh_features(DevParams P, DevArrays A)
 {
@@ -348,23 +349,47 @@ __global__ void __launch_bounds__(128) k_mh_features(DevParams P, DevArrays A)
         const int i = A.mv_i[m], n = A.mv_n[m], row0 = A.mv_row0[m];
         const int jb = type == 2 ? A.mv_j[m] : -1;       // break: features of the state without i-j
         const int *cand = A.mv_cand + m * kMhCand;
-        int ci = 0, my_c = 0;
-        for (int p = 0; p <= n; ++p) {
-            const int x = p == 0 ? i : cand[p - 1];
-            const int pt = partner_type(P, a, A.type[x]);
-            const int nn = A.rnn[x];
-            int cnt = 0;
-            for (int k = lane; k < nn; k += 32) {
-                const int y = A.rnbr[(long long)k * P.nbr_stride + x];
-                if (A.type[y] != pt) continue;
-                const double r2 = exact_r2(A, R, x, y);
-                if (r2 >= P.rx_rmin2[a] && r2 <= P.rx_rmax2[a]) ++cnt;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
-            if (p == 0) ci = cnt;
-            else if (lane == p - 1) my_c = cnt;
+        // the n + 1 reactive lists (list 0: i's, list q: candidate q's), held by
+        // lanes 0..n and concatenated: the warp's lanes walk all their entries
+        // together, 32 per pass, instead of one list after the other
+        int x = -1, len = 0, pt = -1;
+        if (lane <= n) {
+            x = lane == 0 ? i : cand[lane - 1];
+            len = A.rnn[x];
+            pt = partner_type(P, a, A.type[x]);
         }
+        int off = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, off, o);
+            if (lane >= o) off += t;
+        }
+        const int total = __shfl_sync(0xFFFFFFFFu, off, 31);
+        off -= len;                                      // first entry of list `lane`
+        int my_cnt = 0;                                  // lane q <= n: list q's count
+        for (int e0 = 0; e0 < total; e0 += 32) {
+            const int e = e0 + lane;
+            int p = 0;                                   // the list of entry e: the last q with off_q <= e
+            for (int q = 1; q <= n; ++q)
+                if (__shfl_sync(0xFFFFFFFFu, off, q) <= e) p = q;
+            const int xp = __shfl_sync(0xFFFFFFFFu, x, p);
+            const int ptp = __shfl_sync(0xFFFFFFFFu, pt, p);
+            const int k = e - __shfl_sync(0xFFFFFFFFu, off, p);
+            bool hit = false;
+            if (e < total) {
+                const int y = A.rnbr[(long long)k * P.nbr_stride + xp];
+                if (A.type[y] == ptp) {
+                    const double r2 = exact_r2(A, R, xp, y);
+                    hit = r2 >= P.rx_rmin2[a] && r2 <= P.rx_rmax2[a];
+                }
+            }
+            for (int q = 0; q <= n; ++q) {
+                const unsigned bq = __ballot_sync(0xFFFFFFFFu, hit && p == q);
+                if (lane == q) my_cnt += __popc(bq);
+            }
+        }
+        const int ci = __shfl_sync(0xFFFFFFFFu, my_cnt, 0);
+        const int my_c = __shfl_sync(0xFFFFFFFFu, my_cnt, (lane + 1) & 31);   // candidate `lane`'s list
         if (lane < n) {
             const int q = cand[lane];
             const int oi = type == 2 ? A.occ[i] - 1 : A.occ[i];
@@ -458,13 +483,23 @@ __global__ void __launch_bounds__(128) k_mh_decide(DevParams P, DevArrays A)
         const float *logit = LEARNED ? A.mv_logit + A.mv_row0[m] : nullptr;
         if (type == 1) {
             int k = A.mv_c[m];
+            double pk = 0.0;
             if (LEARNED) {
-                // draw from the mixture with a 53-bit uniform
+                // draw from the mixture with a 53-bit uniform; the softmax's max and
+                // normaliser once per move, each candidate's probability as
+                // proposal_prob evaluates it (the same operations, so the same value)
                 const double us = u53(d1.z, d1.w);
+                float mxl = logit[0];
+                for (int cc = 1; cc < n; ++cc) mxl = fmaxf(mxl, logit[cc]);
+                double z = 0.0;
+                for (int cc = 0; cc < n; ++cc) z += exp((double)(logit[cc] - mxl));
+                const double eps = (double)P.mh_eps;
                 double acc = 0.0;
                 k = n - 1;
                 for (int cc = 0; cc < n; ++cc) {
-                    acc += proposal_prob<true>(P, logit, n, cc);
+                    const double pc = (1.0 - eps) * exp((double)(logit[cc] - mxl)) / z + eps / (double)n;
+                    acc += pc;
+                    pk = pc;
                     if (us < acc) {
                         k = cc;
                         break;
@@ -475,7 +510,7 @@ __global__ void __launch_bounds__(128) k_mh_decide(DevParams P, DevArrays A)
             const double e = bond_factor_exact(P, R, a, A.mv_r[m * kMhCand + k]);
             double ratio;
             if (LEARNED)
-                ratio = __ddiv_rn(__dmul_rn(K, e), __dmul_rn((double)b, proposal_prob<true>(P, logit, n, k)));
+                ratio = __ddiv_rn(__dmul_rn(K, e), __dmul_rn((double)b, pk));
             else
                 ratio = __ddiv_rn(__dmul_rn(__dmul_rn(K, e), (double)n), (double)b);
             if (u < ratio) {
