@@ -605,20 +605,28 @@ __device__ __forceinline__ bool force_particle(const DevParams &P, const DevArra
 #pragma unroll
         for (int s = 0; s < kVmax; ++s) dj[s] = dpv[s] >= 0 ? A.rtag[dpv[s]] : -1;
     }
-    // pairs in batches of four: four independent index loads, then four
-    // independent position loads, then the arithmetic in list order; the
-    // pair's cell shift comes with its list entry (s_shift: unit shifts by code)
+    // pairs in batches of four: four independent position loads, then the
+    // arithmetic in list order, while the next batch's four list entries are
+    // already in flight; the pair's cell shift comes with its list entry
+    // (s_shift: unit shifts by code)
     const R wx = Num<R>::w(Rp, 0), wy = Num<R>::w(Rp, 1), wz = Num<R>::w(Rp, 2);
+    auto entry = [&](int k) -> uint32_t {
+        return k >= nn ? (uint32_t)i | (13u << kIdxBits)
+               : MODE == kShiftStore ? (uint32_t)nb[(long long)k * stride]   // rewritten below
+                                     : (uint32_t)__ldg(nb + (long long)k * stride);
+    };
+    uint32_t en[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) en[u] = entry(u);
     for (int k0 = 0; k0 < nn; k0 += 4) {
         uint32_t ee[4];
         V pp[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            ee[u] = k0 + u >= nn ? (uint32_t)i | (13u << kIdxBits)
-                    : MODE == kShiftStore ? (uint32_t)nb[(long long)(k0 + u) * stride]   // rewritten below
-                                          : (uint32_t)__ldg(nb + (long long)(k0 + u) * stride);
+        for (int u = 0; u < 4; ++u) ee[u] = en[u];
 #pragma unroll
         for (int u = 0; u < 4; ++u) pp[u] = pos[ee[u] & kIdxMask];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) en[u] = entry(k0 + 4 + u);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (k0 + u >= nn) break;
