@@ -288,7 +288,7 @@ def _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream):
     from paper_2609_21204_b300 import autotune
     tune = autotune.autotune(batch, precision="mixed", steps=40, warmup=20)
     sim = snap.from_system(batch, precision="mixed", block_size=tune["block_size"],
-                           skin=tune["skin"])
+                           skin=tune["skin"], list_block=tune.get("list_block"))
     nb = sum(s.n for s in batch)
     sim.step(args.warmup)
     sim.prepare()
@@ -308,7 +308,7 @@ def _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream):
             "value": sum_all(float(nb)) * args.batch_steps / t, "unit": UNIT,
             "ms_per_step": t * 1e3 / args.batch_steps, "steps": args.batch_steps,
             "particles": nb, "replicas": len(batch), "n_bonds": st["n_bonds"],
-            "autotune": {k: tune[k] for k in ("block_size", "skin", "cached", "key")},
+            "autotune": {k: tune.get(k) for k in ("block_size", "skin", "list_block", "cached", "key")},
             "vs_oracle": _smallest_replicas_vs_oracle(snap, batch)}
 
 
@@ -618,7 +618,8 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
                                  steps=200, warmup=40, state=state)
 
     def make(precision):
-        return snap.from_system(s, precision=precision, block_size=tune["block_size"], skin=tune["skin"])
+        return snap.from_system(s, precision=precision, block_size=tune["block_size"], skin=tune["skin"],
+                                list_block=tune.get("list_block"))
 
     sim = make("mixed")
     # the equilibrated state, the warm-up, then the step graphs of both buffer
@@ -685,8 +686,9 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": t_max * 1e3 / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": dict(workload_config(args, n), block_size=tune["block_size"], skin=tune["skin"]),
-        "autotune": {k: tune.get(k) for k in ("block_size", "skin", "cached", "key", "ms_per_step")},
+        "config": dict(workload_config(args, n), block_size=tune["block_size"], skin=tune["skin"],
+                       list_block=tune.get("list_block") or 256),
+        "autotune": {k: tune.get(k) for k in ("block_size", "skin", "list_block", "cached", "key", "ms_per_step")},
         "gpu_launches": launches,
         "clocks": clk,
         "phases_ms_per_step": {k: round(v, 5) for k, v in ph.items()},

@@ -266,6 +266,12 @@ snap_status snap_step(snap_ctx *, int64_t nsteps);
  * returns SNAP_ERR_ARG. */
 snap_status snap_set_retry_limit(snap_ctx *, int32_t limit);
 
+/* Threads per block of the neighbour-list build (a launch shape the
+ * autotuner searches beside the particle kernels' block size): 64, 128 or
+ * 256 (the default); anything else returns SNAP_ERR_ARG.  The lists, and so
+ * every result, do not depend on it. */
+snap_status snap_set_list_block(snap_ctx *, int32_t threads);
+
 /* Capture, instantiate and upload the step graphs for both buffer parities
  * now, so that no later snap_step pays for a capture (a step swaps two
  * coordinate buffers; a call with an odd step count leaves the next call on

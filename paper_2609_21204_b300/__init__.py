@@ -233,6 +233,11 @@ class Snap:
         reaching it makes the step return SNAP_ERR_TIMEOUT without taking it."""
         self._check(self._lib.snap_set_retry_limit(self._ctx, int(limit)))
 
+    def set_list_block(self, threads):
+        """Threads per block of the neighbour-list build: 64, 128 or 256 (a
+        launch shape; results do not depend on it)."""
+        self._check(self._lib.snap_set_list_block(self._ctx, int(threads)))
+
     def prepare(self):
         """Capture and upload the step graphs of both buffer parities now (no
         step runs), so that no later step() pays for a capture."""
@@ -474,10 +479,11 @@ def pair_energy_noalloc(n, d_pos3, d_type, box, sigma, eps_pair, rcut=None, d_ou
         raise SnapError(code, "snap_pair_energy_noalloc")
 
 
-def from_system(sysdef, precision="mixed", p_on0=1.0, skin=None, **kw) -> Snap:
+def from_system(sysdef, precision="mixed", p_on0=1.0, skin=None, list_block=None, **kw) -> Snap:
     """Build a context from a `synth.System` (or any object with the same fields).
     A list of systems becomes one batched context of independent replicas.
-    `skin` overrides the systems' neighbour-list skin."""
+    `skin` overrides the systems' neighbour-list skin; `list_block` sets the
+    list build's threads per block."""
     systems = sysdef if isinstance(sysdef, (list, tuple)) else [sysdef]
     s0 = systems[0]
     n = sum(s.n for s in systems)
@@ -488,6 +494,8 @@ def from_system(sysdef, precision="mixed", p_on0=1.0, skin=None, **kw) -> Snap:
     sim = Snap(n, s0.box, dt=s0.dt, kT=s0.kT, gamma=s0.gamma, seed=s0.seed, precision=precision,
                bond_period=s0.bond_period, skin=s0.skin if skin is None else skin, replicas=reps, **kw)
     sim.set_types(s0.sigma, s0.eps_pair, s0.rcut)
+    if list_block:
+        sim.set_list_block(list_block)
     sim.set_valence(s0.valence)
     for i, bt in enumerate(s0.bond_types):
         sim.set_bond_params(i, bt.kind, bt.k, bt.r0, getattr(bt, "extra", ()) or ())

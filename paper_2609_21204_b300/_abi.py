@@ -65,6 +65,7 @@ SIGNATURES = {
     "snap_step": (C.c_int, [_P, C.c_int64]),
     "snap_prepare": (C.c_int, [_P]),
     "snap_set_retry_limit": (C.c_int, [_P, C.c_int32]),
+    "snap_set_list_block": (C.c_int, [_P, C.c_int32]),
     "snap_set_kinetic_temperature": (C.c_int, [_P, C.c_int32]),
     "snap_step_profiled": (C.c_int, [_P, C.c_int64, _P]),
     "snap_bond_update": (C.c_int, [_P]),

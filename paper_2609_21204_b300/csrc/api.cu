@@ -94,6 +94,7 @@ struct snap_ctx {
     int nbr_cap = 0;
     int rnbr_cap = 0;
     int cas_cap = 1 << 16;           // push-mode compare-and-swap retries (snap_set_retry_limit)
+    int list_block = 256;            // threads per block of the list build (snap_set_list_block)
     int kinetic_T = 0;               // sweep temperature: 0 set-point, 1 kinetic (snap_set_kinetic_temperature)
 };
 
@@ -461,7 +462,7 @@ void seq_rebuild(snap_ctx *c, cudaStream_t stream = nullptr)
     launch_scatter(c->P, c->A, L);
     launch_cell_sort(c->A, c->nkeys, L);
     launch_gather(c->P, c->A, c->B, c->fp64, L);
-    launch_nlist(c->P, c->A, c->B, c->fp64, L);   // copies the gathered arrays back too
+    launch_nlist(c->P, c->A, c->B, c->fp64, c->list_block, L);   // copies the gathered arrays back too
     launch_rebuild_done(c->A, L);
 }
 
@@ -1429,6 +1430,16 @@ extern "C" snap_status snap_set_retry_limit(snap_ctx *c, int32_t limit)
     return SNAP_OK;
 }
 
+extern "C" snap_status snap_set_list_block(snap_ctx *c, int32_t threads)
+{
+    if (!c) return SNAP_ERR_ARG;
+    if (threads != 64 && threads != 128 && threads != 256)
+        return fail(c, SNAP_ERR_ARG, "list-build block size must be 64, 128 or 256");
+    c->list_block = threads;
+    c->graph_dirty = true;    // the launch shape is captured in the step graphs
+    return SNAP_OK;
+}
+
 extern "C" snap_status snap_prepare(snap_ctx *c)
 {
     snap_status s = check_ready(c);
@@ -1526,7 +1537,7 @@ extern "C" snap_status snap_rebuild_profiled(snap_ctx *c, double *ms)
     launch_gather(c->P, c->A, c->B, c->fp64, L);
     cudaEventRecord(ev[5], c->stream);
     cudaEventRecord(ev[6], c->stream);             // the copy back runs inside the list build
-    launch_nlist(c->P, c->A, c->B, c->fp64, L);
+    launch_nlist(c->P, c->A, c->B, c->fp64, c->list_block, L);
     cudaEventRecord(ev[7], c->stream);
     launch_rebuild_done(c->A, L);
     cudaEventRecord(ev[8], c->stream);

@@ -860,13 +860,13 @@ void launch_gather(const DevParams &P, const DevArrays &A, const DevArrays &B, b
 
 // the lists (both precisions list from the FP32 wrapped positions) and the
 // copy back of the gathered arrays
-void launch_nlist(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, Launch L)
+void launch_nlist(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, int block, Launch L)
 {
     if (P.n == 0) return;
     if (fp64)
-        k_nlist<double><<<grid_for(P.n, 256), 256, 0, L.stream>>>(P, A, B);
+        k_nlist<double><<<grid_for(P.n, block), block, 0, L.stream>>>(P, A, B);
     else
-        k_nlist<float><<<grid_for(P.n, 256), 256, 0, L.stream>>>(P, A, B);
+        k_nlist<float><<<grid_for(P.n, block), block, 0, L.stream>>>(P, A, B);
 }
 
 void launch_rebuild_done(const DevArrays &A, Launch L) { k_rebuild_done<<<1, 1, 0, L.stream>>>(A); }

@@ -20,7 +20,7 @@ void launch_cell_scan(const DevArrays &A, int32_t *block_sums, int ncell, Launch
 void launch_scatter(const DevParams &P, const DevArrays &A, Launch L);
 void launch_cell_sort(const DevArrays &A, int ncell, Launch L);
 void launch_gather(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, Launch L);
-void launch_nlist(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, Launch L);
+void launch_nlist(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, int block, Launch L);
 void launch_rebuild_done(const DevArrays &A, Launch L);
 // sets a graph conditional to (*need_rebuild && status == 0)
 void launch_set_rebuild_cond(const DevArrays &A, cudaGraphConditionalHandle h, bool end_prev, Launch L);

@@ -29,7 +29,25 @@ def test_autotune_with_fake_timer_caches(tmp_path):
     path = tmp_path / "tune.json"
     r = at.autotune(s, timer=timer, cache_path=path)
     assert r["block_size"] == 64 and r["skin"] == 0.3 and not r["cached"]
-    assert len(calls) == len(at.BLOCKS) * len(at.SKINS)
+    n_trials = len(at.BLOCKS) * len(at.SKINS) + len(at.LIST_BLOCKS) - 1
+    assert len(calls) == n_trials
     r2 = at.autotune(s, timer=timer, cache_path=path)
     assert r2["cached"] and r2["block_size"] == 64
-    assert len(calls) == len(at.BLOCKS) * len(at.SKINS)
+    assert len(calls) == n_trials
+
+
+def test_autotune_searches_list_block_at_the_best_shape(tmp_path):
+    """The list build's block size is searched after (block, skin), at the
+    best of those; a faster list block wins, a slower one does not."""
+    s = assoc_ab(seed=2, n_a=50, n_b=50)
+    calls = []
+
+    def timer(cfg):
+        calls.append(cfg)
+        return 1.0 + abs(cfg["skin"] - 0.4) + cfg["block_size"] / 1000.0 + {128: 0.01, 256: 0.0, 64: 0.02}[cfg["list_block"]]
+
+    r = at.autotune(s, timer=timer, cache_path=tmp_path / "t.json")
+    assert (r["block_size"], r["skin"], r["list_block"]) == (64, 0.4, 256)
+    stage2 = calls[len(at.BLOCKS) * len(at.SKINS):]
+    assert [c["list_block"] for c in stage2] == list(at.LIST_BLOCKS[1:])
+    assert all((c["block_size"], c["skin"]) == (64, 0.4) for c in stage2)

@@ -233,6 +233,23 @@ def test_results_independent_of_block_size(snapmod, block):
     assert np.array_equal(ref.positions(), alt.positions())
 
 
+@pytest.mark.parametrize("list_block", [64, 128])
+def test_results_independent_of_list_block(snapmod, list_block):
+    """The list build's threads per block (an autotuned launch shape) leaves
+    the lists, and so every trajectory, unchanged."""
+    s = colloid_linker(seed=16, n_c=1000, n_l=4000, eps=3.0)
+    ref = snapmod.from_system(s, precision="mixed")
+    ref.step(120)
+    alt = snapmod.from_system(s, precision="mixed", list_block=list_block)
+    alt.step(120)
+    assert ref.stats()["nlist_builds"] == alt.stats()["nlist_builds"] > 1
+    assert np.array_equal(ref.bonds(), alt.bonds())
+    assert np.array_equal(ref.positions(), alt.positions())
+    with pytest.raises(snapmod.SnapError) as e:
+        alt.set_list_block(96)
+    assert e.value.name == "SNAP_ERR_ARG"
+
+
 def test_block_size_above_launch_bound_is_rejected(snapmod):
     s = colloid_linker(seed=15, n_c=100, n_l=400)
     for bad in (512, 1024, 100):
