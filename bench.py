@@ -705,7 +705,7 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
                   "proposals": st2["proposals"], "formed": st2["formed"], "broken": st2["broken"],
                   "n_bonds": st2["n_bonds"], "mean_neighbours": nbar,
                   "nlist_builds_in_timed_region": st1["nlist_builds"] - st0["nlist_builds"]},
-        "roofline": {"kernel": "k_step_md<float> (pair + bond forces, Langevin update)", "bound": "hbm",
+        "roofline": {"kernel": "k_step_md (mixed precision: pair + bond forces, Langevin update)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_kind, "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg_bytes,

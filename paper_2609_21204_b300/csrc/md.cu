@@ -749,11 +749,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_force(DevParams
 // are read from pos4 while the new relative coordinate goes to pos4n, the
 // other of two buffers, which the host swaps after the step.
 template <typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_step_md(DevParams P, DevArrays A)
+__device__ __forceinline__ void step_md_particle(const DevParams &P, DevArrays &A, const float4 *s_shift)
 {
     using V = typename Vec4<R>::T;
-    __shared__ float4 s_shift[27];
-    fill_shift_table(s_shift);
     const long long i = gtid();
     if (i >= P.n) return;
     if (!status_ok(A.status)) return;
@@ -774,6 +772,24 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_step_md(DevPara
     } else {
         integrate_mixed(P, A, i, step, Rp, fx, fy, fz, pi, reinterpret_cast<float4 *>(A.pos4n));
     }
+}
+
+// Mixed precision, capped at 56 registers: one more resident block of 128
+// threads per SM than at 64 (9 instead of 8), for a few spilled words (the
+// kernel is latency-bound: 78.2 -> 75.4 us on the 10^6 gel; a cap of 48
+// spills in the pair loop and is slower).
+__global__ void __maxnreg__(56) k_step_md(DevParams P, DevArrays A)
+{
+    __shared__ float4 s_shift[27];
+    fill_shift_table(s_shift);
+    step_md_particle<float>(P, A, s_shift);
+}
+
+__global__ void __launch_bounds__(256, 2) k_step_md_fp64(DevParams P, DevArrays A)
+{
+    __shared__ float4 s_shift[27];
+    fill_shift_table(s_shift);
+    step_md_particle<double>(P, A, s_shift);
 }
 
 // deterministic column sums: one block, fixed stride order, fixed tree
@@ -880,8 +896,8 @@ void launch_step_md(const DevParams &P, const DevArrays &A, bool fp64, Launch L)
 {
     if (P.n == 0) return;
     const unsigned g = grid_for(P.n, L.block);
-    if (fp64) k_step_md<double><<<g, L.block, 0, L.stream>>>(P, A);
-    else k_step_md<float><<<g, L.block, 0, L.stream>>>(P, A);
+    if (fp64) k_step_md_fp64<<<g, L.block, 0, L.stream>>>(P, A);
+    else k_step_md<<<g, L.block, 0, L.stream>>>(P, A);
 }
 
 void launch_force(const DevParams &P, const DevArrays &A, bool fp64, bool energy, Launch L)
