@@ -120,17 +120,83 @@ def build_system(args, seed, rho=None):
 
 
 # ----------------------------------------------------------------- clocks
+class _Nvml:
+    """The few read-only NVML queries the clock sampler needs, through the
+    driver's libnvidia-ml with ctypes (no Python package required)."""
+    CLOCK_SM = 1
+    # clock-event reason bits (NVML's public constants)
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, dev):
+        import ctypes
+        self.C = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit")
+        self.h = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(int(dev)).uuid)
+            uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            ok = self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) == 0
+        except Exception:
+            ok = False
+        if not ok and self.lib.nvmlDeviceGetHandleByIndex_v2(int(dev), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("nvmlDeviceGetHandle")
+        self.get_reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        C = self.C
+        sm, smax, r = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        if (self.lib.nvmlDeviceGetClockInfo(self.h, self.CLOCK_SM, C.byref(sm)) != 0 or
+                self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.CLOCK_SM, C.byref(smax)) != 0 or
+                self.get_reasons(self.h, C.byref(r)) != 0):
+            raise RuntimeError("nvml query")
+        return float(sm.value), float(smax.value), {k for k, b in self.REASONS.items() if r.value & b}
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
 class Clocks:
+    """SM clocks and clock-event reasons sampled during the timed region: NVML
+    every 2 ms from a host thread (the GPU runs the queued steps while the host
+    waits), with one sample when sampling starts and one when it stops, so
+    that even a timed region of a few milliseconds has samples; nvidia-smi
+    -lms 200 when NVML cannot be loaded.  Read-only queries."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
         self.path = None
+        self.nvml = None
+        self.thread = None
+        self.samples = []
 
     def start(self):
+        try:
+            import threading
+            self.nvml = _Nvml(self.dev)
+            self.samples = [self.nvml.sample()]
+            self.stop_flag = threading.Event()
+
+            def loop():
+                while not self.stop_flag.wait(0.002):
+                    try:
+                        self.samples.append(self.nvml.sample())
+                    except Exception:
+                        return
+            self.thread = threading.Thread(target=loop, daemon=True)
+            self.thread.start()
+            return
+        except Exception:
+            self.nvml = None
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -142,33 +208,50 @@ class Clocks:
             self.proc = None
 
     def stop(self):
-        if self.proc is None:
-            return None
-        self.proc.send_signal(signal.SIGTERM)
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.f.close()
         sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in Path(self.path).read_text().splitlines():
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
+        if self.nvml is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=5)
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        os.unlink(self.path)
+                self.samples.append(self.nvml.sample())
+            except Exception:
+                pass
+            for a, b, r in self.samples:
+                sm.append(a)
+                smax.append(b)
+                reasons |= r
+            try:
+                self.nvml.close()
+            except Exception:
+                pass
+            source = "nvml"
+        elif self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+            for line in Path(self.path).read_text().splitlines():
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(self.NAMES, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+            source = "nvidia-smi"
+        else:
+            return None
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": source}
 
 
 def measured_peaks():
