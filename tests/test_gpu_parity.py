@@ -146,6 +146,40 @@ def test_neighbor_list_contains_all_pairs(snapmod, precision):
     assert got <= allowed
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("box", [5.2, 7.0])
+def test_neighbor_list_small_boxes(snapmod, precision, box):
+    """Boxes of three and four cells per axis: every run of row-adjacent
+    cells touches the periodic boundary (the runs across it are split), and
+    the lists still hold every pair within reach and nothing beyond."""
+    s = random_frozen(seed=61, n=int(0.4 * box ** 3), box=box, overlap_factor=1.0, r_max=1.3)
+    sim, orc = make_pair(snapmod, s, precision)
+    need = {tuple(p) for p in orc.pairs_within(extra=0.0, reactive=True)}
+    got = {tuple(p) for p in sim.neighbors()}
+    assert len(need) > 50
+    assert need <= got, len(need - got)
+    allowed = {tuple(p) for p in orc.pairs_within(extra=2 * s.skin + 1e-3, reactive=True)}
+    assert got <= allowed
+
+
+def test_fp64_trajectory_in_a_three_cell_box(snapmod):
+    """The smallest periodic box the cell list takes (three cells per axis):
+    FP64 MD with the sweep follows the oracle step for step, so the list
+    build's boundary runs and the force list's stored cell shifts are right
+    when every neighbour cell is a periodic image."""
+    s = colloid_linker(seed=62, n_c=40, n_l=160, eps=3.0)
+    assert s.box[0] < 4 * (1.2 + s.skin + 1e-3)
+    sim, orc = make_pair(snapmod, s, "fp64")
+    for _ in range(6):
+        sim.step(20)
+        orc.run(20)
+        d = sim.positions() - orc.pos
+        d -= s.box * np.rint(d / s.box)
+        assert np.abs(d).max() < 1e-9
+        assert np.array_equal(sim.bonds(), orc.bonds())
+    assert sim.stats()["nlist_builds"] > 2
+
+
 def _force_err(f, g, scale):
     """Normwise relative error, and the per-particle error against the
     sensitivity scale G_i = sum_j (|F_ij| + r_ij |dF_ij/dr|) the oracle reports:
