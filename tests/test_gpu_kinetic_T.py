@@ -117,6 +117,43 @@ def test_kinetic_T_fp64_trajectory_follows_oracle(snapmod):
     assert sim.stats()["n_bonds"] > 50
 
 
+def test_kinetic_T_batched_replicas_follow_their_oracles(snapmod):
+    """Four replicas in one context, each with its own kinetic temperature
+    (velocities drawn at different scales, uneven sizes): the fixed-point sum
+    is per replica, so one sweep and 25 FP64 MD steps match each replica's
+    own oracle bit for bit in the bonds and to 1e-9 in the positions."""
+    reps = [random_frozen(seed=70 + r, n=500 + 123 * r, box=12.0 + r, overlap_factor=1.0,
+                          r_max=1.4, eps=1.5 + r) for r in range(4)]
+    rng = np.random.default_rng(71)
+    for r, s in enumerate(reps):
+        s.seed = 2000 + 31 * r
+        s.kinetic_T = 1
+        s.vel = rng.normal(size=(s.n, 3)) * np.sqrt(0.4 + 0.3 * r)
+    sim = snapmod.from_system(reps, precision="fp64", p_on0=0.8)
+    orcs = [oracle.OracleSystem(s, p_on0=0.8) for s in reps]
+    temps = [o.kinetic_T() for o in orcs]
+    assert max(temps) - min(temps) > 0.5
+    sim.bond_update()
+    for o in orcs:
+        o.sweep(step=0)
+    sim.step(25)
+    for o in orcs:
+        o.run(25)
+    bonds = sim.bonds()
+    pos = sim.positions()
+    off = 0
+    for s, o in zip(reps, orcs):
+        sel = (bonds[:, 0] >= off) & (bonds[:, 0] < off + s.n)
+        mine = bonds[sel].copy()
+        mine[:, :2] -= off
+        assert np.array_equal(mine, o.bonds())
+        d = pos[off:off + s.n] - o.pos
+        d -= s.box * np.rint(d / s.box)
+        assert np.abs(d).max() < 1e-9
+        off += s.n
+    assert bonds.shape[0] > 100
+
+
 def test_kinetic_T_refused_with_mh(snapmod):
     s = assoc_ab(seed=34)
     sim = snapmod.from_system(s, precision="mixed")
