@@ -58,6 +58,8 @@ def parse():
                     help="threads per block of the particle kernels (0 with --skin 0: autotuned)")
     ap.add_argument("--skin", type=float, default=0.0,
                     help="neighbour-list skin (0 with --block 0: autotuned)")
+    ap.add_argument("--subcells", type=int, default=-1,
+                    help="list build's sub-cells along x per cell (0 automatic, 1/2/4/8; with --block/--skin)")
     ap.add_argument("--batch-replicas", type=int, default=256,
                     help="replicas of the batched telechelic sweep leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=500)
@@ -371,7 +373,8 @@ def _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream):
     from paper_2609_21204_b300 import autotune
     tune = autotune.autotune(batch, precision="mixed", steps=40, warmup=20)
     sim = snap.from_system(batch, precision="mixed", block_size=tune["block_size"],
-                           skin=tune["skin"], list_block=tune.get("list_block"))
+                           skin=tune["skin"], list_block=tune.get("list_block"),
+                           list_subcells=tune.get("list_subcells"))
     nb = sum(s.n for s in batch)
     sim.step(args.warmup)
     sim.prepare()
@@ -385,13 +388,15 @@ def _run_batched(args, torch, snap, batch, barrier, max_all, sum_all, stream):
     torch.cuda.synchronize()
     t = max_all(e0.elapsed_time(e1) / 1e3)
     st = sim.stats()
+    sim_subcells = sim.list_subcells()
     sim.close()
     return {"workload": f"{len(batch)} telechelic replicas (N log-uniform in [2k, 50k], "
                         f"eps U[2,10] kT, kT U[0.8,1.2]), {nb} particles in one context",
             "value": sum_all(float(nb)) * args.batch_steps / t, "unit": UNIT,
             "ms_per_step": t * 1e3 / args.batch_steps, "steps": args.batch_steps,
             "particles": nb, "replicas": len(batch), "n_bonds": st["n_bonds"],
-            "autotune": {k: tune.get(k) for k in ("block_size", "skin", "list_block", "cached", "key")},
+            "autotune": dict({k: tune.get(k) for k in ("block_size", "skin", "list_block", "list_subcells",
+                                                        "cached", "key")}, subcells_in_use=sim_subcells),
             "vs_oracle": _smallest_replicas_vs_oracle(snap, batch)}
 
 
@@ -692,9 +697,9 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
         eq_check["sweep_stats"] = e1.stats()
         e1.close()
     eq.close()
-    if args.block or args.skin:
+    if args.block or args.skin or args.subcells >= 0:
         tune = {"block_size": args.block or 128, "skin": args.skin or s.skin, "cached": None,
-                "key": "set by flags"}
+                "key": "set by flags", "list_subcells": max(args.subcells, 0)}
     else:
         from paper_2609_21204_b300 import autotune
         tune = autotune.autotune(s, precision="mixed", blocks=(128, 256), skins=(0.3, 0.4, 0.5, 0.6, 0.7),
@@ -702,9 +707,10 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
 
     def make(precision):
         return snap.from_system(s, precision=precision, block_size=tune["block_size"], skin=tune["skin"],
-                                list_block=tune.get("list_block"))
+                                list_block=tune.get("list_block"), list_subcells=tune.get("list_subcells"))
 
     sim = make("mixed")
+    subcells = sim.list_subcells()
     # the equilibrated state, the warm-up, then the step graphs of both buffer
     # parities are captured and uploaded so that no capture falls inside the
     # timed region
@@ -770,8 +776,9 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
         "ms_per_step": t_max * 1e3 / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": dict(workload_config(args, n), block_size=tune["block_size"], skin=tune["skin"],
-                       list_block=tune.get("list_block") or 256),
-        "autotune": {k: tune.get(k) for k in ("block_size", "skin", "list_block", "cached", "key", "ms_per_step")},
+                       list_block=tune.get("list_block") or 256, list_subcells=subcells),
+        "autotune": {k: tune.get(k) for k in ("block_size", "skin", "list_block", "list_subcells", "cached", "key",
+                                              "ms_per_step")},
         "gpu_launches": launches,
         "clocks": clk,
         "phases_ms_per_step": {k: round(v, 5) for k, v in ph.items()},

@@ -272,6 +272,24 @@ snap_status snap_set_retry_limit(snap_ctx *, int32_t limit);
  * every result, do not depend on it. */
 snap_status snap_set_list_block(snap_ctx *, int32_t threads);
 
+/* Sub-cells along x per neighbour cell for the list build: each cell is cut
+ * into k slices of equal width along x, the particles are sorted by slice
+ * within their cell, and the list build scans only the slices that overlap a
+ * particle's x window in each row of cells, so fewer candidates are tested
+ * where the cut-offs are short against the cell width.  k is 1, 2, 4 or 8, or
+ * 0 (the default) for automatic: the most slices (at most 8) that keep at
+ * least half a particle per (type, slice) on average.  Fewer are used where
+ * the sort keys (cells x types x k) would exceed 2^24.  Only before
+ * snap_set_particles lays the cell grid out (SNAP_ERR_STATE after); any other
+ * k returns SNAP_ERR_ARG.  The lists hold the same pairs for every k; the
+ * order of particles inside a cell, and so the order of list entries and of
+ * the force sums, follows the slices. */
+snap_status snap_set_list_subcells(snap_ctx *, int32_t k);
+
+/* The number of sub-cells along x per cell in use (after snap_set_particles;
+ * SNAP_ERR_STATE before). */
+snap_status snap_get_list_subcells(snap_ctx *, int32_t *k);
+
 /* Capture, instantiate and upload the step graphs for both buffer parities
  * now, so that no later snap_step pays for a capture (a step swaps two
  * coordinate buffers; a call with an odd step count leaves the next call on

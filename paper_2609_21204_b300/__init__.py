@@ -238,6 +238,18 @@ class Snap:
         launch shape; results do not depend on it)."""
         self._check(self._lib.snap_set_list_block(self._ctx, int(threads)))
 
+    def set_list_subcells(self, k):
+        """Sub-cells along x per neighbour cell for the list build: 1, 2, 4 or
+        8, or 0 for automatic; only before the particles are set (the lists
+        hold the same pairs for every k)."""
+        self._check(self._lib.snap_set_list_subcells(self._ctx, int(k)))
+
+    def list_subcells(self):
+        """Sub-cells along x per cell in use."""
+        k = C.c_int32()
+        self._check(self._lib.snap_get_list_subcells(self._ctx, C.byref(k)))
+        return int(k.value)
+
     def prepare(self):
         """Capture and upload the step graphs of both buffer parities now (no
         step runs), so that no later step() pays for a capture."""
@@ -479,11 +491,13 @@ def pair_energy_noalloc(n, d_pos3, d_type, box, sigma, eps_pair, rcut=None, d_ou
         raise SnapError(code, "snap_pair_energy_noalloc")
 
 
-def from_system(sysdef, precision="mixed", p_on0=1.0, skin=None, list_block=None, **kw) -> Snap:
+def from_system(sysdef, precision="mixed", p_on0=1.0, skin=None, list_block=None, list_subcells=None,
+                **kw) -> Snap:
     """Build a context from a `synth.System` (or any object with the same fields).
     A list of systems becomes one batched context of independent replicas.
     `skin` overrides the systems' neighbour-list skin; `list_block` sets the
-    list build's threads per block."""
+    list build's threads per block and `list_subcells` its sub-cells along x
+    per cell."""
     systems = sysdef if isinstance(sysdef, (list, tuple)) else [sysdef]
     s0 = systems[0]
     n = sum(s.n for s in systems)
@@ -496,6 +510,8 @@ def from_system(sysdef, precision="mixed", p_on0=1.0, skin=None, list_block=None
     sim.set_types(s0.sigma, s0.eps_pair, s0.rcut)
     if list_block:
         sim.set_list_block(list_block)
+    if list_subcells:
+        sim.set_list_subcells(list_subcells)
     sim.set_valence(s0.valence)
     for i, bt in enumerate(s0.bond_types):
         sim.set_bond_params(i, bt.kind, bt.k, bt.r0, getattr(bt, "extra", ()) or ())

@@ -66,6 +66,8 @@ SIGNATURES = {
     "snap_prepare": (C.c_int, [_P]),
     "snap_set_retry_limit": (C.c_int, [_P, C.c_int32]),
     "snap_set_list_block": (C.c_int, [_P, C.c_int32]),
+    "snap_set_list_subcells": (C.c_int, [_P, C.c_int32]),
+    "snap_get_list_subcells": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "snap_set_kinetic_temperature": (C.c_int, [_P, C.c_int32]),
     "snap_step_profiled": (C.c_int, [_P, C.c_int64, _P]),
     "snap_bond_update": (C.c_int, [_P]),

@@ -1,7 +1,8 @@
 """Autotuner for the launch shapes and neighbour-list skin of a context.
 
 Candidates (threads per block for the particle kernels x neighbour-list skin,
-then the list build's threads per block at the best of those) are timed on
+then the list build's threads per block and its sub-cells along x per cell
+at the best of those) are timed on
 the caller's own system with CUDA events over a short run after a
 warm-up; the fastest is returned and cached in a JSON file keyed by the GPU
 name, the precision mode, the particle count (rounded to a power of two), the
@@ -22,6 +23,7 @@ DEFAULT_CACHE = Path(os.environ.get("SNAP_AUTOTUNE_CACHE",
 BLOCKS = (64, 128, 256)
 SKINS = (0.25, 0.3, 0.4)
 LIST_BLOCKS = (128, 256, 64)   # the list build's block size, searched at the best (block, skin)
+LIST_SUBCELLS = (0, 8, 2)      # its sub-cells along x per cell (0: the library's choice), searched after it
 
 
 def cache_key(gpu_name: str, precision: str, n: int, density: float, n_replicas: int) -> str:
@@ -60,8 +62,9 @@ def choose(trials):
 
 
 def autotune(systems, precision="mixed", blocks=BLOCKS, skins=SKINS, steps=60, warmup=30,
-             cache_path: Path = DEFAULT_CACHE, use_cache=True, timer=None, state=None, list_blocks=LIST_BLOCKS):
-    """Pick (block_size, skin, list_block) for these systems.  `systems` is one synth
+             cache_path: Path = DEFAULT_CACHE, use_cache=True, timer=None, state=None, list_blocks=LIST_BLOCKS,
+             list_subcells=LIST_SUBCELLS):
+    """Pick (block_size, skin, list_block, list_subcells) for these systems.  `systems` is one synth
     System or a list of them (a batched context).  `state` (bytes from
     Snap.get_state of a context over the same systems) starts every trial from
     that state instead of the systems' own coordinates, so that the choice is
@@ -88,15 +91,21 @@ def autotune(systems, precision="mixed", blocks=BLOCKS, skins=SKINS, steps=60, w
             return None
 
     lb0 = int(list_blocks[0]) if list_blocks else 256
+    ls0 = int(list_subcells[0]) if list_subcells else 0
     trials = []
     for skin in skins:
         for block in blocks:
-            cfg = dict(block_size=int(block), skin=float(skin), list_block=lb0)
+            cfg = dict(block_size=int(block), skin=float(skin), list_block=lb0, list_subcells=ls0)
             trials.append((cfg, timed(cfg)))
     best = choose(trials)
-    # the list build's block size at the best (block, skin)
+    # the list build's block size, then its sub-cells, at the best (block, skin)
     for lb in list(list_blocks)[1:]:
-        cfg = dict(block_size=best["block_size"], skin=best["skin"], list_block=int(lb))
+        cfg = dict(block_size=best["block_size"], skin=best["skin"], list_block=int(lb), list_subcells=ls0)
+        trials.append((cfg, timed(cfg)))
+    best = choose(trials)
+    for ls in list(list_subcells)[1:]:
+        cfg = dict(block_size=best["block_size"], skin=best["skin"], list_block=best["list_block"],
+                   list_subcells=int(ls))
         trials.append((cfg, timed(cfg)))
     best = choose(trials)
     best["trials"] = [dict(c, ms_per_step=m) for c, m in trials]
@@ -112,7 +121,8 @@ def _gpu_timer(systems, precision, steps, warmup, state=None):
 
     def run(cfg):
         sim = from_system(systems if len(systems) > 1 else systems[0], precision=precision,
-                          block_size=cfg["block_size"], skin=cfg["skin"], list_block=cfg.get("list_block"))
+                          block_size=cfg["block_size"], skin=cfg["skin"], list_block=cfg.get("list_block"),
+                          list_subcells=cfg.get("list_subcells"))
         try:
             if state is not None:
                 sim.set_state(state)

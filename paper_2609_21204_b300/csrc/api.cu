@@ -95,6 +95,9 @@ struct snap_ctx {
     int rnbr_cap = 0;
     int cas_cap = 1 << 16;           // push-mode compare-and-swap retries (snap_set_retry_limit)
     int list_block = 256;            // threads per block of the list build (snap_set_list_block)
+    int list_sub = 0;                // sub-cells along x per cell requested (snap_set_list_subcells; 0: automatic)
+    int list_staged = 0;             // list build variant, from SNAP_LIST_BUILD when the context is made
+    int sub_shift = 0;               // log2 of the sub-cells in use (set when the cell grid is laid out)
     int kinetic_T = 0;               // sweep temperature: 0 set-point, 1 kinetic (snap_set_kinetic_temperature)
 };
 
@@ -151,6 +154,16 @@ uint32_t morton2(uint32_t y, uint32_t z)
     uint32_t m = 0;
     for (int b = 0; b < 10; ++b) m |= ((y >> b) & 1u) << (2 * b) | ((z >> b) & 1u) << (2 * b + 1);
     return m;
+}
+
+// Which list build runs: SNAP_LIST_BUILD=staged (warps stage candidates in
+// shared memory) or lane (each lane reads its candidates itself); both build
+// the same lists, entry for entry.
+bool list_build_staged()
+{
+    const char *m = std::getenv("SNAP_LIST_BUILD");
+    if (!m) return false;
+    return std::strcmp(m, "staged") == 0;
 }
 
 // Margin added to every list cut-off: 1e-4, or more where the FP32 wrapped
@@ -320,6 +333,8 @@ void fill_params(snap_ctx *c)
     P.nrep = (int)c->reps.size();
     P.screen = c->fp64 ? 0 : 1;
     P.ncell = c->ncell_total;
+    P.sub_shift = c->sub_shift;
+    P.list_staged = c->list_staged;
     P.mh_cells = c->mh_mode ? c->mh_nc[0] * c->mh_nc[1] * c->mh_nc[2] : 0;
     P.mh_moves = c->mh_mode ? P.mh_cells / 8 : 0;
     P.mh_eps = (float)c->mh_eps;
@@ -430,8 +445,21 @@ snap_status ensure_ready(snap_ctx *c)
                 rank_of[R.cell_off + rows[k].second * nx + x] = R.cell_off + (int)k * nx + x;
     }
     DevArrays &A = c->A;
-    const long long nkeys = (long long)off * c->ntypes;   // sort keys: type * ncell + cell
-    if (nkeys > (long long)4096 * 4096) return fail(c, SNAP_ERR_ARG, "too many cells x types");
+    // sort keys: (type, cell, sub-cell along x).  Sub-cells per cell: as
+    // requested, else the most (<= 8) that keep at least half a particle per key
+    // on average; fewer where the key count would pass the scan's limit.
+    constexpr long long kMaxKeys = (long long)4096 * 4096;
+    const long long ncoarse = (long long)off * c->ntypes;
+    if (ncoarse > kMaxKeys) return fail(c, SNAP_ERR_ARG, "too many cells x types");
+    int sh = 0;
+    if (c->list_sub > 0) {
+        while ((1 << sh) < c->list_sub) ++sh;
+    } else {
+        while (sh < 3 && (ncoarse << (sh + 1)) <= 2 * (long long)c->n) ++sh;
+    }
+    while (sh > 0 && (ncoarse << sh) > kMaxKeys) --sh;
+    c->sub_shift = sh;
+    const long long nkeys = ncoarse << sh;
     c->nkeys = (int)nkeys;
     const int nb = (int)((nkeys + 4095) / 4096) + 1;
     if (!alloc_arr(c, A.cell_count, nkeys) || !alloc_arr(c, A.cell_start, nkeys + 1) ||
@@ -459,8 +487,8 @@ void seq_rebuild(snap_ctx *c, cudaStream_t stream = nullptr)
     const Launch L = launch_on(c, stream ? stream : c->stream);
     launch_cell_key(c->P, c->A, L);
     launch_cell_scan(c->A, c->d_bsum, c->nkeys, L);
-    launch_scatter(c->P, c->A, L);
-    launch_cell_sort(c->A, c->nkeys, L);
+    launch_scatter(c->P, c->A, c->d_bsum, L);
+    launch_cell_sort(c->A, c->nkeys, c->d_bsum, L);
     launch_gather(c->P, c->A, c->B, c->fp64, L);
     launch_nlist(c->P, c->A, c->B, c->fp64, c->list_block, L);   // copies the gathered arrays back too
     launch_rebuild_done(c->A, L);
@@ -965,6 +993,7 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
 
     snap_ctx *c = new snap_ctx();
     c->cfg = *cfg;
+    c->list_staged = list_build_staged() ? 1 : 0;
     c->cfg.replica_n = nullptr;
     c->cfg.replica_box = nullptr;
     c->cfg.replica_kT = nullptr;
@@ -1440,6 +1469,24 @@ extern "C" snap_status snap_set_list_block(snap_ctx *c, int32_t threads)
     return SNAP_OK;
 }
 
+extern "C" snap_status snap_set_list_subcells(snap_ctx *c, int32_t k)
+{
+    if (!c) return SNAP_ERR_ARG;
+    if (k != 0 && k != 1 && k != 2 && k != 4 && k != 8)
+        return fail(c, SNAP_ERR_ARG, "sub-cells per cell must be 0 (automatic), 1, 2, 4 or 8");
+    if (c->ready) return fail(c, SNAP_ERR_STATE, "the cell grid is laid out: set the sub-cells before snap_set_particles");
+    c->list_sub = k;
+    return SNAP_OK;
+}
+
+extern "C" snap_status snap_get_list_subcells(snap_ctx *c, int32_t *k)
+{
+    if (!c || !k) return SNAP_ERR_ARG;
+    if (!c->ready) return fail(c, SNAP_ERR_STATE, "the cell grid is laid out by snap_set_particles");
+    *k = 1 << c->sub_shift;
+    return SNAP_OK;
+}
+
 extern "C" snap_status snap_prepare(snap_ctx *c)
 {
     snap_status s = check_ready(c);
@@ -1530,9 +1577,9 @@ extern "C" snap_status snap_rebuild_profiled(snap_ctx *c, double *ms)
     cudaEventRecord(ev[1], c->stream);
     launch_cell_scan(c->A, c->d_bsum, c->nkeys, L);
     cudaEventRecord(ev[2], c->stream);
-    launch_scatter(c->P, c->A, L);
+    launch_scatter(c->P, c->A, c->d_bsum, L);
     cudaEventRecord(ev[3], c->stream);
-    launch_cell_sort(c->A, c->nkeys, L);
+    launch_cell_sort(c->A, c->nkeys, c->d_bsum, L);
     cudaEventRecord(ev[4], c->stream);
     launch_gather(c->P, c->A, c->B, c->fp64, L);
     cudaEventRecord(ev[5], c->stream);

@@ -41,6 +41,16 @@ __device__ __forceinline__ void cell_of(const RepDev &R, double x, double y, dou
     cz = min(max(cz, 0), R.nc[2] - 1);
 }
 
+// Sub-cell along x: every cell is cut into 2^s slices of equal width along x
+// for the sort and the list build.  The scale is the cell scale times 2^s,
+// exact in FP32, so that sx >> s is the cell cx that cell_of gives for the
+// same coordinate (clamps included).
+__device__ __forceinline__ int subcell_x(const RepDev &R, double x, int s)
+{
+    const float v = (float)x * (R.cscale[0] * (float)(1 << s));
+    return (int)fminf(fmaxf(v, 0.f), (float)((R.nc[0] << s) - 1));   // truncation = floor for v >= 0
+}
+
 // wrap into [0, L) and count the crossing in the image counter
 __device__ __forceinline__ double wrap_img(double x, double L, int &img)
 {
@@ -79,8 +89,9 @@ __global__ void k_cell_key(DevParams P, DevArrays A)
     }
     int cx, cy, cz;
     cell_of(R, x, y, z, cx, cy, cz);
-    const int lin = (cz * R.nc[1] + cy) * R.nc[0] + cx;
-    const int c = A.type[i] * P.ncell + A.rank_of[R.cell_off + lin];
+    // rank of the row's first cell: the row's cells, and so its sub-cells, follow it in x order
+    const int row = A.rank_of[R.cell_off + (cz * R.nc[1] + cy) * R.nc[0]];
+    const int c = ((A.type[i] * P.ncell + row) << P.sub_shift) + subcell_x(R, x, P.sub_shift);
     A.cell_key[i] = c;
     // particles are still nearly sorted: lanes of a warp mostly share a key,
     // so one atomic per distinct key and warp
@@ -182,7 +193,10 @@ __global__ void k_scan_add(int32_t *out, const int32_t *bsum, int n, int nb, con
     if (k == 0) out[n] = bsum[nb];
 }
 
-__global__ void k_scatter(DevParams P, DevArrays A)
+// The cell scan leaves in cell_start each key's exclusive prefix within its
+// tile of kScanTile keys and in bsum the tiles' offsets; the scatter adds the
+// offset itself, and the cell sort (one thread per key) writes the final start.
+__global__ void k_scatter(DevParams P, DevArrays A, const int32_t *bsum)
 {
     const long long i = gtid();
     if (i >= P.n) return;
@@ -194,17 +208,19 @@ __global__ void k_scatter(DevParams P, DevArrays A)
     int base = 0;
     if (lane == leader) base = atomicAdd(&A.cell_cursor[c], __popc(peers));
     base = __shfl_sync(peers, base, leader);
-    const int pos = A.cell_start[c] + base + __popc(peers & ((1u << lane) - 1u));
+    const int pos = A.cell_start[c] + bsum[c / kScanTile] + base + __popc(peers & ((1u << lane) - 1u));
     A.order[pos] = (int32_t)i;
 }
 
-// deterministic order inside a cell: ascending tag (insertion sort, cells are small)
-__global__ void k_cell_sort(DevArrays A, int ncell)
+// deterministic order inside a cell: ascending tag (insertion sort, cells are
+// small); then the cell's final start (each thread reads and writes only its
+// own key's entries)
+__global__ void k_cell_sort(DevArrays A, int ncell, const int32_t *bsum)
 {
     const long long c = gtid();
     if (c >= ncell) return;
     if (!status_ok(A.status) || !*A.need_rebuild) return;
-    const int s = A.cell_start[c], e = A.cell_start[c + 1];
+    const int s = A.cell_start[c] + bsum[c / kScanTile], e = s + A.cell_count[c];
     for (int k = s + 1; k < e; ++k) {
         const int v = A.order[k];
         const int tv = A.tag[v];
@@ -215,6 +231,8 @@ __global__ void k_cell_sort(DevArrays A, int ncell)
         }
         A.order[m + 1] = v;
     }
+    A.cell_start[c] = s;
+    if (c == ncell - 1) A.cell_start[ncell] = e;
     A.cell_count[c] = 0;
     A.cell_cursor[c] = 0;
 }
@@ -295,12 +313,16 @@ __device__ __forceinline__ void copyback_particle(const DevParams &P, DevArrays 
 // with r^2 < (r_max + skin + margin)^2.  The force loop then never visits
 // pairs that are only within reach of a bond, and the sweep never visits
 // pairs that cannot bond.  Cells are ranked row by row (x innermost, rows in
-// 2-D Morton order of (y, z)), so for each of the 9 rows around a particle and
-// each type the admitted cells x-1..x+1 are one contiguous run of the sorted
+// 2-D Morton order of (y, z)), and every cell is cut into 2^sub_shift slices
+// along x (sub-cells, sorted in x order), so for each of the 9 rows around a
+// particle and each type the candidates are one contiguous run of the sorted
 // particles: 18 candidate runs per particle instead of 54 single cells.  A
-// cell is admitted when the particle's distance to the cell box is below the
-// larger of the two cut-offs of the type pair, so short-ranged pairs (small
-// spheres) skip most cells.  Separations come from the FP32 wrapped positions
+// row is admitted when the particle's distance to the row's (y, z) box is
+// below the larger of the two cut-offs of the type pair, and within the row
+// only the sub-cells that overlap the x window that distance leaves are
+// scanned, so short-ranged pairs (small spheres) and far rows test few
+// candidates (on the colloid-linker gel 4 slices per cell cut the candidates
+// per particle from ~89 to ~60, 8 slices to ~54).  Separations come from the FP32 wrapped positions
 // the rebuild stored (npos) plus a periodic shift per run; their error (a few
 // units in the last place of the box edge) is inside the list margin, and the
 // lists only need to hold every pair within reach.  (A warp-per-cell variant
@@ -350,8 +372,14 @@ __device__ __forceinline__ int2 scan_lists(const float4 *npos, int s0, int e, lo
     return scan_range<true, true>(npos, s0, e, i, ox, oy, oz, fcut2, xcut2, nbr, rnbr, stride, cap, rcap, c.x, c.y);
 }
 
+// Slack of the x window of a row (squared and linear, length units): the row
+// and sub-cell tests compare FP32 coordinates whose cell faces and roundings
+// are off by ~1e-5 at the box sizes the cell bits allow.
+constexpr float kWinSlack2 = 5e-4f;
+constexpr float kWinSlack = 5e-4f;
+
 template <typename R>
-__global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A, DevArrays B)
+__global__ void __launch_bounds__(256, 8) k_nlist(DevParams P, DevArrays A, DevArrays B)
 {
     if (!status_ok(A.status) || !*A.need_rebuild) return;   // uniform
     const long long i = gtid();
@@ -363,16 +391,17 @@ __global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A, DevArra
         const int ti = bits_type(b), cx = bits_cx(b), cy = bits_cy(b), cz = bits_cz(b);
         const RepDev &Rp = A.reps[rep_of(P, B, i)];   // B: the new order (A is copied back below)
         const int nx = Rp.nc[0], ny = Rp.nc[1], nz = Rp.nc[2];
-        const float wx = Rp.wf[0], wy = Rp.wf[1], wz = Rp.wf[2];
+        const float wy = Rp.wf[1], wz = Rp.wf[2];
         const float Lx = (float)Rp.L[0], Ly = (float)Rp.L[1], Lz = (float)Rp.L[2];
         const long long stride = P.nbr_stride;
         // distances to the faces of the home cell (the cell bits were taken from
         // the same wrapped position: the cell test admits at least what it must)
-        const float rx = p.x - (float)cx * wx, ry = p.y - (float)cy * wy, rz = p.z - (float)cz * wz;
-        const float gxl = fmaxf(rx, 0.f), gxu = fmaxf(wx - rx, 0.f);
+        const float ry = p.y - (float)cy * wy, rz = p.z - (float)cz * wz;
         const float gyl = fmaxf(ry, 0.f), gyu = fmaxf(wy - ry, 0.f);
         const float gzl = fmaxf(rz, 0.f), gzu = fmaxf(wz - rz, 0.f);
-        const float gxl2 = gxl * gxl, gxu2 = gxu * gxu;
+        const int sh = P.sub_shift, nsx = nx << sh;
+        const float csk = Rp.cscale[0] * (float)(1 << sh);   // sub-cells per unit length along x
+        const float xlo = (float)((cx - 1) << sh), xhi = (float)(((cx + 2) << sh) - 1);
         for (int dz = -1; dz <= 1; ++dz) {
             int zz = cz + dz;
             float oz = -p.z;
@@ -393,21 +422,31 @@ __global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A, DevArra
                     const float xcut2 = P.xl2f[ti * kMaxTypes + t];
                     const float cut = fmaxf(fcut2, xcut2);
                     if (d2r >= cut) continue;
-                    int xa = cx - (d2r + gxl2 < cut ? 1 : 0);
-                    int xb = cx + (d2r + gxu2 < cut ? 1 : 0);
-                    const int kb = t * P.ncell + row;
-                    // a cell across the periodic x boundary is its own run
+                    // x window of the row: |dx|^2 < cut^2 - d2r, widened by slack that
+                    // covers the FP32 cell faces and coordinates (~1e-5 here)
+                    // (never beyond the cells x-1..x+1, which hold every pair within reach:
+                    // this also bounds the indices of a particle whose coordinate has left
+                    // the box by more than its edge, e.g. in an exploding system)
+                    const float wr = sqrtf(cut - d2r + kWinSlack2) + kWinSlack;
+                    int xa = (int)fminf(fmaxf(floorf((p.x - wr) * csk), xlo), xhi);
+                    int xb = (int)fminf(fmaxf(floorf((p.x + wr) * csk), xlo), xhi);
+                    const int kb = (t * P.ncell + row) << sh;
+                    // the part of the window across the periodic x boundary is its own
+                    // run, kept clear of the main run
                     if (xa < 0) {
-                        const int k = kb + nx - 1;
-                        cc = scan_lists(A.npos, A.cell_start[k], A.cell_start[k + 1], i, -p.x - Lx, oy, oz, fcut2,
-                                        xcut2, A.nbr, A.rnbr, stride, cap, rcap, cc);
+                        const int a = min(max(xa + nsx, xb + 1), nsx);
+                        cc = scan_lists(A.npos, A.cell_start[kb + a], A.cell_start[kb + nsx], i, -p.x - Lx, oy, oz,
+                                        fcut2, xcut2, A.nbr, A.rnbr, stride, cap, rcap, cc);
                         xa = 0;
                     }
-                    if (xb >= nx) {
-                        cc = scan_lists(A.npos, A.cell_start[kb], A.cell_start[kb + 1], i, Lx - p.x, oy, oz, fcut2,
-                                        xcut2, A.nbr, A.rnbr, stride, cap, rcap, cc);
-                        xb = nx - 1;
+                    if (xb >= nsx) {
+                        const int b = min(xb - nsx, xa - 1);
+                        cc = scan_lists(A.npos, A.cell_start[kb], A.cell_start[kb + b + 1], i, Lx - p.x, oy, oz,
+                                        fcut2, xcut2, A.nbr, A.rnbr, stride, cap, rcap, cc);
+                        xb = nsx - 1;
                     }
+                    xa = min(xa, nsx);     // a coordinate outside the box: an empty main run
+                    xb = max(xb, -1);
                     cc = scan_lists(A.npos, A.cell_start[kb + xa], A.cell_start[kb + xb + 1], i, -p.x, oy, oz, fcut2,
                                     xcut2, A.nbr, A.rnbr, stride, cap, rcap, cc);
                 }
@@ -425,6 +464,175 @@ __global__ void __launch_bounds__(256) k_nlist(DevParams P, DevArrays A, DevArra
     const unsigned long long v[2] = {(unsigned long long)min(cc.x, cap), (unsigned long long)min(cc.y, rcap)};
     warp_counts<2>(A.counters, idx, v);
     if (i < P.n) copyback_particle<R>(P, A, B, i);
+}
+
+// The same lists built by warps that stage candidates in shared memory.  The
+// lanes of a warp whose home cells lie in one row of cells (same type and
+// replica: nearly every warp, particles being sorted by row) share the 9 rows
+// around it; for each row and type the warp loads the union of its lanes'
+// x windows once, coalesced, into shared memory, and every lane then tests its
+// own window from there, in the same order as the per-lane build, so the
+// lists are identical entry for entry.  A union longer than the staging
+// buffer is tested from global memory lane by lane.  Lanes of different rows
+// (at row, type or replica boundaries) take turns, group by group.
+constexpr int kStageCap = 256;   // staged candidates per warp
+
+template <bool F, bool X>
+__device__ __forceinline__ int2 scan_range_smem(const float4 *sm, int base, int s0, int e, long long i, float ox,
+                                                float oy, float oz, float fcut2, float xcut2, int *nbr, int *rnbr,
+                                                long long stride, int cap, int rcap, int cnt, int rcnt)
+{
+    for (int j = s0; j < e; ++j) {
+        if (j == i) continue;
+        const float4 q = sm[j - base];
+        const float ddx = q.x + ox;
+        const float ddy = q.y + oy;
+        const float ddz = q.z + oz;
+        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+        if (F && r2 < fcut2) {
+            if (cnt < cap) nbr[(long long)cnt * stride + i] = j;
+            ++cnt;
+        }
+        if (X && r2 < xcut2) {
+            if (rcnt < rcap) rnbr[(long long)rcnt * stride + i] = j;
+            ++rcnt;
+        }
+    }
+    return make_int2(cnt, rcnt);
+}
+
+// One part (a run of sub-cells [ua, ub] of a row, periodic shift in ox) for
+// the whole warp: staged when it fits, each lane over its own sub-range
+// [a, b] (empty when b < a).
+__device__ __forceinline__ int2 scan_part(const DevParams &P, const DevArrays &A, float4 *sm, int kb, int ua, int ub,
+                                          int a, int b, long long i, float ox, float oy, float oz, float fcut2,
+                                          float xcut2, int2 c)
+{
+    const int S = A.cell_start[kb + ua], E = A.cell_start[kb + ub + 1];   // the same for every lane
+    const int s0 = b >= a ? A.cell_start[kb + a] : 0, e = b >= a ? A.cell_start[kb + b + 1] : 0;
+    const int cap = P.nbr_cap, rcap = P.rnbr_cap;
+    const long long stride = P.nbr_stride;
+    if (E - S > kStageCap)
+        return scan_lists(A.npos, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr, stride, cap, rcap, c);
+    __syncwarp();                              // the previous part's reads are done
+    for (int k = (int)(threadIdx.x & 31); k < E - S; k += 32) sm[k] = A.npos[S + k];
+    __syncwarp();
+    if (xcut2 <= 0.f)
+        return scan_range_smem<true, false>(sm, S, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr, stride, cap,
+                                            rcap, c.x, c.y);
+    if (fcut2 <= 0.f)
+        return scan_range_smem<false, true>(sm, S, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr, stride, cap,
+                                            rcap, c.x, c.y);
+    return scan_range_smem<true, true>(sm, S, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr, stride, cap, rcap,
+                                       c.x, c.y);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256, 8) k_nlist_staged(DevParams P, DevArrays A, DevArrays B)
+{
+    extern __shared__ float4 s_stage[];
+    if (!status_ok(A.status) || !*A.need_rebuild) return;   // uniform
+    const long long i = gtid();
+    const unsigned full = 0xFFFFFFFFu;
+    float4 *sm = s_stage + (threadIdx.x >> 5) * kStageCap;
+    const bool valid = i < P.n;
+    int2 cc = make_int2(0, 0);
+    const float4 p = valid ? A.npos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t bits = __float_as_uint(p.w);
+    const int ti = bits_type(bits), cx = bits_cx(bits), cy = bits_cy(bits), cz = bits_cz(bits);
+    const int rp = valid ? rep_of(P, B, i) : 0;   // B: the new order (A is copied back below)
+    const RepDev &Rp = A.reps[rp];
+    const int sh = P.sub_shift;
+    // lanes of one type whose home cells are in one row (of one replica) form a group
+    const int gkey = valid ? ti * P.ncell + A.rank_of[Rp.cell_off + (cz * Rp.nc[1] + cy) * Rp.nc[0]] : -1;
+    const float wy = Rp.wf[1], wz = Rp.wf[2];
+    const float ry = p.y - (float)cy * wy, rz = p.z - (float)cz * wz;
+    const float gyl = fmaxf(ry, 0.f), gyu = fmaxf(wy - ry, 0.f);
+    const float gzl = fmaxf(rz, 0.f), gzu = fmaxf(wz - rz, 0.f);
+    const float csk = Rp.cscale[0] * (float)(1 << sh);
+    const float xlo = (float)((cx - 1) << sh), xhi = (float)(((cx + 2) << sh) - 1);
+    unsigned pending = __ballot_sync(full, valid);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int gk = __shfl_sync(full, gkey, leader);
+        const bool member = valid && gkey == gk;
+        pending &= ~__ballot_sync(full, member);
+        // the group's rows, the same for every member: from the leader
+        const int gt = __shfl_sync(full, ti, leader), gcy = __shfl_sync(full, cy, leader);
+        const int gcz = __shfl_sync(full, cz, leader), grp = __shfl_sync(full, rp, leader);
+        const RepDev &G = A.reps[grp];
+        const int nx = G.nc[0], ny = G.nc[1], nz = G.nc[2], nsx = nx << sh;
+        const float Lx = (float)G.L[0], Ly = (float)G.L[1], Lz = (float)G.L[2];
+        for (int dz = -1; dz <= 1; ++dz) {
+            int zz = gcz + dz;
+            float oz = -p.z;
+            if (zz < 0) { zz += nz; oz -= Lz; }
+            if (zz >= nz) { zz -= nz; oz += Lz; }
+            const float gz = dz < 0 ? gzl : (dz > 0 ? gzu : 0.f);
+            for (int dy = -1; dy <= 1; ++dy) {
+                int yy = gcy + dy;
+                float oy = -p.y;
+                if (yy < 0) { yy += ny; oy -= Ly; }
+                if (yy >= ny) { yy -= ny; oy += Ly; }
+                const float gy = dy < 0 ? gyl : (dy > 0 ? gyu : 0.f);
+                const float d2r = gy * gy + gz * gz;
+                const int row = A.rank_of[G.cell_off + (zz * ny + yy) * nx];
+                for (int t = 0; t < P.ntypes; ++t) {
+                    const float fcut2 = P.fl2f[gt * kMaxTypes + t];
+                    const float xcut2 = P.xl2f[gt * kMaxTypes + t];
+                    const float cut = fmaxf(fcut2, xcut2);
+                    const bool adm = member && d2r < cut;
+                    if (!__any_sync(full, adm)) continue;
+                    // this lane's window and parts, exactly as in k_nlist
+                    int xa = 0, xb = -1;
+                    if (adm) {
+                        const float wr = sqrtf(cut - d2r + kWinSlack2) + kWinSlack;
+                        xa = (int)fminf(fmaxf(floorf((p.x - wr) * csk), xlo), xhi);
+                        xb = (int)fminf(fmaxf(floorf((p.x + wr) * csk), xlo), xhi);
+                    }
+                    const int ua = __reduce_min_sync(full, adm ? xa : INT_MAX);
+                    const int ub = __reduce_max_sync(full, adm ? xb : INT_MIN);
+                    const int kb = (t * P.ncell + row) << sh;
+                    int la = 1, lb = 0, ra = 1, rb = 0;   // this lane's wrapped parts (empty)
+                    if (adm && xa < 0) {
+                        la = min(max(xa + nsx, xb + 1), nsx);
+                        lb = nsx - 1;
+                        xa = 0;
+                    }
+                    if (adm && xb >= nsx) {
+                        ra = 0;
+                        rb = min(xb - nsx, xa - 1);
+                        xb = nsx - 1;
+                    }
+                    if (adm) {
+                        xa = min(xa, nsx);
+                        xb = max(xb, -1);
+                    }
+                    if (ua < 0)
+                        cc = scan_part(P, A, sm, kb, ua + nsx, nsx - 1, la, lb, i, -p.x - Lx, oy, oz, fcut2, xcut2,
+                                       cc);
+                    if (ub >= nsx)
+                        cc = scan_part(P, A, sm, kb, 0, ub - nsx, ra, rb, i, Lx - p.x, oy, oz, fcut2, xcut2, cc);
+                    cc = scan_part(P, A, sm, kb, min(max(ua, 0), nsx), max(min(ub, nsx - 1), -1), xa, xb, i, -p.x,
+                                   oy, oz, fcut2, xcut2, cc);
+                }
+            }
+        }
+    }
+    const int cap = P.nbr_cap, rcap = P.rnbr_cap;
+    if (valid) {
+        A.nn[i] = min(cc.x, cap);
+        A.rnn[i] = min(cc.y, rcap);
+        if (cc.x > cap || cc.y > rcap) {
+            atomicOr(A.status, (uint32_t)kStOverflow);
+            atomicMax(&A.nbr_need[0], cc.x);
+            atomicMax(&A.nbr_need[1], cc.y);
+        }
+    }
+    const int idx[2] = {cNlistEntries, cRnlistEntries};
+    const unsigned long long v[2] = {(unsigned long long)min(cc.x, cap), (unsigned long long)min(cc.y, rcap)};
+    warp_counts<2>(A.counters, idx, v);
+    if (valid) copyback_particle<R>(P, A, B, i);
 }
 
 // Start of a captured step: with end_prev, first the end of the step before
@@ -834,14 +1042,13 @@ void launch_cell_key(const DevParams &P, const DevArrays &A, Launch L)
     k_cell_key<<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A);
 }
 
+// tile-local prefixes and tile offsets only: k_scatter and k_cell_sort add the offsets
 void launch_cell_scan(const DevArrays &A, int32_t *block_sums, int ncell, Launch L)
 {
     const int nb = (ncell + kScanTile - 1) / kScanTile;
     k_scan_tiles<<<nb, kScanThreads, 0, L.stream>>>(A.cell_count, A.cell_start, block_sums, ncell,
                                                      A.need_rebuild, A.status);
     k_scan_sums<<<1, kScanThreads, 0, L.stream>>>(block_sums, nb, A.need_rebuild, A.status);
-    k_scan_add<<<grid_for(ncell, 256), 256, 0, L.stream>>>(A.cell_start, block_sums, ncell, nb,
-                                                           A.need_rebuild, A.status);
 }
 
 void launch_scan(const int32_t *in, int32_t *out, int32_t *bsum, int n, const int32_t *gate, const uint32_t *status,
@@ -854,15 +1061,15 @@ void launch_scan(const int32_t *in, int32_t *out, int32_t *bsum, int n, const in
     k_scan_add<<<grid_for(n, 256), 256, 0, L.stream>>>(out, bsum, n, nb, gate, status);
 }
 
-void launch_scatter(const DevParams &P, const DevArrays &A, Launch L)
+void launch_scatter(const DevParams &P, const DevArrays &A, const int32_t *block_sums, Launch L)
 {
     if (P.n == 0) return;
-    k_scatter<<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A);
+    k_scatter<<<grid_for(P.n, L.block), L.block, 0, L.stream>>>(P, A, block_sums);
 }
 
-void launch_cell_sort(const DevArrays &A, int ncell, Launch L)
+void launch_cell_sort(const DevArrays &A, int ncell, const int32_t *block_sums, Launch L)
 {
-    k_cell_sort<<<grid_for(ncell, 128), 128, 0, L.stream>>>(A, ncell);
+    k_cell_sort<<<grid_for(ncell, 128), 128, 0, L.stream>>>(A, ncell, block_sums);
 }
 
 void launch_gather(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, Launch L)
@@ -879,10 +1086,16 @@ void launch_gather(const DevParams &P, const DevArrays &A, const DevArrays &B, b
 void launch_nlist(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, int block, Launch L)
 {
     if (P.n == 0) return;
-    if (fp64)
-        k_nlist<double><<<grid_for(P.n, block), block, 0, L.stream>>>(P, A, B);
-    else
-        k_nlist<float><<<grid_for(P.n, block), block, 0, L.stream>>>(P, A, B);
+    const unsigned g = grid_for(P.n, block);
+    if (P.list_staged) {
+        const size_t sm = (size_t)(block / 32) * kStageCap * sizeof(float4);
+        if (fp64) k_nlist_staged<double><<<g, block, sm, L.stream>>>(P, A, B);
+        else k_nlist_staged<float><<<g, block, sm, L.stream>>>(P, A, B);
+    } else if (fp64) {
+        k_nlist<double><<<g, block, 0, L.stream>>>(P, A, B);
+    } else {
+        k_nlist<float><<<g, block, 0, L.stream>>>(P, A, B);
+    }
 }
 
 void launch_rebuild_done(const DevArrays &A, Launch L) { k_rebuild_done<<<1, 1, 0, L.stream>>>(A); }

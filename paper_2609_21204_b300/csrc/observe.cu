@@ -38,8 +38,9 @@ __global__ void k_rdf(DevParams P, DevArrays A, int rep, int ta, int tb, double 
             const int yy = (cy + dy + ny) % ny;
             for (int dx = -1; dx <= 1; ++dx) {
                 const int xx = (cx + dx + nx) % nx;
-                const int key = tb * P.ncell + A.rank_of[R.cell_off + (zz * ny + yy) * nx + xx];
-                const int s0 = A.cell_start[key], e = A.cell_start[key + 1];
+                // the cell's 2^sub_shift sub-cells are consecutive sort keys
+                const int key = (tb * P.ncell + A.rank_of[R.cell_off + (zz * ny + yy) * nx + xx]) << P.sub_shift;
+                const int s0 = A.cell_start[key], e = A.cell_start[key + (1 << P.sub_shift)];
                 for (int j = s0; j < e; ++j) {
                     if (j == i) continue;
                     if (ta == tb && A.tag[j] <= tgi) continue;

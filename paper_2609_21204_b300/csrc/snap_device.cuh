@@ -64,7 +64,10 @@ struct DevParams {
     int64_t nbr_stride;     // column stride of both neighbour lists
     int32_t nrep;
     int32_t screen;         // mixed mode: FP32 pre-screen of the proposal test, FP32 velocities
-    int32_t ncell;          // cells over all replicas; sort keys are type * ncell + cell
+    int32_t ncell;          // cells over all replicas
+    int32_t list_staged;    // list build: 1 warps staging candidates in shared memory, 0 lane by lane
+    int32_t sub_shift;      // log2 of the sub-cells along x per cell: sort keys are
+                            // ((type * ncell + rank of the row's first cell) << sub_shift) + sub-cell x
     int32_t mh_cells, mh_moves;   // MH checkerboard cells and active cells per sweep
     float mh_eps;           // weight of the uniform component of the learned proposal
     int32_t log_events;     // record bond-formation events in the plain sweep

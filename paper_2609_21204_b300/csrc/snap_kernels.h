@@ -17,8 +17,8 @@ int sm_count();
 // ---- neighbour-list maintenance (all early-exit unless *need_rebuild) ----
 void launch_cell_key(const DevParams &P, const DevArrays &A, Launch L);
 void launch_cell_scan(const DevArrays &A, int32_t *block_sums, int ncell, Launch L);
-void launch_scatter(const DevParams &P, const DevArrays &A, Launch L);
-void launch_cell_sort(const DevArrays &A, int ncell, Launch L);
+void launch_scatter(const DevParams &P, const DevArrays &A, const int32_t *block_sums, Launch L);
+void launch_cell_sort(const DevArrays &A, int ncell, const int32_t *block_sums, Launch L);
 void launch_gather(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, Launch L);
 void launch_nlist(const DevParams &P, const DevArrays &A, const DevArrays &B, bool fp64, int block, Launch L);
 void launch_rebuild_done(const DevArrays &A, Launch L);

@@ -29,7 +29,7 @@ def test_autotune_with_fake_timer_caches(tmp_path):
     path = tmp_path / "tune.json"
     r = at.autotune(s, timer=timer, cache_path=path)
     assert r["block_size"] == 64 and r["skin"] == 0.3 and not r["cached"]
-    n_trials = len(at.BLOCKS) * len(at.SKINS) + len(at.LIST_BLOCKS) - 1
+    n_trials = len(at.BLOCKS) * len(at.SKINS) + len(at.LIST_BLOCKS) - 1 + len(at.LIST_SUBCELLS) - 1
     assert len(calls) == n_trials
     r2 = at.autotune(s, timer=timer, cache_path=path)
     assert r2["cached"] and r2["block_size"] == 64
@@ -48,6 +48,24 @@ def test_autotune_searches_list_block_at_the_best_shape(tmp_path):
 
     r = at.autotune(s, timer=timer, cache_path=tmp_path / "t.json")
     assert (r["block_size"], r["skin"], r["list_block"]) == (64, 0.4, 256)
-    stage2 = calls[len(at.BLOCKS) * len(at.SKINS):]
+    stage2 = calls[len(at.BLOCKS) * len(at.SKINS):][:len(at.LIST_BLOCKS) - 1]
     assert [c["list_block"] for c in stage2] == list(at.LIST_BLOCKS[1:])
     assert all((c["block_size"], c["skin"]) == (64, 0.4) for c in stage2)
+
+
+def test_autotune_searches_list_subcells_after_the_list_block(tmp_path):
+    """The sub-cells per cell are searched last, at the best (block, skin,
+    list block); a faster choice wins."""
+    s = assoc_ab(seed=3, n_a=50, n_b=50)
+    calls = []
+
+    def timer(cfg):
+        calls.append(cfg)
+        return (1.0 + abs(cfg["skin"] - 0.3) + cfg["block_size"] / 1000.0
+                + {128: 0.0, 256: 0.01, 64: 0.02}[cfg["list_block"]] + {0: 0.01, 8: 0.0, 2: 0.02}[cfg["list_subcells"]])
+
+    r = at.autotune(s, timer=timer, cache_path=tmp_path / "t.json")
+    assert (r["block_size"], r["skin"], r["list_block"], r["list_subcells"]) == (64, 0.3, 128, 8)
+    stage3 = calls[-(len(at.LIST_SUBCELLS) - 1):]
+    assert [c["list_subcells"] for c in stage3] == list(at.LIST_SUBCELLS[1:])
+    assert all((c["block_size"], c["skin"], c["list_block"]) == (64, 0.3, 128) for c in stage3)
