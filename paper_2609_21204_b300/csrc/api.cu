@@ -96,7 +96,6 @@ struct snap_ctx {
     int cas_cap = 1 << 16;           // push-mode compare-and-swap retries (snap_set_retry_limit)
     int list_block = 256;            // threads per block of the list build (snap_set_list_block)
     int list_sub = 0;                // sub-cells along x per cell requested (snap_set_list_subcells; 0: automatic)
-    int list_staged = 0;             // list build variant, from SNAP_LIST_BUILD when the context is made
     int sub_shift = 0;               // log2 of the sub-cells in use (set when the cell grid is laid out)
     int kinetic_T = 0;               // sweep temperature: 0 set-point, 1 kinetic (snap_set_kinetic_temperature)
 };
@@ -154,16 +153,6 @@ uint32_t morton2(uint32_t y, uint32_t z)
     uint32_t m = 0;
     for (int b = 0; b < 10; ++b) m |= ((y >> b) & 1u) << (2 * b) | ((z >> b) & 1u) << (2 * b + 1);
     return m;
-}
-
-// Which list build runs: SNAP_LIST_BUILD=staged (warps stage candidates in
-// shared memory) or lane (each lane reads its candidates itself); both build
-// the same lists, entry for entry.
-bool list_build_staged()
-{
-    const char *m = std::getenv("SNAP_LIST_BUILD");
-    if (!m) return false;
-    return std::strcmp(m, "staged") == 0;
 }
 
 // Margin added to every list cut-off: 1e-4, or more where the FP32 wrapped
@@ -334,7 +323,6 @@ void fill_params(snap_ctx *c)
     P.screen = c->fp64 ? 0 : 1;
     P.ncell = c->ncell_total;
     P.sub_shift = c->sub_shift;
-    P.list_staged = c->list_staged;
     P.mh_cells = c->mh_mode ? c->mh_nc[0] * c->mh_nc[1] * c->mh_nc[2] : 0;
     P.mh_moves = c->mh_mode ? P.mh_cells / 8 : 0;
     P.mh_eps = (float)c->mh_eps;
@@ -993,7 +981,6 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
 
     snap_ctx *c = new snap_ctx();
     c->cfg = *cfg;
-    c->list_staged = list_build_staged() ? 1 : 0;
     c->cfg.replica_n = nullptr;
     c->cfg.replica_box = nullptr;
     c->cfg.replica_kT = nullptr;
@@ -1047,6 +1034,7 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
               alloc_arr(c, A.prop_d, n) && alloc_arr(c, A.prio, n) && alloc_arr(c, A.best, n) &&
               alloc_arr(c, A.fpart, n) && alloc_arr(c, A.brk, n) && alloc_arr(c, A.rx_order, (size_t)nrep * kMaxRx) &&
               alloc_arr(c, A.step, 1) && alloc_arr(c, A.status, 1) && alloc_arr(c, A.need_rebuild, 1) && alloc_arr(c, A.list_fresh, 1) &&
+              alloc_arr(c, A.gathered, 1) &&
               alloc_arr(c, A.nbr_need, 2) && alloc_arr(c, A.counters, (size_t)cNumCounters * kCopies) &&
               alloc_arr(c, A.site_list, n) && alloc_arr(c, A.list_count, 1) &&
               alloc_arr(c, A.cont, n * kContenders) && alloc_arr(c, A.ncont, n) &&
@@ -1058,11 +1046,12 @@ extern "C" snap_status snap_init(snap_ctx **out, const snap_config *cfg)
     // B shares the non-permuted arrays with A
     DevArrays &B = c->B;
     B.rtag = A.rtag; B.ref4 = A.ref4; B.npos = A.npos; B.force = A.force; B.status = A.status; B.need_rebuild = A.need_rebuild;
-    B.step = A.step; B.reps = A.reps; B.order = A.order; B.ksum = A.ksum;
+    B.step = A.step; B.reps = A.reps; B.order = A.order; B.ksum = A.ksum; B.gathered = A.gathered;
     if (cudaMemsetAsync(A.status, 0, 4, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.step, 0, 8, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.need_rebuild, 0, 4, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.list_fresh, 0, 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(A.gathered, 0, 4, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.nbr_need, 0, 8, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.counters, 0, sizeof(unsigned long long) * cNumCounters * kCopies, c->stream) != cudaSuccess ||
         cudaMemsetAsync(A.list_count, 0, 4, c->stream) != cudaSuccess ||

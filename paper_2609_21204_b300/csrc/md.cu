@@ -244,6 +244,7 @@ __global__ void k_gather(DevParams P, DevArrays A, DevArrays B)
     const long long k = gtid();
     if (k >= P.n) return;
     if (!status_ok(A.status) || !*A.need_rebuild) return;
+    if (k == 0) *A.gathered = 1;
     const int i = A.order[k];
     const double x = A.x[i], y = A.y[i], z = A.z[i];
     B.x[k] = x; B.y[k] = y; B.z[k] = z;
@@ -381,7 +382,10 @@ constexpr float kWinSlack = 5e-4f;
 template <typename R>
 __global__ void __launch_bounds__(256, 8) k_nlist(DevParams P, DevArrays A, DevArrays B)
 {
-    if (!status_ok(A.status) || !*A.need_rebuild) return;   // uniform
+    // uniform: this rebuild's gather ran (the status was clear at its start).
+    // Not the status itself: a block that overflows its list latches a status
+    // bit, and every block must still copy its particles back.
+    if (!*A.gathered) return;
     const long long i = gtid();
     int2 cc = make_int2(0, 0);
     const int cap = P.nbr_cap, rcap = P.rnbr_cap;
@@ -466,175 +470,6 @@ __global__ void __launch_bounds__(256, 8) k_nlist(DevParams P, DevArrays A, DevA
     if (i < P.n) copyback_particle<R>(P, A, B, i);
 }
 
-// The same lists built by warps that stage candidates in shared memory.  The
-// lanes of a warp whose home cells lie in one row of cells (same type and
-// replica: nearly every warp, particles being sorted by row) share the 9 rows
-// around it; for each row and type the warp loads the union of its lanes'
-// x windows once, coalesced, into shared memory, and every lane then tests its
-// own window from there, in the same order as the per-lane build, so the
-// lists are identical entry for entry.  A union longer than the staging
-// buffer is tested from global memory lane by lane.  Lanes of different rows
-// (at row, type or replica boundaries) take turns, group by group.
-constexpr int kStageCap = 256;   // staged candidates per warp
-
-template <bool F, bool X>
-__device__ __forceinline__ int2 scan_range_smem(const float4 *sm, int base, int s0, int e, long long i, float ox,
-                                                float oy, float oz, float fcut2, float xcut2, int *nbr, int *rnbr,
-                                                long long stride, int cap, int rcap, int cnt, int rcnt)
-{
-    for (int j = s0; j < e; ++j) {
-        if (j == i) continue;
-        const float4 q = sm[j - base];
-        const float ddx = q.x + ox;
-        const float ddy = q.y + oy;
-        const float ddz = q.z + oz;
-        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-        if (F && r2 < fcut2) {
-            if (cnt < cap) nbr[(long long)cnt * stride + i] = j;
-            ++cnt;
-        }
-        if (X && r2 < xcut2) {
-            if (rcnt < rcap) rnbr[(long long)rcnt * stride + i] = j;
-            ++rcnt;
-        }
-    }
-    return make_int2(cnt, rcnt);
-}
-
-// One part (a run of sub-cells [ua, ub] of a row, periodic shift in ox) for
-// the whole warp: staged when it fits, each lane over its own sub-range
-// [a, b] (empty when b < a).
-__device__ __forceinline__ int2 scan_part(const DevParams &P, const DevArrays &A, float4 *sm, int kb, int ua, int ub,
-                                          int a, int b, long long i, float ox, float oy, float oz, float fcut2,
-                                          float xcut2, int2 c)
-{
-    const int S = A.cell_start[kb + ua], E = A.cell_start[kb + ub + 1];   // the same for every lane
-    const int s0 = b >= a ? A.cell_start[kb + a] : 0, e = b >= a ? A.cell_start[kb + b + 1] : 0;
-    const int cap = P.nbr_cap, rcap = P.rnbr_cap;
-    const long long stride = P.nbr_stride;
-    if (E - S > kStageCap)
-        return scan_lists(A.npos, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr, stride, cap, rcap, c);
-    __syncwarp();                              // the previous part's reads are done
-    for (int k = (int)(threadIdx.x & 31); k < E - S; k += 32) sm[k] = A.npos[S + k];
-    __syncwarp();
-    if (xcut2 <= 0.f)
-        return scan_range_smem<true, false>(sm, S, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr, stride, cap,
-                                            rcap, c.x, c.y);
-    if (fcut2 <= 0.f)
-        return scan_range_smem<false, true>(sm, S, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr, stride, cap,
-                                            rcap, c.x, c.y);
-    return scan_range_smem<true, true>(sm, S, s0, e, i, ox, oy, oz, fcut2, xcut2, A.nbr, A.rnbr, stride, cap, rcap,
-                                       c.x, c.y);
-}
-
-template <typename R>
-__global__ void __launch_bounds__(256, 8) k_nlist_staged(DevParams P, DevArrays A, DevArrays B)
-{
-    extern __shared__ float4 s_stage[];
-    if (!status_ok(A.status) || !*A.need_rebuild) return;   // uniform
-    const long long i = gtid();
-    const unsigned full = 0xFFFFFFFFu;
-    float4 *sm = s_stage + (threadIdx.x >> 5) * kStageCap;
-    const bool valid = i < P.n;
-    int2 cc = make_int2(0, 0);
-    const float4 p = valid ? A.npos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const uint32_t bits = __float_as_uint(p.w);
-    const int ti = bits_type(bits), cx = bits_cx(bits), cy = bits_cy(bits), cz = bits_cz(bits);
-    const int rp = valid ? rep_of(P, B, i) : 0;   // B: the new order (A is copied back below)
-    const RepDev &Rp = A.reps[rp];
-    const int sh = P.sub_shift;
-    // lanes of one type whose home cells are in one row (of one replica) form a group
-    const int gkey = valid ? ti * P.ncell + A.rank_of[Rp.cell_off + (cz * Rp.nc[1] + cy) * Rp.nc[0]] : -1;
-    const float wy = Rp.wf[1], wz = Rp.wf[2];
-    const float ry = p.y - (float)cy * wy, rz = p.z - (float)cz * wz;
-    const float gyl = fmaxf(ry, 0.f), gyu = fmaxf(wy - ry, 0.f);
-    const float gzl = fmaxf(rz, 0.f), gzu = fmaxf(wz - rz, 0.f);
-    const float csk = Rp.cscale[0] * (float)(1 << sh);
-    const float xlo = (float)((cx - 1) << sh), xhi = (float)(((cx + 2) << sh) - 1);
-    unsigned pending = __ballot_sync(full, valid);
-    while (pending) {
-        const int leader = __ffs(pending) - 1;
-        const int gk = __shfl_sync(full, gkey, leader);
-        const bool member = valid && gkey == gk;
-        pending &= ~__ballot_sync(full, member);
-        // the group's rows, the same for every member: from the leader
-        const int gt = __shfl_sync(full, ti, leader), gcy = __shfl_sync(full, cy, leader);
-        const int gcz = __shfl_sync(full, cz, leader), grp = __shfl_sync(full, rp, leader);
-        const RepDev &G = A.reps[grp];
-        const int nx = G.nc[0], ny = G.nc[1], nz = G.nc[2], nsx = nx << sh;
-        const float Lx = (float)G.L[0], Ly = (float)G.L[1], Lz = (float)G.L[2];
-        for (int dz = -1; dz <= 1; ++dz) {
-            int zz = gcz + dz;
-            float oz = -p.z;
-            if (zz < 0) { zz += nz; oz -= Lz; }
-            if (zz >= nz) { zz -= nz; oz += Lz; }
-            const float gz = dz < 0 ? gzl : (dz > 0 ? gzu : 0.f);
-            for (int dy = -1; dy <= 1; ++dy) {
-                int yy = gcy + dy;
-                float oy = -p.y;
-                if (yy < 0) { yy += ny; oy -= Ly; }
-                if (yy >= ny) { yy -= ny; oy += Ly; }
-                const float gy = dy < 0 ? gyl : (dy > 0 ? gyu : 0.f);
-                const float d2r = gy * gy + gz * gz;
-                const int row = A.rank_of[G.cell_off + (zz * ny + yy) * nx];
-                for (int t = 0; t < P.ntypes; ++t) {
-                    const float fcut2 = P.fl2f[gt * kMaxTypes + t];
-                    const float xcut2 = P.xl2f[gt * kMaxTypes + t];
-                    const float cut = fmaxf(fcut2, xcut2);
-                    const bool adm = member && d2r < cut;
-                    if (!__any_sync(full, adm)) continue;
-                    // this lane's window and parts, exactly as in k_nlist
-                    int xa = 0, xb = -1;
-                    if (adm) {
-                        const float wr = sqrtf(cut - d2r + kWinSlack2) + kWinSlack;
-                        xa = (int)fminf(fmaxf(floorf((p.x - wr) * csk), xlo), xhi);
-                        xb = (int)fminf(fmaxf(floorf((p.x + wr) * csk), xlo), xhi);
-                    }
-                    const int ua = __reduce_min_sync(full, adm ? xa : INT_MAX);
-                    const int ub = __reduce_max_sync(full, adm ? xb : INT_MIN);
-                    const int kb = (t * P.ncell + row) << sh;
-                    int la = 1, lb = 0, ra = 1, rb = 0;   // this lane's wrapped parts (empty)
-                    if (adm && xa < 0) {
-                        la = min(max(xa + nsx, xb + 1), nsx);
-                        lb = nsx - 1;
-                        xa = 0;
-                    }
-                    if (adm && xb >= nsx) {
-                        ra = 0;
-                        rb = min(xb - nsx, xa - 1);
-                        xb = nsx - 1;
-                    }
-                    if (adm) {
-                        xa = min(xa, nsx);
-                        xb = max(xb, -1);
-                    }
-                    if (ua < 0)
-                        cc = scan_part(P, A, sm, kb, ua + nsx, nsx - 1, la, lb, i, -p.x - Lx, oy, oz, fcut2, xcut2,
-                                       cc);
-                    if (ub >= nsx)
-                        cc = scan_part(P, A, sm, kb, 0, ub - nsx, ra, rb, i, Lx - p.x, oy, oz, fcut2, xcut2, cc);
-                    cc = scan_part(P, A, sm, kb, min(max(ua, 0), nsx), max(min(ub, nsx - 1), -1), xa, xb, i, -p.x,
-                                   oy, oz, fcut2, xcut2, cc);
-                }
-            }
-        }
-    }
-    const int cap = P.nbr_cap, rcap = P.rnbr_cap;
-    if (valid) {
-        A.nn[i] = min(cc.x, cap);
-        A.rnn[i] = min(cc.y, rcap);
-        if (cc.x > cap || cc.y > rcap) {
-            atomicOr(A.status, (uint32_t)kStOverflow);
-            atomicMax(&A.nbr_need[0], cc.x);
-            atomicMax(&A.nbr_need[1], cc.y);
-        }
-    }
-    const int idx[2] = {cNlistEntries, cRnlistEntries};
-    const unsigned long long v[2] = {(unsigned long long)min(cc.x, cap), (unsigned long long)min(cc.y, rcap)};
-    warp_counts<2>(A.counters, idx, v);
-    if (valid) copyback_particle<R>(P, A, B, i);
-}
-
 // Start of a captured step: with end_prev, first the end of the step before
 // it in the same graph (what k_step_end does, one launch fewer per step),
 // then the rebuild condition.
@@ -650,6 +485,7 @@ __global__ void k_set_rebuild_cond(DevArrays A, cudaGraphConditionalHandle h, in
 
 __global__ void k_rebuild_done(DevArrays A)
 {
+    *A.gathered = 0;
     if (!status_ok(A.status)) return;
     if (*A.need_rebuild) {
         *A.need_rebuild = 0;
@@ -1087,15 +923,8 @@ void launch_nlist(const DevParams &P, const DevArrays &A, const DevArrays &B, bo
 {
     if (P.n == 0) return;
     const unsigned g = grid_for(P.n, block);
-    if (P.list_staged) {
-        const size_t sm = (size_t)(block / 32) * kStageCap * sizeof(float4);
-        if (fp64) k_nlist_staged<double><<<g, block, sm, L.stream>>>(P, A, B);
-        else k_nlist_staged<float><<<g, block, sm, L.stream>>>(P, A, B);
-    } else if (fp64) {
-        k_nlist<double><<<g, block, 0, L.stream>>>(P, A, B);
-    } else {
-        k_nlist<float><<<g, block, 0, L.stream>>>(P, A, B);
-    }
+    if (fp64) k_nlist<double><<<g, block, 0, L.stream>>>(P, A, B);
+    else k_nlist<float><<<g, block, 0, L.stream>>>(P, A, B);
 }
 
 void launch_rebuild_done(const DevArrays &A, Launch L) { k_rebuild_done<<<1, 1, 0, L.stream>>>(A); }

@@ -65,7 +65,6 @@ struct DevParams {
     int32_t nrep;
     int32_t screen;         // mixed mode: FP32 pre-screen of the proposal test, FP32 velocities
     int32_t ncell;          // cells over all replicas
-    int32_t list_staged;    // list build: 1 warps staging candidates in shared memory, 0 lane by lane
     int32_t sub_shift;      // log2 of the sub-cells along x per cell: sort keys are
                             // ((type * ncell + rank of the row's first cell) << sub_shift) + sub-cell x
     int32_t mh_cells, mh_moves;   // MH checkerboard cells and active cells per sweep
@@ -145,6 +144,7 @@ struct DevArrays {
     uint32_t *status;
     int32_t *need_rebuild;
     int32_t *list_fresh;            // 1 from a rebuild until an MD step has stored the force-list shift codes
+    int32_t *gathered;              // 1 from a rebuild's gather until its end: the list build copies back
     int32_t *nbr_need;              // largest [force, reactive] count seen (overflow sizing)
     unsigned long long *counters;   // sweep counters, see Counter
     unsigned long long *life_hist;
