@@ -17,7 +17,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
           "--expt-relaxed-constexpr", "-I", str(ROOT / "include")]
 # the bond sweep and the integrator must not contract a*b+c into fma
 PER_FILE = {"exact.cu": ["-fmad=false"], "mh.cu": ["-fmad=false"], "observe.cu": ["-fmad=false"]}
-SOURCES = ["md.cu", "exact.cu", "io.cu", "api.cu", "noalloc.cu", "mlp.cu", "mlp_api.cu", "mh.cu", "observe.cu"]
+SOURCES = ["md.cu", "nlist.cu", "exact.cu", "io.cu", "api.cu", "noalloc.cu", "mlp.cu", "mlp_api.cu", "mh.cu", "observe.cu"]
 
 
 def nvcc() -> str:
