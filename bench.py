@@ -764,12 +764,13 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
     sweep_bytes = (9 + 24 + 60) * n + 21 * st2["scanned"]
     sweep_gbs = sweep_bytes / (ph["sweep"] / 1e3) / 1e9 if ph["sweep"] > 0 else None
 
-    # kernels launched: per step the rebuild condition, the sweep (begin + 4 per
-    # reaction: proposals and break draws, resolution, acceptance, apply), the
-    # fused force + Langevin kernel and step end; per rebuild 10 more (cell keys,
-    # 3 scan kernels, scatter, cell sort, gather, copy back, lists, done)
+    # kernels launched: per step the rebuild condition (which also ends the step
+    # before it), the sweep (begin + 4 per reaction: proposals and break draws,
+    # resolution, acceptance, apply) and the fused force + Langevin kernel; one
+    # step end per 20-step graph; per rebuild 8 more (cell keys, 2 scan kernels,
+    # scatter, cell sort, gather, lists with the copy back, done)
     builds = st1["nlist_builds"] - st0["nlist_builds"]
-    launches = K * (1 + (1 + 4 * len(s.reactions)) + 2) + 10 * builds
+    launches = K * (2 + 1 + 4 * len(s.reactions)) + -(-K // 20) + 8 * builds
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
