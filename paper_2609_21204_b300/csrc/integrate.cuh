@@ -13,7 +13,7 @@ namespace snap {
 
 __device__ __forceinline__ U4 langevin_draw(const RepDev &Rp, const DevArrays &A, long long i, long long step)
 {
-    const uint32_t tl = (uint32_t)(A.tag[i] - Rp.tag_off);
+    const uint32_t tl = (uint32_t)(__ldcs(A.tag + i) - Rp.tag_off);
     return philox10(U4{(uint32_t)((unsigned long long)step & 0xFFFFFFFFull), (uint32_t)((unsigned long long)step >> 32),
                        tl, 0u},
                     Rp.key0, rx_key1(Rp, 0, kLangevin));
@@ -22,7 +22,7 @@ __device__ __forceinline__ U4 langevin_draw(const RepDev &Rp, const DevArrays &A
 __device__ __forceinline__ bool moved_past_skin(const DevParams &P, const DevArrays &A, long long i, float rx,
                                                 float ry, float rz)
 {
-    const float4 ref = A.ref4[i];
+    const float4 ref = __ldcs(A.ref4 + i);
     const float ex = __fsub_rn(rx, ref.x), ey = __fsub_rn(ry, ref.y), ez = __fsub_rn(rz, ref.z);
     return __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez)) > P.disp2f;
 }
@@ -104,7 +104,7 @@ __device__ __forceinline__ void integrate_mixed(const DevParams &P, DevArrays &A
                                                 float4 *pos_out)
 {
     const U4 w = langevin_draw(Rp, A, i, step);
-    float4 v = A.v4[i];
+    float4 v = __ldcs(A.v4 + i);   // streaming: read once per step
     const float cn = Rp.noise_cf, g = P.gammaf, s3 = P.sqrt3f, dt = P.dtf;   // rounded on the host
     // xi = sqrt(3) (2u - 1) with u = (w >> 8 + 1/2) 2^-24 in (0, 1)
     const float ux = fmaf((float)(w.x >> 8), 0x1.0p-24f, 0x1.0p-25f);
@@ -113,9 +113,9 @@ __device__ __forceinline__ void integrate_mixed(const DevParams &P, DevArrays &A
     v.x = fmaf(dt, fmaf(cn, __fmul_rn(s3, fmaf(2.0f, ux, -1.0f)), fmaf(-g, v.x, fx)), v.x);
     v.y = fmaf(dt, fmaf(cn, __fmul_rn(s3, fmaf(2.0f, uy, -1.0f)), fmaf(-g, v.y, fy)), v.y);
     v.z = fmaf(dt, fmaf(cn, __fmul_rn(s3, fmaf(2.0f, uz, -1.0f)), fmaf(-g, v.z, fz)), v.z);
-    const double x1 = fma(P.dt, (double)v.x, A.x[i]);
-    const double y1 = fma(P.dt, (double)v.y, A.y[i]);
-    const double z1 = fma(P.dt, (double)v.z, A.z[i]);
+    const double x1 = fma(P.dt, (double)v.x, __ldcs(A.x + i));
+    const double y1 = fma(P.dt, (double)v.y, __ldcs(A.y + i));
+    const double z1 = fma(P.dt, (double)v.z, __ldcs(A.z + i));
     if ((step & (kMixedResync - 1)) == 0) {          // uniform over the grid
         // origin of the frozen cell, as the rebuild computed it
         const uint32_t b = w_bits(p);

@@ -163,13 +163,13 @@ __device__ __forceinline__ bool force_particle(const DevParams &P, const DevArra
     using V = typename Vec4<R>::T;
     const V *pos = reinterpret_cast<const V *>(A.pos4);
     const int ti = bits_type(w_bits(pi));
-    const int nn = A.nn[i];
+    const int nn = __ldcs(A.nn + i);
     const long long stride = P.nbr_stride;
     int *nb = A.nbr + i;
     // bond partners first: their slot words and sorted indices are independent
     // of the pair loop, so the tag -> index loads overlap it
-    const int4 dp = A.dp[i];
-    const int drx = A.drx[i];
+    const int4 dp = __ldcs(A.dp + i);
+    const int drx = __ldcs(A.drx + i);
     int dj[kVmax];
     {
         const int dpv[4] = {dp.x, dp.y, dp.z, dp.w};
@@ -179,12 +179,14 @@ __device__ __forceinline__ bool force_particle(const DevParams &P, const DevArra
     // pairs in batches of four: four independent position loads, then the
     // arithmetic in list order, while the next batch's four list entries are
     // already in flight; the pair's cell shift comes with its list entry
-    // (s_shift: unit shifts by code)
+    // (s_shift: unit shifts by code).  The particle's own words, read once per
+    // step, are streaming loads (__ldcs, evicted first) so that the L1 keeps the
+    // neighbours' coordinates, which the block's other threads read again.
     const R wx = Num<R>::w(Rp, 0), wy = Num<R>::w(Rp, 1), wz = Num<R>::w(Rp, 2);
     auto entry = [&](int k) -> uint32_t {
         return k >= nn ? (uint32_t)i | (13u << kIdxBits)
                : MODE == kShiftStore ? (uint32_t)nb[(long long)k * stride]   // rewritten below
-                                     : (uint32_t)__ldg(nb + (long long)k * stride);
+                                     : (uint32_t)__ldcs(nb + (long long)k * stride);
     };
     uint32_t en[4];
 #pragma unroll
@@ -234,8 +236,8 @@ __device__ __forceinline__ bool force_particle(const DevParams &P, const DevArra
     // static bonds
     bool bad = false;
     if (P.has_static) {
-        const int4 sp = A.sp[i];
-        const int sbt = A.sbt[i];
+        const int4 sp = __ldcs(A.sp + i);
+        const int sbt = __ldcs(A.sbt + i);
         const int spv[4] = {sp.x, sp.y, sp.z, sp.w};
 #pragma unroll
         for (int s = 0; s < kSmax; ++s) {
