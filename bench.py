@@ -264,6 +264,48 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+def inside_cut_fraction(s, pos, nbar):
+    """Fraction of force-list entries whose pair lies inside its WCA cut at
+    these positions (pairs counted with a k-d tree; nbar = entries per particle)."""
+    try:
+        from scipy.spatial import cKDTree
+        box = np.asarray(s.box, dtype=np.float64)
+        p = np.mod(pos, box)
+        sig = np.asarray(s.sigma, dtype=np.float64)
+        rc = 0.5 * (sig[:, None] + sig[None, :]) * 2.0 ** (1.0 / 6.0)
+        pairs = cKDTree(p, boxsize=box).query_pairs(float(rc.max()), output_type="ndarray")
+        d = p[pairs[:, 0]] - p[pairs[:, 1]]
+        d -= box * np.rint(d / box)
+        r2 = (d * d).sum(1)
+        t = np.asarray(s.types)
+        inside = int((r2 < rc[t[pairs[:, 0]], t[pairs[:, 1]]] ** 2).sum())
+        return 2.0 * inside / (nbar * len(p))
+    except Exception:
+        return None
+
+
+def fp64_dgemm_tflops(torch):
+    """FP64 rate of this GPU: cuBLAS DGEMM of two 8192^2 matrices, best of 3."""
+    try:
+        a = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+        b = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+        torch.matmul(a, b)
+        best = None
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        del a, b
+        return 2.0 * 8192 ** 3 / best / 1e12
+    except Exception:
+        return None
+
+
 def md_traffic_from_profile(n):
     """DRAM bytes per launch of the fused force + Langevin kernel from the
     committed ncu summary, if it was taken on the current kernel sources;
@@ -821,11 +863,29 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
                 t64 = max_all(e0.elapsed_time(e1) / 1e3)
                 v64 = n_all * K64 / t64
                 ph64 = sim64.step_profiled(max(5, args.profile_steps // 5))
+                pos64 = sim64.positions()
             finally:
                 sim64.close()
             out["speedup_mixed_vs_fp64_plain"] = value / v64
+            # the FP64 force + Langevin kernel is bound by the FP64 pipe, not HBM:
+            # algorithmic FP64 FLOPs per particle, counted from the kernel's
+            # operations (per list entry 14 for the separation and r^2, per pair
+            # inside the cut 15 for the WCA force and its accumulation; per dynamic
+            # bond end 24; 47 for the Langevin update and the relative coordinate),
+            # against the FP64 rate of cuBLAS DGEMM on this GPU, measured here
+            nb_dyn = 2.0 * st2["n_bonds"] / n
+            frac_in = inside_cut_fraction(s, pos64, nbar)
+            flop_pp = 14 * nbar + 15 * nbar * (frac_in or 0.0) + 24 * nb_dyn + 47
+            md64_ms = ph64["md"]
+            achieved = flop_pp * n / (md64_ms / 1e3) / 1e12
+            peak64 = fp64_dgemm_tflops(torch)
             return {"value": v64, "ms_per_step": t64 * 1e3 / K64, "steps": K64,
-                    "phases_ms_per_step": {k: round(v, 5) for k, v in ph64.items()}}
+                    "phases_ms_per_step": {k: round(v, 5) for k, v in ph64.items()},
+                    "roofline": {"kernel": "k_step_md_fp64", "bound": "fp64", "achieved": achieved,
+                                 "peak": peak64, "unit": "TFLOP/s",
+                                 "frac": achieved / peak64 if peak64 else None,
+                                 "flop_per_particle": flop_pp, "inside_cut_fraction": frac_in,
+                                 "peak_source": "cuBLAS DGEMM 8192^3 on this GPU (torch.matmul, FP64), best of 3"}}
 
         run_leg(out, "fp64_plain", world, fp64_leg)
         sim = make("mixed")

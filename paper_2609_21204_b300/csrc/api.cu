@@ -516,7 +516,7 @@ void seq_step(snap_ctx *c)
 }
 
 // One captured step whose neighbour-list rebuild is the body of a conditional
-// (IF) node: between rebuilds the ten rebuild kernels are not launched at all.
+// (IF) node: between rebuilds the eight rebuild kernels are not launched at all.
 // first: the graph's first step; the others end the step before them in the
 // condition kernel, last: the graph's last step, which ends with k_step_end.
 cudaError_t capture_step_conditional(snap_ctx *c, bool first, bool last)

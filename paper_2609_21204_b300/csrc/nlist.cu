@@ -286,23 +286,30 @@ __global__ void k_gather(DevParams P, DevArrays A, DevArrays B)
 template <typename R>
 __device__ __forceinline__ void copyback_particle(const DevParams &P, DevArrays &A, const DevArrays &B, long long k)
 {
+    // streaming loads (__ldcs, evicted first): the L1 keeps the candidates'
+    // coordinates that the list scans read
     using V = typename Vec4<R>::T;
-    A.x[k] = B.x[k]; A.y[k] = B.y[k]; A.z[k] = B.z[k];
+    A.x[k] = __ldcs(B.x + k); A.y[k] = __ldcs(B.y + k); A.z[k] = __ldcs(B.z + k);
     if (sizeof(R) == 8) {
-        A.vx[k] = B.vx[k]; A.vy[k] = B.vy[k]; A.vz[k] = B.vz[k];
+        A.vx[k] = __ldcs(B.vx + k); A.vy[k] = __ldcs(B.vy + k); A.vz[k] = __ldcs(B.vz + k);
     } else {
-        A.v4[k] = B.v4[k];
+        A.v4[k] = __ldcs(B.v4 + k);
     }
-    A.ix[k] = B.ix[k]; A.iy[k] = B.iy[k]; A.iz[k] = B.iz[k];
-    A.type[k] = B.type[k]; A.tag[k] = B.tag[k];
-    if (P.nrep > 1) A.rep[k] = B.rep[k];
+    A.ix[k] = __ldcs(B.ix + k); A.iy[k] = __ldcs(B.iy + k); A.iz[k] = __ldcs(B.iz + k);
+    A.type[k] = __ldcs(B.type + k); A.tag[k] = __ldcs(B.tag + k);
+    if (P.nrep > 1) A.rep[k] = __ldcs(B.rep + k);
     if (P.has_static) {
-        A.sp[k] = B.sp[k];
-        A.sbt[k] = B.sbt[k];
+        A.sp[k] = __ldcs(B.sp + k);
+        A.sbt[k] = __ldcs(B.sbt + k);
     }
-    A.dp[k] = B.dp[k]; A.drx[k] = B.drx[k]; A.dbirth[k] = B.dbirth[k];
-    A.occ[k] = B.occ[k];
-    reinterpret_cast<V *>(A.pos4)[k] = reinterpret_cast<const V *>(B.pos4)[k];
+    A.dp[k] = __ldcs(B.dp + k); A.drx[k] = __ldcs(B.drx + k); A.dbirth[k] = __ldcs(B.dbirth + k);
+    A.occ[k] = __ldcs(B.occ + k);
+    if (sizeof(R) == 8) {
+        const double4_32a *src = reinterpret_cast<const double4_32a *>(B.pos4);
+        reinterpret_cast<double4_32a *>(A.pos4)[k] = src[k];
+    } else {
+        reinterpret_cast<float4 *>(A.pos4)[k] = __ldcs(reinterpret_cast<const float4 *>(B.pos4) + k);
+    }
 }
 
 // Two neighbour lists, column-major (entry k of particle i at k * stride + i):
