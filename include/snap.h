@@ -272,7 +272,9 @@ snap_status snap_set_retry_limit(snap_ctx *, int32_t limit);
  * every result, do not depend on it. */
 snap_status snap_set_list_block(snap_ctx *, int32_t threads);
 
-/* Sub-cells along x per neighbour cell for the list build: each cell is cut
+/* (A layout parameter of the neighbour-list build that Sec. II.C's sweep and
+ * the force loop read; the paper has no counterpart.)
+ * Sub-cells along x per neighbour cell for the list build: each cell is cut
  * into k slices of equal width along x, the particles are sorted by slice
  * within their cell, and the list build scans only the slices that overlap a
  * particle's x window in each row of cells, so fewer candidates are tested
