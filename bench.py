@@ -744,7 +744,7 @@ def _run_snap_on_stream(args, torch, dist, snap, rank, world, dev_index, barrier
                 "key": "set by flags", "list_subcells": max(args.subcells, 0)}
     else:
         from paper_2609_21204_b300 import autotune
-        tune = autotune.autotune(s, precision="mixed", blocks=(128, 256), skins=(0.3, 0.4, 0.5, 0.6, 0.7),
+        tune = autotune.autotune(s, precision="mixed", blocks=(128, 256), skins=(0.3, 0.35, 0.4, 0.45, 0.5, 0.6),
                                  steps=200, warmup=40, state=state)
 
     def make(precision):
